@@ -1,0 +1,278 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each test ties one part of the oracle to the paper or to mathematics that the oracle's
+code does not share: an independent Philox implementation, a 60-digit evaluation of the
+threshold table, a dynamic-programming knapsack optimum and the closed-form cases of
+eq. (1), binomial frequencies of the observation, and the amplitude (rotation-matrix)
+form of the loop against the angle-index form.
+"""
+import math
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2609_30862_gb300 import workload as W
+
+
+# --------------------------------------------------------------------------- Philox
+
+_TORCH_PHILOX_PROG = r"""
+#include <ATen/core/PhiloxRNGEngine.h>
+#include <cstdio>
+#include <cstdint>
+int main() {
+  unsigned c0, c1, c2, c3, k0, k1;
+  while (std::scanf("%u %u %u %u %u %u", &c0, &c1, &c2, &c3, &k0, &k1) == 6) {
+    uint64_t seed = (uint64_t)k0 | ((uint64_t)k1 << 32);
+    uint64_t sub = (uint64_t)c2 | ((uint64_t)c3 << 32);
+    uint64_t off = (uint64_t)c0 | ((uint64_t)c1 << 32);
+    at::philox_engine e(seed, sub, off);
+    unsigned a = e(), b = e(), c = e(), d = e();
+    std::printf("%u %u %u %u\n", a, b, c, d);
+  }
+  return 0;
+}
+"""
+
+
+def _torch_include():
+    try:
+        import torch
+    except Exception:
+        return None
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    return inc if os.path.exists(os.path.join(inc, "ATen/core/PhiloxRNGEngine.h")) else None
+
+
+def test_philox_matches_pytorch_header(oracle_mod):
+    """Philox4x32-10 (Salmon et al. 2011) against PyTorch's own engine, which keys with
+    the 64-bit seed and counts (offset, subsequence) in the same four words."""
+    inc = _torch_include()
+    if inc is None or shutil.which("g++") is None:
+        pytest.skip("PyTorch headers or g++ unavailable")
+    rng = np.random.default_rng(2609)
+    cases = rng.integers(0, 2**32, size=(200, 6), dtype=np.uint64)
+    cases[0] = 0
+    cases[1] = 2**32 - 1
+    cases[2, :4] = [5, 17, 3, 0]          # the shape of a QIEO counter: (j/4, c, t, 0)
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "p.cpp")
+        exe = os.path.join(d, "p")
+        with open(src, "w") as fh:
+            fh.write(_TORCH_PHILOX_PROG)
+        try:
+            subprocess.check_call(["g++", "-O1", "-std=c++17", "-I", inc,
+                                   "-I", os.path.join(inc, "torch/csrc/api/include"),
+                                   src, "-o", exe], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            pytest.skip("PyTorch Philox header does not compile standalone here")
+        inp = "\n".join(" ".join(str(int(x)) for x in row) for row in cases) + "\n"
+        out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout
+    ref = np.array([[int(x) for x in line.split()] for line in out.strip().splitlines()],
+                   dtype=np.uint64)
+    for row, want in zip(cases, ref):
+        got = oracle_mod.philox4x32_10(row[:4], row[4:])
+        assert [int(x) for x in got] == [int(x) for x in want], row
+
+
+def test_philox_uniform_bytes(oracle_mod):
+    """Chi-square on the bytes of 16k Philox words: no bias at the 1e-6 level."""
+    out = np.concatenate([oracle_mod.philox4x32_10([i, 7, 3, 0], [1, 0]) for i in range(4096)])
+    counts = np.bincount(out.view(np.uint8), minlength=256)
+    exp = counts.sum() / 256.0
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    # 255 degrees of freedom: mean 255, sd ~22.6; 6 sd band.
+    assert 255 - 6 * 22.6 < chi2 < 255 + 6 * 22.6
+
+
+# --------------------------------------------------------------------------- table
+
+@pytest.mark.parametrize("D", [4, 8, 12, 20, 100, 200, 1000, 4000])
+def test_threshold_table_exact(oracle_mod, D):
+    """T[n] = round(sin^2(n pi / D) 2^32) exactly (60-digit evaluation), with the
+    closed-form end points T[0] = 0, T[K] = 2^31, T[2K] = 2^32 and symmetry."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    T = oracle_mod.threshold_table(D)
+    K = D // 4
+    assert T.shape == (2 * K + 1,)
+    assert int(T[0]) == 0 and int(T[K]) == 2**31 and int(T[2 * K]) == 2**32
+    for n in range(2 * K + 1):
+        exact = mp.sin(n * mp.pi / D) ** 2 * 2**32
+        want = int(mp.floor(exact + mp.mpf(1) / 2))
+        assert abs(exact - mp.floor(exact) - mp.mpf(1) / 2) > mp.mpf(10) ** -20
+        assert int(T[n]) == want, (D, n)
+        assert int(T[n]) + int(T[2 * K - n]) == 2**32
+    assert np.all(np.diff(T.astype(np.int64)) > 0)
+
+
+def test_table_rejects_bad_D(oracle_mod):
+    with pytest.raises(ValueError):
+        oracle_mod.threshold_table(10)
+
+
+# --------------------------------------------------------------------------- eq. (1)
+
+def _dp_knapsack(w, v, W_):
+    """Textbook 0/1 knapsack dynamic program over capacity (max value, weight <= W)."""
+    best = np.zeros(W_ + 1, dtype=np.int64)
+    for wi, vi in zip(w, v):
+        if wi <= W_:
+            best[wi:] = np.maximum(best[wi:], best[:W_ + 1 - wi] + vi)
+    return int(best[W_])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_equals_dp_optimum(oracle_mod, seed):
+    """Maximum of eq. (1) over all subsets = the DP optimum: every feasible subset has
+    f >= 0 and every infeasible one f < 0, so the maximiser is a feasible optimum."""
+    rng = np.random.default_rng(seed)
+    ng = int(rng.integers(1, 17))
+    w = rng.integers(1, 30, ng).astype(np.int32)
+    v = rng.integers(0, 40, ng).astype(np.int32)
+    cap = int(rng.integers(0, w.sum() + 1))
+    best, x = oracle_mod.bruteforce(w, v, cap, 3)
+    assert best == _dp_knapsack(w, v, cap)
+    assert int((w.astype(np.int64) * x).sum()) <= cap
+
+
+def test_fitness_closed_forms(oracle_mod):
+    w = np.array([4, 7, 1, 9], dtype=np.int32)
+    v = np.array([10, 3, 8, 20], dtype=np.int32)
+    cap = 11
+    assert oracle_mod.fitness([0, 0, 0, 0], w, v, cap) == 0                  # empty pack
+    assert oracle_mod.fitness([1, 1, 0, 0], w, v, cap) == 13                 # sum w = 11 = W: feasible
+    assert oracle_mod.fitness([1, 1, 1, 0], w, v, cap, 1) == -1              # sum w = 12 > W
+    assert oracle_mod.fitness([1, 1, 1, 1], w, v, cap, 1) == -(21 - 11)
+    assert oracle_mod.fitness([1, 1, 1, 1], w, v, cap, 5) == -5 * (21 - 11)  # linear in lambda
+    for j in range(4):
+        e = np.zeros(4, dtype=np.uint8)
+        e[j] = 1
+        want = int(v[j]) if w[j] <= cap else -(int(w[j]) - cap)
+        assert oracle_mod.fitness(e, w, v, cap) == want
+
+
+def test_determine_elite_lowest_index(oracle_mod):
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        f = rng.integers(-3, 3, int(rng.integers(1, 40))).astype(np.int64)
+        assert oracle_mod.determine_elite(f) == int(np.argmax(f))   # argmax: first maximum
+
+
+# --------------------------------------------------------------------------- observation
+
+@pytest.mark.parametrize("n", [0, 1, 7, 13, 25, 37, 49, 50])
+def test_observation_frequency(oracle_mod, n):
+    """With every qubit at angle index n, P(x = 1) = sin^2(n pi / D) (5 sigma band);
+    the end points are deterministic."""
+    D, K = 100, 25
+    prob = W.knapsack(500, 4)
+    st = oracle_mod.State(200, 500)
+    st.k[:] = n - K
+    st = oracle_mod.run(prob, 200, 1, seed=9, state=st)
+    p = math.sin(n * math.pi / D) ** 2
+    m = st.x.size
+    mean = st.x.mean()
+    if n in (0, 2 * K):
+        assert mean == (1.0 if n == 2 * K else 0.0)
+    else:
+        assert abs(mean - p) < 5 * math.sqrt(p * (1 - p) / m)
+
+
+# --------------------------------------------------------------------------- loop
+
+def _amplitude_angle_index(alpha, beta, D):
+    theta = np.arctan2(beta, alpha)
+    k = (theta - math.pi / 4) / (math.pi / D)
+    return np.rint(k).astype(np.int64), np.abs(k - np.rint(k)) * (math.pi / D)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+@pytest.mark.parametrize("D,ng,np_,gens,seed", [(100, 60, 24, 150, 1), (12, 30, 16, 80, 2),
+                                                (4, 20, 8, 40, 3), (100, 100, 64, 60, 5)])
+def test_angle_index_form_equals_amplitude_form(oracle_mod, rule, D, ng, np_, gens, seed):
+    """The integer angle-index loop and the rotation-matrix loop in (alpha, beta) give the
+    same alleles, fitness, elites and best record; the angle index tracks
+    atan2(beta, alpha) and the amplitudes stay normalised."""
+    prob = W.knapsack(ng, seed)
+    a = oracle_mod.run(prob, np_, gens, seed=seed, inst=7, D=D, rule=rule)
+    b = oracle_mod.run_fp64(prob, np_, gens, seed=seed, inst=7, D=D, rule=rule)
+    assert b["near_ties"] == 0
+    assert np.array_equal(a.x, b["x"]) and np.array_equal(a.f, b["f"])
+    assert np.array_equal(a.hist_e, b["hist_e"]) and np.array_equal(a.hist_f, b["hist_f"])
+    assert np.array_equal(a.best, b["best"]) and np.array_equal(a.best_x, b["best_x"])
+    k, err = _amplitude_angle_index(b["alpha"], b["beta"], D)
+    assert np.array_equal(k, a.k.astype(np.int64))
+    assert err.max() < 1e-12 * (gens + 1)
+    assert b["max_norm_err"] < 1e-12
+    assert a.k.min() >= -(D // 4) and a.k.max() <= D // 4
+
+
+def test_elite_and_best_record(oracle_mod):
+    prob = W.knapsack(80, 11)
+    st = oracle_mod.run(prob, 32, 120, seed=11)
+    # the best-so-far is the first generation elite of maximal fitness
+    g = int(np.argmax(st.hist_f))
+    assert st.best[0] == st.hist_f.max() and st.best[1] == g
+    assert st.best[2] == st.hist_e[g]
+    assert oracle_mod.fitness(st.best_x, prob.weights, prob.values, prob.capacity) == st.best[0]
+    # the last generation's elite is the lowest-index maximum of its fitness array
+    assert st.hist_e[-1] == int(np.argmax(st.f)) and st.hist_f[-1] == st.f.max()
+    # fitness of every chromosome of the last generation agrees with eq. (1)
+    for c in range(32):
+        assert st.f[c] == oracle_mod.fitness(st.x[c], prob.weights, prob.values, prob.capacity)
+
+
+def test_ties_pick_lowest_index(oracle_mod):
+    """With two items there are at most four distinct strings, so many chromosomes tie
+    for the maximum in every generation; the elite must be the first of them."""
+    prob = W.custom_problem([3, 4], [5, 6], 5)
+    st = oracle_mod.State(16, 2)
+    for _ in range(30):
+        st = oracle_mod.run(prob, 16, 1, seed=5, state=st)
+        assert st.hist_e[-1] == int(np.argmax(st.f))
+        assert (st.f == st.f.max()).sum() >= 1
+
+
+def test_split_runs_equal_one_run(oracle_mod):
+    """run(a) then run(b) equals run(a + b): the random stream is keyed by the absolute
+    generation and the last CIP of a run is not repeated."""
+    prob = W.knapsack(70, 2)
+    one = oracle_mod.run(prob, 20, 90, seed=3, rule=1)
+    two = oracle_mod.run(prob, 20, 35, seed=3, rule=1)
+    two = oracle_mod.run(prob, 20, 55, seed=3, rule=1, state=two)
+    for name in ("k", "t", "best", "best_x", "x", "f", "hist_e", "hist_f"):
+        assert np.array_equal(getattr(one, name), getattr(two, name)), name
+
+
+def test_best_bounded_by_optimum(oracle_mod):
+    """QIEO is a heuristic: its best is never above the exact optimum (reaching it is
+    reported, not required)."""
+    for seed in range(4):
+        prob = W.knapsack(18, 40 + seed)
+        opt, _ = oracle_mod.bruteforce(prob.weights, prob.values, prob.capacity)
+        st = oracle_mod.run(prob, 32, 200, seed=seed)
+        assert st.best[0] <= opt
+        assert st.best[0] >= 0
+
+
+def test_openmp_build_identical(oracle_mod):
+    prob = W.knapsack(300, 6)
+    a = oracle_mod.run(prob, 96, 40, seed=2)
+    b = oracle_mod.run(prob, 96, 40, seed=2, kind="omp", threads=4)
+    for name in ("k", "t", "best", "best_x", "x", "f", "hist_e", "hist_f"):
+        assert np.array_equal(getattr(a, name), getattr(b, name)), name
+
+
+def test_rejects_invalid(oracle_mod):
+    prob = W.knapsack(10, 1)
+    with pytest.raises(ValueError):
+        oracle_mod.run(prob, 4, 1, D=30)
+    with pytest.raises(ValueError):
+        oracle_mod.run(prob, 4, 1, lam=0)
+    with pytest.raises(ValueError):
+        oracle_mod.run(prob, 0, 1)
