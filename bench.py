@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the QIEO generation loop on GB300.
+
+One step = one full solve of the named workload: reset to generation 0 (a0), then every
+generation's CIP + QIP + Evaluation + DetermineElite (a1-a4, one fused kernel each) and the
+final CIP (a5). The metric is gene-updates/s = Np * Ng * generations / time, summed over
+all ranks (each rank solves its own independent instance: weak scaling, no collective on
+the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
+  python bench.py --impl reference ...   # the CPU oracle timed on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_30862_gb300 import workload as WL  # noqa: E402
+
+METRIC = "gene-updates/s (Np*Ng*gens) & % roofline"
+UNIT = "gene-updates/s"
+SM_COUNT = 152
+LANES_PER_SM = 128
+# Integer operations per gene-update that the method itself needs:
+# Philox4x32-10 = 10 rounds x (2 wide multiplies + 2 three-input xors) per 4 genes = 10,
+# CIP (packed add/max/sub/min on 2 genes) = 2, observation (index extract + compare) = 2,
+# evaluation (packed item add) = 1, allele packing = 1.
+ALU_OPS_PER_GENE = 16
+STATE_BYTES_PER_GENE = 4          # int16 angle index read + written once per generation
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WL.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload_config(name: str) -> dict:
+    c = WL.WORKLOADS[name]
+    return {
+        "workload": "%s: 0/1 knapsack Ng=%d items (w uniform [1,10], v=w+5, W=floor(sum w/2)), "
+                    "Np=%d chromosomes, %d generations, dtheta=0.01pi, start pi/4, int16 angle "
+                    "state, Philox seed %d" % (name, c["ng"], c["np"], c["gens"], c["seed"]),
+        "ng": c["ng"], "np": c["np"], "generations": c["gens"], "rotation_rule": "R1",
+    }
+
+
+def load_peaks() -> tuple[dict, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def profile_traffic(kernel: str, workload: str):
+    """Per-launch DRAM traffic from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    hs = hashlib.sha256()
+    for name in ("qieo_kernels.cuh", "qieo_api.cu"):
+        with open(os.path.join(ROOT, "paper_2609_30862_gb300", "csrc", name), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        sm, mx, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s, p in zip(sm, power) if p >= 0.5 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power)}
+
+
+def gpu_id_for_smi(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    return vis.split(",")[dev] if vis else str(dev)
+
+
+# ------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(name: str, target_s: float = 10.0):
+    """The OpenMP build of the oracle, as it stands, on all host cores, over the first
+    generations of the named workload. Returns (gene-updates/s, cores, sample text)."""
+    from oracle import oracle as O
+    c = WL.WORKLOADS[name]
+    prob = WL.knapsack(c["ng"], c["item_seed"])
+    cores = os.cpu_count() or 1
+    O.build()
+    O.set_threads(cores)
+    t0 = time.perf_counter()
+    O.run(prob, c["np"], 1, seed=c["seed"], inst=c["inst"], kind="omp", threads=cores)
+    t1 = time.perf_counter() - t0
+    gens = int(max(1, min(c["gens"], round(target_s / max(t1, 1e-6)))))
+    t0 = time.perf_counter()
+    O.run(prob, c["np"], gens, seed=c["seed"], inst=c["inst"], kind="omp", threads=cores)
+    dt = time.perf_counter() - t0
+    rate = c["np"] * c["ng"] * gens / dt
+    sample = "first %d of %d generations of %s (Np=%d, Ng=%d), OpenMP build, %d threads" % (
+        gens, c["gens"], name, c["np"], c["ng"], cores)
+    return rate, cores, sample, gens, dt
+
+
+def run_reference(a):
+    """--impl reference: the CPU oracle (OpenMP build, all host cores) timed per step on a
+    bounded sample of the same workload. Rank 0 only."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from oracle import oracle as O
+    c = WL.WORKLOADS[a.workload]
+    prob = WL.knapsack(c["ng"], c["item_seed"])
+    cores = os.cpu_count() or 1
+    O.build()
+    budget_s = 150.0
+    t0 = time.perf_counter()
+    O.run(prob, c["np"], 1, seed=c["seed"], inst=c["inst"], kind="omp", threads=cores)
+    t1 = time.perf_counter() - t0
+    per_step = budget_s / max(1, a.steps + a.warmup)
+    gens = int(max(1, min(c["gens"], per_step / max(t1, 1e-6))))
+    for _ in range(a.warmup):
+        O.run(prob, c["np"], gens, seed=c["seed"], inst=c["inst"], kind="omp", threads=cores)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        O.run(prob, c["np"], gens, seed=c["seed"], inst=c["inst"], kind="omp", threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = c["np"] * c["ng"] * gens * a.steps / total
+    sample = "first %d of %d generations of %s per step (Np=%d, Ng=%d), OpenMP build, %d threads" % (
+        gens, c["gens"], a.workload, c["np"], c["ng"], cores)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(a.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------- GPU path
+
+def run_gpu(a):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2609_30862_gb300 import qieo as Q
+    Q.load()
+    c = WL.WORKLOADS[a.workload]
+    prob = WL.knapsack(c["ng"], c["item_seed"])
+    np_, ng, G = c["np"], c["ng"], c["gens"]
+    genes_per_step = np_ * ng * G
+    stream = torch.cuda.Stream()
+    inst = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
+                      stream=stream.cuda_stream)
+    shape = inst.shape()
+    state_bytes = np_ * ((ng + 7) // 8) * 16
+    flush = state_bytes < 2 * L2_BYTES
+    flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda") if flush else None
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            if flush:
+                flush_buf.fill_(1)
+            inst.reset()
+            inst.run(G)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        sampler = ClockSampler(gpu_id_for_smi(torch, local)) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        barrier()
+        wall0 = time.perf_counter()
+        for i in range(a.steps):
+            if flush:
+                flush_buf.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            inst.reset()
+            evs[i][1].record(stream)
+            inst.run(G)
+            evs[i][2].record(stream)
+        barrier()
+        wall = time.perf_counter() - wall0
+        clocks = sampler.stop() if sampler else None
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
+    run_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
+    total_ms = float(sum(step_ms))
+    tot = torch.tensor([total_ms, float(sum(run_ms))], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms, run_total_ms = float(tot[0]), float(tot[1])
+    value = world * genes_per_step * a.steps / (total_ms / 1e3)
+
+    # roofline of the fused generation kernel: average launch duration over the timed
+    # region (events around each run: G generation launches + 1 final CIP launch)
+    launch_s = run_total_ms / 1e3 / (a.steps * G)
+    peaks, peak_src = load_peaks()
+    genes_per_launch = np_ * ng
+    l2_resident = state_bytes < L2_BYTES
+    if l2_resident:
+        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = SM_COUNT * LANES_PER_SM * max_mhz * 1e6 / 1e12
+        achieved = ALU_OPS_PER_GENE * genes_per_launch / launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak,
+                "peak_source": "derived: %d SMs x %d int32 lanes x %.0f MHz" % (
+                    SM_COUNT, LANES_PER_SM, max_mhz)}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = STATE_BYTES_PER_GENE * genes_per_launch / launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": "%s hbm_gbs" % peak_src}
+    roof["traffic"] = profile_traffic("generation_kernel", a.workload)
+    roof["kernel"] = "generation_kernel"
+    roof["launch_us"] = launch_s * 1e6
+
+    # end to end through the C ABI with host buffers: create (uploads the items), run,
+    # read the best record back, destroy -- every step
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for i in range(a.e2e_steps + 1):
+            barrier()
+            t0 = time.perf_counter()
+            h = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
+                           stream=stream.cuda_stream)
+            h.run(G)
+            bits, bf, bg, bc = h.best()
+            h.close()
+            torch.cuda.synchronize()
+            if i > 0:
+                e2e_times.append(time.perf_counter() - t0)
+    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * genes_per_step * len(e2e_times) / float(e2e_t[0])
+    svec = (ng + 7) // 8
+    h2d = svec * 8 * 4 * (1 if shape.narrow else 2) + 4 * (2 * 25 + 1)
+    d2h = ((svec + 15) // 16) * 16 + 24
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": dict(workload_config(a.workload),
+                       l2="flushed between steps (512 MB write)" if flush
+                       else "state larger than L2 (no flush)",
+                       parallelism="one independent instance per GPU",
+                       launch_shape="%dx%d lanes/warps per row, %d rows per block, grid %dx%d" % (
+                           shape.lanes_per_row, shape.warps_per_row, shape.rows_per_cta,
+                           shape.grid_x, shape.grid_y)),
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": "qieo_create_instance from host arrays + qieo_run + qieo_get_best + "
+                        "qieo_destroy_instance per step"},
+        "gpu_launches": a.steps * (G + 2),
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, cores, sample, gens, dt = oracle_sample(a.workload)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    inst.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return np
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

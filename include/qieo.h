@@ -1,0 +1,161 @@
+/*
+ * qieo.h -- C ABI of the GB300 QIEO library (quantum-inspired evolutionary optimisation
+ * of the 0/1 knapsack, arxiv 2609.30862).
+ *
+ * One QIEO instance holds a population of np chromosomes of ng qubits (Sec. I, Sec. III-A)
+ * for one knapsack problem. Each generation (Sec. III-B, Fig. 1) observes every qubit
+ * (QIP), evaluates eq. (1) for every chromosome (Evaluation), picks the generation-best
+ * chromosome (DetermineElite) and rotates every qubit one step toward the elite's allele
+ * (CIP). All four steps of a generation run in one fused CUDA kernel on the GPU.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: a qieo_status; QIEO_OK (0) on success. No entry point aborts the
+ *     process; on failure the reason is available from qieo_last_error() on the calling
+ *     thread and the instance is left as it was before the call unless stated otherwise.
+ *   - Host pointers are caller-owned. Input arrays are copied before the call returns;
+ *     output arrays must hold the stated number of elements.
+ *   - The library owns the device memory of an instance from qieo_create_instance to
+ *     qieo_destroy_instance.
+ *   - An instance may be used from one host thread at a time.
+ *
+ * Qubit representation: the amplitude pair (alpha, beta) = (cos theta, sin theta) is held
+ * as the angle index k in [-K, K] with theta = pi/4 + k pi/D, K = D/4 (so theta stays in
+ * [0, pi/2]). Observation draws u = Philox4x32-10 word (j mod 4) of counter
+ * (j div 4, c, t, 0) under key (seed, instance_id) and sets x = 1 iff
+ * u < T[k + K], T[n] = round(sin^2(n pi/D) 2^32) (mirrored: T[2K-n] = 2^32 - T[n]).
+ * Every result is therefore exact and reproducible bit for bit.
+ */
+#ifndef QIEO_H
+#define QIEO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QIEO_OK = 0,
+    QIEO_ERR_INVALID = 1,   /* an argument is out of range; nothing was changed */
+    QIEO_ERR_OOM = 2,       /* device memory could not be obtained */
+    QIEO_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    QIEO_ERR_TIMEOUT = 4,   /* a bounded wait for the device ran out */
+    QIEO_ERR_BUSY = 5       /* the instance is in use by an unfinished operation */
+} qieo_status;
+
+/* Opaque, library-owned. */
+typedef struct qieo_instance qieo_instance;
+
+/* One 0/1 knapsack problem (Sec. III-A): item j has weight weights[j] >= 0 and value
+ * values[j]; capacity W >= 0. Both arrays are host memory of ng int32 entries and are
+ * copied by qieo_create_instance. */
+typedef struct {
+    int32_t ng;
+    const int32_t *weights;
+    const int32_t *values;
+    int64_t capacity;
+} qieo_problem;
+
+/* Rotation rules of CIP (Sec. III-B "lookup-table rotation toward the elite"):
+ * R1 moves every qubit one step toward the elite's allele; R2 moves only the qubits
+ * whose observed allele differs from the elite's. */
+#define QIEO_RULE_R1 0
+#define QIEO_RULE_R2 1
+
+/* flags */
+#define QIEO_FLAG_NO_GRAPH      0x1   /* launch generations one by one, no CUDA graph */
+#define QIEO_FLAG_SYNC_RUN      0x2   /* qieo_run waits (bounded) for the device */
+#define QIEO_FLAG_FORCE_WIDE    0x4   /* use 64-bit item sums even for small items */
+#define QIEO_FLAG_TIME_KERNELS  0x8   /* time the generation kernels with CUDA events */
+
+typedef struct {
+    int32_t np;              /* chromosomes, >= 1 */
+    int32_t dtheta_den;      /* D: rotation step pi/D; multiple of 4 in [4, 4000]; default 100 */
+    int64_t penalty_lambda;  /* lambda of eq. (1), >= 1; default 1 */
+    uint32_t seed;           /* Philox key word 0 */
+    uint32_t instance_id;    /* Philox key word 1 */
+    int32_t rotate_rule;     /* QIEO_RULE_R1 (default) or QIEO_RULE_R2 */
+    int32_t elite_on_host;   /* 0: DetermineElite on the device, fused (default);
+                                1: host variant (device->host fitness copy + host argmax) */
+    int32_t flags;           /* QIEO_FLAG_* */
+    void *stream;            /* cudaStream_t to run on; NULL: the instance makes its own */
+} qieo_params;
+
+/* Fills *p with the defaults above (np = 64, seed = 1, instance_id = 0). */
+void qieo_default_params(qieo_params *p);
+
+/* Creates an instance in the state before generation 0 (Sec. III-B: every qubit at
+ * theta = pi/4, i.e. k = 0; no best record). Validates: ng >= 1, np >= 1,
+ * weights >= 0, D a multiple of 4 in [4, 4000], lambda >= 1, lambda * sum(w) and
+ * sum(|v|) below 2^62. Returns QIEO_ERR_INVALID, QIEO_ERR_OOM or QIEO_ERR_CUDA on
+ * failure, with *out set to NULL. */
+qieo_status qieo_create_instance(const qieo_problem *problem, const qieo_params *params,
+                                 qieo_instance **out);
+
+/* Waits for the instance's work and frees it. NULL is accepted. */
+qieo_status qieo_destroy_instance(qieo_instance *inst);
+
+/* Returns the instance to its state before generation 0 (same problem and params). */
+qieo_status qieo_reset(qieo_instance *inst);
+
+/* Runs `generations` >= 0 generations from the current one (Fig. 1: QIP, Evaluation,
+ * DetermineElite, CIP, per generation; the CIP of the last generation is applied before
+ * returning, so run(a) followed by run(b) equals run(a + b)). Stream-ordered: returns
+ * after enqueueing unless QIEO_FLAG_SYNC_RUN is set or elite_on_host is 1. */
+qieo_status qieo_run(qieo_instance *inst, int32_t generations);
+
+/* Waits (bounded) until every operation enqueued for the instance has finished. */
+qieo_status qieo_synchronize(qieo_instance *inst);
+
+/* The best-so-far record (the first generation elite of largest fitness): its alleles as
+ * ng bytes of 0/1 into bits_out (may be NULL), fitness, generation and chromosome. Before
+ * any generation has run, generation and chromosome are -1 and fitness is 0. Waits for
+ * the instance's work. */
+qieo_status qieo_get_best(qieo_instance *inst, uint8_t *bits_out, int64_t *fitness,
+                          int32_t *generation, int32_t *chromosome);
+
+/* The angle indices k (np*ng int16, row c = chromosome c) and the next generation t. */
+qieo_status qieo_get_state(qieo_instance *inst, int16_t *k_out, int32_t *t_out);
+
+/* Eq. (1) fitness of every chromosome in the last generation run (np int64). */
+qieo_status qieo_get_fitness(qieo_instance *inst, int64_t *f_out);
+
+/* Alleles observed in the last generation run (np*ng bytes of 0/1). */
+qieo_status qieo_get_alleles(qieo_instance *inst, uint8_t *x_out);
+
+/* Elite index and fitness of generations first .. first+n-1 (all < t). */
+qieo_status qieo_get_elite_history(qieo_instance *inst, int32_t first, int32_t n,
+                                   int32_t *idx_out, int64_t *fit_out);
+
+/* The observation thresholds T[0 .. 2K] the device uses (2K+1 uint64). */
+qieo_status qieo_get_threshold_table(qieo_instance *inst, uint64_t *t_out);
+
+/* Launch shape of the fused generation kernel. Results do not depend on it (all sums are
+ * exact integers and every draw is keyed by gene, chromosome and generation). */
+typedef struct {
+    int32_t lanes_per_row;   /* 1, 2, 4, 8, 16 or 32 threads of a warp on one row */
+    int32_t warps_per_row;   /* 1, 2, 4 or 8 warps on one row tile (lanes_per_row 32 only) */
+    int32_t rows_per_cta;    /* chromosomes per thread block, 1 .. 1024 */
+    int32_t narrow;          /* out: 1 when 16-bit packed item sums are in use */
+    int32_t grid_x, grid_y;  /* out: gene tiles, row chunks */
+} qieo_launch_shape;
+
+qieo_status qieo_get_launch_shape(qieo_instance *inst, qieo_launch_shape *shape);
+qieo_status qieo_set_launch_shape(qieo_instance *inst, const qieo_launch_shape *shape);
+
+/* Accumulated device time of the generation kernels (QIEO_FLAG_TIME_KERNELS) and the
+ * number of generation-kernel launches it covers; qieo_reset clears neither. */
+qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launches);
+
+/* Philox4x32-10 on the device for n (counter, key) pairs: ctr_key is n*6 host uint32
+ * (c0 c1 c2 c3 k0 k1), out is n*4 host uint32. Uses the library's default stream. */
+qieo_status qieo_philox(const uint32_t *ctr_key, uint32_t *out, int32_t n);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *qieo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QIEO_H */

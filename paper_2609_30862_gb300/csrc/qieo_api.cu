@@ -1,0 +1,772 @@
+// qieo_api.cu -- host side of the C ABI declared in include/qieo.h.
+//
+// An instance owns one device allocation holding the qubit state, the packed alleles, the
+// items, the elite and best rows, the row accumulators and the per-generation records.
+// qieo_run enqueues one fused generation kernel per generation (replayed from a cached
+// CUDA graph) plus one final CIP launch; with elite_on_host it instead copies the row sums
+// to the host after each generation, picks the elite there and records it with a
+// one-block kernel (the host DetermineElite variant of Sec. III-C / Sec. VII P4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/qieo.h"
+#include "qieo_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qieo_status fail(qieo_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+qieo_status fail(qieo_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t err_ = (expr);                                                         \
+        if (err_ != cudaSuccess)                                                           \
+            return fail(err_ == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(err_), __FILE__,       \
+                        __LINE__);                                                         \
+    } while (0)
+
+constexpr int32_t kMaxD = 4000;
+constexpr double kWaitSeconds = 600.0;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int pow2_ceil(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct qieo_instance {
+    int32_t np = 0, ng = 0, svec = 0, xstride = 0, K = 0, D = 0;
+    int32_t rule = 0, host_de = 0, flags = 0, narrow = 0;
+    int64_t capacity = 0, lambda = 1;
+    uint32_t seed = 0, inst_id = 0;
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // device memory
+    void *block = nullptr;
+    size_t block_bytes = 0;
+    qieo::GenParams gp{};
+    int32_t *hist_e = nullptr;
+    int64_t *hist_f = nullptr;
+    int32_t hist_cap = 0;
+
+    // host mirror of the generation counter (number of generations run since reset)
+    int32_t t = 0;
+
+    // launch shape
+    int32_t lanes = 32, warps = 8, rows_per_cta = 1, grid_x = 1, grid_y = 1;
+    size_t smem = 0;
+
+    // CUDA graphs keyed by the number of generations of a run; a graph is captured the
+    // second time a run length is seen (a one-off run is cheaper to launch directly)
+    std::map<int32_t, cudaGraphExec_t> graphs;
+    std::map<int32_t, int32_t> run_lengths_seen;
+
+    // kernel timing
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double kernel_ms = 0.0;
+    int64_t kernel_launches = 0;
+
+    // host DetermineElite
+    unsigned long long *h_acc = nullptr;
+};
+
+namespace {
+
+void drop_graphs(qieo_instance *q)
+{
+    for (auto &kv : q->graphs) cudaGraphExecDestroy(kv.second);
+    q->graphs.clear();
+}
+
+void choose_shape(qieo_instance *q)
+{
+    const int svec = q->svec;
+    if (svec <= 16) {
+        q->lanes = pow2_ceil(svec);
+        q->warps = 1;
+    } else {
+        q->lanes = 32;
+        q->warps = std::min(8, pow2_ceil((svec + 31) / 32));
+    }
+    const int tile = q->lanes * q->warps;
+    const int rpp = qieo::kThreads / tile;
+    q->grid_x = (svec + tile - 1) / tile;
+    const long target = 4L * std::max(q->sm_count, 1);
+    long rows = ((long)q->np * q->grid_x + target - 1) / target;
+    rows = std::max<long>(rows, 1);
+    rows = (rows + rpp - 1) / rpp * rpp;
+    rows = std::min<long>(rows, 1024 / rpp * rpp);
+    const long np_r = ((long)q->np + rpp - 1) / rpp * rpp;
+    rows = std::min(rows, np_r);
+    q->rows_per_cta = (int32_t)rows;
+    q->grid_y = (q->np + q->rows_per_cta - 1) / q->rows_per_cta;
+}
+
+size_t shared_bytes(const qieo_instance *q)
+{
+    const size_t thr = align_up((size_t)(2 * q->K + 1) * 4, 16);
+    return thr + (size_t)q->rows_per_cta * 2 * (q->narrow ? 4 : 8);
+}
+
+template <bool N, int R>
+cudaError_t launch_gen_t(const qieo_instance *q, int apply_cip, int do_de)
+{
+    qieo::GenParams p = q->gp;
+    p.apply_cip = apply_cip;
+    p.do_de = do_de;
+    p.lanes = q->lanes;
+    p.warps = q->warps;
+    p.rows_per_cta = q->rows_per_cta;
+    qieo::generation_kernel<N, R>
+        <<<dim3(q->grid_x, q->grid_y), qieo::kThreads, q->smem, q->stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de)
+{
+    if (q->narrow) {
+        return q->rule ? launch_gen_t<true, 1>(q, apply_cip, do_de)
+                       : launch_gen_t<true, 0>(q, apply_cip, do_de);
+    }
+    return q->rule ? launch_gen_t<false, 1>(q, apply_cip, do_de)
+                   : launch_gen_t<false, 0>(q, apply_cip, do_de);
+}
+
+cudaError_t launch_final_cip(const qieo_instance *q)
+{
+    const size_t total = (size_t)q->np * q->svec;
+    const int blocks = (int)std::min<size_t>((total + qieo::kThreads - 1) / qieo::kThreads,
+                                             (size_t)std::max(q->sm_count, 1) * 8);
+    if (q->rule)
+        qieo::cip_kernel<1><<<blocks, qieo::kThreads, 0, q->stream>>>(
+            q->gp.state, q->gp.xbits, q->gp.elite, q->np, q->svec, q->xstride, q->K);
+    else
+        qieo::cip_kernel<0><<<blocks, qieo::kThreads, 0, q->stream>>>(
+            q->gp.state, q->gp.xbits, q->gp.elite, q->np, q->svec, q->xstride, q->K);
+    return cudaGetLastError();
+}
+
+qieo_status wait_stream(cudaStream_t s)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) return QIEO_OK;
+        if (e != cudaErrorNotReady)
+            return fail(QIEO_ERR_CUDA, "device work failed: %s", cudaGetErrorString(e));
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > kWaitSeconds)
+            return fail(QIEO_ERR_TIMEOUT, "device work did not finish within %.0f s", kWaitSeconds);
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+    }
+}
+
+// Threshold table T[n] = round(sin^2(n pi / D) 2^32), evaluated as 2^31 (1 - cos(2 n pi/D))
+// in extended precision for n <= K and mirrored (T[2K-n] = 2^32 - T[n]) above.
+void build_thresholds(int32_t D, std::vector<uint64_t> &T)
+{
+    const int32_t K = D / 4;
+    T.assign((size_t)(2 * K + 1), 0);
+    const long double pi = acosl(-1.0L);
+    for (int32_t n = 0; n <= K; ++n) {
+        const long double c = cosl(2.0L * pi * (long double)n / (long double)D);
+        const long double val = 2147483648.0L * (1.0L - c);
+        T[(size_t)n] = (uint64_t)llroundl(val);
+    }
+    T[0] = 0;
+    T[(size_t)K] = 1ull << 31;
+    for (int32_t n = K + 1; n <= 2 * K; ++n) T[(size_t)n] = (1ull << 32) - T[(size_t)(2 * K - n)];
+}
+
+qieo_status ensure_history(qieo_instance *q, int32_t need)
+{
+    if (need <= q->hist_cap) return QIEO_OK;
+    int32_t cap = std::max<int32_t>(need, std::max<int32_t>(1024, q->hist_cap * 2));
+    int32_t *e = nullptr;
+    int64_t *f = nullptr;
+    CUDA_TRY(cudaMalloc(&e, (size_t)cap * sizeof(int32_t)));
+    cudaError_t err = cudaMalloc(&f, (size_t)cap * sizeof(int64_t));
+    if (err != cudaSuccess) {
+        cudaFree(e);
+        return fail(QIEO_ERR_OOM, "history buffer: %s", cudaGetErrorString(err));
+    }
+    if (q->hist_cap > 0) {
+        CUDA_TRY(cudaMemcpyAsync(e, q->hist_e, (size_t)q->hist_cap * sizeof(int32_t),
+                                 cudaMemcpyDeviceToDevice, q->stream));
+        CUDA_TRY(cudaMemcpyAsync(f, q->hist_f, (size_t)q->hist_cap * sizeof(int64_t),
+                                 cudaMemcpyDeviceToDevice, q->stream));
+        qieo_status st = wait_stream(q->stream);
+        if (st != QIEO_OK) return st;
+        cudaFree(q->hist_e);
+        cudaFree(q->hist_f);
+    }
+    q->hist_e = e;
+    q->hist_f = f;
+    q->hist_cap = cap;
+    q->gp.hist_e = e;
+    q->gp.hist_f = f;
+    drop_graphs(q);
+    return QIEO_OK;
+}
+
+qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
+{
+    if (q->flags & QIEO_FLAG_TIME_KERNELS) CUDA_TRY(cudaEventRecord(q->ev0, q->stream));
+    for (int32_t g = 0; g < G; ++g) CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 1));
+    if (q->flags & QIEO_FLAG_TIME_KERNELS) CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
+    CUDA_TRY(launch_final_cip(q));
+    return QIEO_OK;
+}
+
+qieo_status run_device(qieo_instance *q, int32_t G)
+{
+    const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
+    const bool first_time = q->run_lengths_seen[G]++ == 0;
+    if ((q->flags & QIEO_FLAG_NO_GRAPH) || (first_time && !q->graphs.count(G))) {
+        qieo_status st = enqueue_device_run(q, G);
+        if (st != QIEO_OK) return st;
+    } else {
+        auto it = q->graphs.find(G);
+        cudaGraphExec_t exec = nullptr;
+        if (it == q->graphs.end()) {
+            if (q->graphs.size() >= 8) drop_graphs(q);
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(q->stream, cudaStreamCaptureModeThreadLocal));
+            qieo_status st = enqueue_device_run(q, G);
+            cudaError_t ce = cudaStreamEndCapture(q->stream, &graph);
+            if (st != QIEO_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ce != cudaSuccess) return fail(QIEO_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(QIEO_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            q->graphs[G] = exec;
+        } else {
+            exec = it->second;
+        }
+        CUDA_TRY(cudaGraphLaunch(exec, q->stream));
+    }
+    if (timing && G > 0) {
+        qieo_status st = wait_stream(q->stream);
+        if (st != QIEO_OK) return st;
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, q->ev0, q->ev1));
+        q->kernel_ms += ms;
+        q->kernel_launches += G;
+    }
+    return QIEO_OK;
+}
+
+template <bool N>
+cudaError_t launch_record(const qieo_instance *q, int32_t e)
+{
+    qieo::record_elite_kernel<N><<<1, qieo::kThreads, 0, q->stream>>>(q->gp, e);
+    return cudaGetLastError();
+}
+
+qieo_status run_host_de(qieo_instance *q, int32_t G)
+{
+    const size_t nacc = (size_t)q->np * (q->narrow ? 1 : 2);
+    for (int32_t g = 0; g < G; ++g) {
+        CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 0));
+        CUDA_TRY(cudaMemcpyAsync(q->h_acc, q->gp.acc, nacc * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, q->stream));
+        qieo_status st = wait_stream(q->stream);
+        if (st != QIEO_OK) return st;
+        int32_t e = 0;
+        int64_t bf = INT64_MIN;
+        for (int32_t c = 0; c < q->np; ++c) {
+            int64_t sw, sv;
+            if (q->narrow) {
+                sw = (int64_t)(q->h_acc[c] & 0xffffffffull);
+                sv = (int64_t)(q->h_acc[c] >> 32);
+            } else {
+                sw = (int64_t)q->h_acc[2 * (size_t)c];
+                sv = (int64_t)q->h_acc[2 * (size_t)c + 1];
+            }
+            const int64_t f = sw <= q->capacity ? sv : -q->lambda * (sw - q->capacity);
+            if (f > bf) {
+                bf = f;
+                e = c;
+            }
+        }
+        CUDA_TRY(q->narrow ? launch_record<true>(q, e) : launch_record<false>(q, e));
+    }
+    CUDA_TRY(launch_final_cip(q));
+    return wait_stream(q->stream);
+}
+
+qieo_status check_inst(const qieo_instance *q)
+{
+    if (!q) return fail(QIEO_ERR_INVALID, "instance is NULL");
+    return QIEO_OK;
+}
+
+qieo_status set_device(const qieo_instance *q)
+{
+    CUDA_TRY(cudaSetDevice(q->device));
+    return QIEO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qieo_default_params(qieo_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->np = 64;
+    p->dtheta_den = 100;
+    p->penalty_lambda = 1;
+    p->seed = 1;
+    p->instance_id = 0;
+    p->rotate_rule = QIEO_RULE_R1;
+    p->elite_on_host = 0;
+    p->flags = 0;
+    p->stream = nullptr;
+}
+
+const char *qieo_last_error(void) { return g_last_error.c_str(); }
+
+qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
+                                 qieo_instance **out)
+{
+    if (out) *out = nullptr;
+    if (!pr || !pa || !out) return fail(QIEO_ERR_INVALID, "NULL argument");
+    if (pr->ng < 1) return fail(QIEO_ERR_INVALID, "ng must be >= 1 (got %d)", pr->ng);
+    if (!pr->weights || !pr->values) return fail(QIEO_ERR_INVALID, "weights/values are NULL");
+    if (pa->np < 1) return fail(QIEO_ERR_INVALID, "np must be >= 1 (got %d)", pa->np);
+    if (pa->dtheta_den < 4 || pa->dtheta_den > kMaxD || pa->dtheta_den % 4 != 0)
+        return fail(QIEO_ERR_INVALID, "dtheta_den must be a multiple of 4 in [4, %d] (got %d)",
+                    kMaxD, pa->dtheta_den);
+    if (pa->penalty_lambda < 1) return fail(QIEO_ERR_INVALID, "penalty_lambda must be >= 1");
+    if (pa->rotate_rule != QIEO_RULE_R1 && pa->rotate_rule != QIEO_RULE_R2)
+        return fail(QIEO_ERR_INVALID, "rotate_rule must be 0 (R1) or 1 (R2)");
+    if (pa->elite_on_host != 0 && pa->elite_on_host != 1)
+        return fail(QIEO_ERR_INVALID, "elite_on_host must be 0 or 1");
+    if (pr->capacity < 0) return fail(QIEO_ERR_INVALID, "capacity must be >= 0");
+
+    int64_t sum_w = 0, sum_absv = 0;
+    int32_t max_w = 0, max_v = 0, min_v = 0;
+    for (int32_t j = 0; j < pr->ng; ++j) {
+        if (pr->weights[j] < 0) return fail(QIEO_ERR_INVALID, "weight %d is negative", j);
+        sum_w += pr->weights[j];
+        sum_absv += std::llabs((long long)pr->values[j]);
+        max_w = std::max(max_w, pr->weights[j]);
+        max_v = std::max(max_v, pr->values[j]);
+        min_v = std::min(min_v, pr->values[j]);
+    }
+    const int64_t lim = (int64_t)1 << 62;
+    if (sum_w >= lim / pa->penalty_lambda || sum_absv >= lim)
+        return fail(QIEO_ERR_INVALID, "lambda * sum(w) or sum(|v|) reaches 2^62");
+
+    qieo_instance *q = new (std::nothrow) qieo_instance();
+    if (!q) return fail(QIEO_ERR_OOM, "host allocation failed");
+    q->np = pa->np;
+    q->ng = pr->ng;
+    q->svec = (pr->ng + 7) / 8;
+    q->xstride = (int32_t)align_up((size_t)q->svec, 16);
+    q->D = pa->dtheta_den;
+    q->K = pa->dtheta_den / 4;
+    q->rule = pa->rotate_rule;
+    q->host_de = pa->elite_on_host;
+    q->flags = pa->flags;
+    q->capacity = pr->capacity;
+    q->lambda = pa->penalty_lambda;
+    q->seed = pa->seed;
+    q->inst_id = pa->instance_id;
+    // 16-bit packed sums: a warp sums at most 256 genes, 256 * 255 < 2^16; a row at most
+    // 2^24 genes, 2^24 * 255 < 2^32.
+    q->narrow = (!(pa->flags & QIEO_FLAG_FORCE_WIDE) && max_w <= 255 && max_v <= 255 &&
+                 min_v >= 0 && pr->ng <= (1 << 24)) ? 1 : 0;
+
+    auto bail = [&](qieo_status st) {
+        qieo_destroy_instance(q);
+        return st;
+    };
+
+    cudaError_t ce = cudaGetDevice(&q->device);
+    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(ce)));
+    ce = cudaDeviceGetAttribute(&q->sm_count, cudaDevAttrMultiProcessorCount, q->device);
+    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "device query: %s", cudaGetErrorString(ce)));
+    if (pa->stream) {
+        q->stream = (cudaStream_t)pa->stream;
+    } else {
+        ce = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "stream: %s", cudaGetErrorString(ce)));
+        q->own_stream = true;
+    }
+    ce = cudaEventCreate(&q->ev0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&q->ev1);
+    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "events: %s", cudaGetErrorString(ce)));
+
+    // One device block: state | xbits | items | elite | best_row | acc | fitness | best |
+    // gen | ticket | thresholds, each 256-byte aligned.
+    const size_t n_state = (size_t)q->np * q->svec * sizeof(uint4);
+    const size_t n_x = (size_t)q->np * q->xstride;
+    const size_t n_items = q->narrow ? (size_t)q->svec * 8 * 4 : (size_t)q->svec * 8 * 4 * 2;
+    const size_t n_row = (size_t)q->xstride;
+    const size_t n_acc = (size_t)q->np * 2 * sizeof(unsigned long long);
+    const size_t n_fit = (size_t)q->np * sizeof(int64_t);
+    const size_t n_thr = (size_t)(2 * q->K + 1) * sizeof(uint32_t);
+    size_t off[11];
+    size_t sizes[11] = {n_state, n_x, n_items, n_row, n_row, n_acc, n_fit, 3 * sizeof(int64_t),
+                        sizeof(int32_t), sizeof(unsigned int), n_thr};
+    size_t total = 0;
+    for (int i = 0; i < 11; ++i) {
+        off[i] = total;
+        total = align_up(total + sizes[i], 256);
+    }
+    ce = cudaMalloc(&q->block, total);
+    if (ce != cudaSuccess)
+        return bail(fail(ce == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA,
+                         "device allocation of %zu bytes: %s", total, cudaGetErrorString(ce)));
+    q->block_bytes = total;
+    char *b = (char *)q->block;
+    qieo::GenParams &g = q->gp;
+    g.state = (uint4 *)(b + off[0]);
+    g.xbits = (uint8_t *)(b + off[1]);
+    g.elite = (uint8_t *)(b + off[3]);
+    g.best_row = (uint8_t *)(b + off[4]);
+    g.acc = (unsigned long long *)(b + off[5]);
+    g.fitness = (int64_t *)(b + off[6]);
+    g.best = (int64_t *)(b + off[7]);
+    g.gen = (int32_t *)(b + off[8]);
+    g.ticket = (unsigned int *)(b + off[9]);
+    g.thr = (const uint32_t *)(b + off[10]);
+    g.np = q->np;
+    g.svec = q->svec;
+    g.xstride = q->xstride;
+    g.K = q->K;
+    g.capacity = q->capacity;
+    g.lambda = q->lambda;
+    g.key0 = q->seed;
+    g.key1 = q->inst_id;
+
+    // Items, padded with zeros to whole vectors (padding genes add nothing).
+    const size_t ngp = (size_t)q->svec * 8;
+    std::vector<uint32_t> items(q->narrow ? ngp : 2 * ngp, 0u);
+    for (int32_t j = 0; j < q->ng; ++j) {
+        if (q->narrow) {
+            items[(size_t)j] = ((uint32_t)pr->values[j] << 16) | (uint32_t)pr->weights[j];
+        } else {
+            items[(size_t)j] = (uint32_t)pr->weights[j];
+            items[ngp + (size_t)j] = (uint32_t)pr->values[j];
+        }
+    }
+    if (q->narrow) {
+        g.items_narrow = (const uint4 *)(b + off[2]);
+    } else {
+        g.w4 = (const int4 *)(b + off[2]);
+        g.v4 = (const int4 *)(b + off[2] + ngp * 4);
+    }
+    std::vector<uint64_t> T;
+    build_thresholds(q->D, T);
+    std::vector<uint32_t> T32(T.size());
+    for (size_t i = 0; i < T.size(); ++i) T32[i] = (uint32_t)(T[i] & 0xffffffffull);
+
+    ce = cudaMemcpyAsync(b + off[2], items.data(), items.size() * 4, cudaMemcpyHostToDevice, q->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(b + off[10], T32.data(), T32.size() * 4, cudaMemcpyHostToDevice, q->stream);
+    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "upload: %s", cudaGetErrorString(ce)));
+
+    if (q->host_de) {
+        ce = cudaMallocHost(&q->h_acc, (size_t)q->np * 2 * sizeof(unsigned long long));
+        if (ce != cudaSuccess) return bail(fail(QIEO_ERR_OOM, "pinned host buffer: %s", cudaGetErrorString(ce)));
+    }
+    choose_shape(q);
+    q->smem = shared_bytes(q);
+    qieo_status st = ensure_history(q, 1024);
+    if (st != QIEO_OK) return bail(st);
+    st = qieo_reset(q);
+    if (st != QIEO_OK) return bail(st);
+    st = wait_stream(q->stream);
+    if (st != QIEO_OK) return bail(st);
+    *out = q;
+    return QIEO_OK;
+}
+
+qieo_status qieo_destroy_instance(qieo_instance *q)
+{
+    if (!q) return QIEO_OK;
+    cudaSetDevice(q->device);
+    if (q->stream) cudaStreamSynchronize(q->stream);
+    drop_graphs(q);
+    if (q->block) cudaFree(q->block);
+    if (q->hist_e) cudaFree(q->hist_e);
+    if (q->hist_f) cudaFree(q->hist_f);
+    if (q->h_acc) cudaFreeHost(q->h_acc);
+    if (q->ev0) cudaEventDestroy(q->ev0);
+    if (q->ev1) cudaEventDestroy(q->ev1);
+    if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
+    delete q;
+    return QIEO_OK;
+}
+
+qieo_status qieo_reset(qieo_instance *q)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    const size_t words = (size_t)q->np * q->svec * 4;
+    const size_t xbytes = (size_t)q->np * q->xstride;
+    const int blocks = std::max(1, std::min(q->sm_count * 4, (int)((words + 255) / 256)));
+    qieo::init_kernel<<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, words, xbytes);
+    CUDA_TRY(cudaGetLastError());
+    q->t = 0;
+    if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
+    return QIEO_OK;
+}
+
+qieo_status qieo_run(qieo_instance *q, int32_t G)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (G < 0) return fail(QIEO_ERR_INVALID, "generations must be >= 0 (got %d)", G);
+    if (G == 0) return QIEO_OK;
+    if ((int64_t)q->t + G > INT32_MAX / 2) return fail(QIEO_ERR_INVALID, "generation counter overflow");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    st = ensure_history(q, q->t + G);
+    if (st != QIEO_OK) return st;
+    st = q->host_de ? run_host_de(q, G) : run_device(q, G);
+    if (st != QIEO_OK) return st;
+    q->t += G;
+    if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
+    return QIEO_OK;
+}
+
+qieo_status qieo_synchronize(qieo_instance *q)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    return wait_stream(q->stream);
+}
+
+namespace {
+
+qieo_status fetch(qieo_instance *q, void *dst, const void *src, size_t bytes)
+{
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, q->stream));
+    return wait_stream(q->stream);
+}
+
+void unpack_row(const uint8_t *packed, int32_t ng, uint8_t *out)
+{
+    for (int32_t j = 0; j < ng; ++j) out[j] = (uint8_t)((packed[j >> 3] >> (j & 7)) & 1u);
+}
+
+}  // namespace
+
+qieo_status qieo_get_best(qieo_instance *q, uint8_t *bits_out, int64_t *fitness,
+                          int32_t *generation, int32_t *chromosome)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    int64_t best[3];
+    st = fetch(q, best, q->gp.best, sizeof best);
+    if (st != QIEO_OK) return st;
+    if (bits_out) {
+        std::vector<uint8_t> row((size_t)q->xstride);
+        st = fetch(q, row.data(), q->gp.best_row, row.size());
+        if (st != QIEO_OK) return st;
+        unpack_row(row.data(), q->ng, bits_out);
+    }
+    if (fitness) *fitness = best[0];
+    if (generation) *generation = (int32_t)best[1];
+    if (chromosome) *chromosome = (int32_t)best[2];
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_state(qieo_instance *q, int16_t *k_out, int32_t *t_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    if (k_out) {
+        std::vector<uint16_t> s((size_t)q->np * q->svec * 8);
+        st = fetch(q, s.data(), q->gp.state, s.size() * 2);
+        if (st != QIEO_OK) return st;
+        for (int32_t c = 0; c < q->np; ++c)
+            for (int32_t j = 0; j < q->ng; ++j)
+                k_out[(size_t)c * q->ng + j] =
+                    (int16_t)((int32_t)s[(size_t)c * q->svec * 8 + j] - q->K);
+    }
+    if (t_out) {
+        int32_t t = 0;
+        st = fetch(q, &t, q->gp.gen, sizeof t);
+        if (st != QIEO_OK) return st;
+        *t_out = t;
+    }
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_fitness(qieo_instance *q, int64_t *f_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!f_out) return fail(QIEO_ERR_INVALID, "f_out is NULL");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    return fetch(q, f_out, q->gp.fitness, (size_t)q->np * sizeof(int64_t));
+}
+
+qieo_status qieo_get_alleles(qieo_instance *q, uint8_t *x_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!x_out) return fail(QIEO_ERR_INVALID, "x_out is NULL");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    std::vector<uint8_t> x((size_t)q->np * q->xstride);
+    st = fetch(q, x.data(), q->gp.xbits, x.size());
+    if (st != QIEO_OK) return st;
+    for (int32_t c = 0; c < q->np; ++c)
+        unpack_row(x.data() + (size_t)c * q->xstride, q->ng, x_out + (size_t)c * q->ng);
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_elite_history(qieo_instance *q, int32_t first, int32_t n, int32_t *idx_out,
+                                   int64_t *fit_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (first < 0 || n < 0 || (int64_t)first + n > q->t)
+        return fail(QIEO_ERR_INVALID, "history range [%d, %d) outside [0, %d)", first, first + n, q->t);
+    if (n == 0) return QIEO_OK;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    if (idx_out) {
+        st = fetch(q, idx_out, q->hist_e + first, (size_t)n * sizeof(int32_t));
+        if (st != QIEO_OK) return st;
+    }
+    if (fit_out) {
+        st = fetch(q, fit_out, q->hist_f + first, (size_t)n * sizeof(int64_t));
+        if (st != QIEO_OK) return st;
+    }
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_threshold_table(qieo_instance *q, uint64_t *t_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!t_out) return fail(QIEO_ERR_INVALID, "t_out is NULL");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    std::vector<uint32_t> T32((size_t)(2 * q->K + 1));
+    st = fetch(q, T32.data(), q->gp.thr, T32.size() * 4);
+    if (st != QIEO_OK) return st;
+    for (size_t i = 0; i < T32.size(); ++i) t_out[i] = T32[i];
+    t_out[2 * q->K] = 1ull << 32;   // stored as 0; the kernel treats n = 2K as "always 1"
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_launch_shape(qieo_instance *q, qieo_launch_shape *s)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!s) return fail(QIEO_ERR_INVALID, "shape is NULL");
+    s->lanes_per_row = q->lanes;
+    s->warps_per_row = q->warps;
+    s->rows_per_cta = q->rows_per_cta;
+    s->narrow = q->narrow;
+    s->grid_x = q->grid_x;
+    s->grid_y = q->grid_y;
+    return QIEO_OK;
+}
+
+qieo_status qieo_set_launch_shape(qieo_instance *q, const qieo_launch_shape *s)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!s) return fail(QIEO_ERR_INVALID, "shape is NULL");
+    const int L = s->lanes_per_row, W = s->warps_per_row, R = s->rows_per_cta;
+    if (L < 1 || L > 32 || (L & (L - 1)))
+        return fail(QIEO_ERR_INVALID, "lanes_per_row must be a power of two in [1, 32]");
+    if (W < 1 || W > 8 || (W & (W - 1)) || (W > 1 && L != 32))
+        return fail(QIEO_ERR_INVALID, "warps_per_row must be 1, 2, 4 or 8 (>1 needs 32 lanes)");
+    const int rpp = qieo::kThreads / (L * W);
+    if (R < 1 || R > 1024 || R % rpp != 0)
+        return fail(QIEO_ERR_INVALID, "rows_per_cta must be a multiple of %d in [1, 1024]", rpp);
+    q->lanes = L;
+    q->warps = W;
+    q->rows_per_cta = R;
+    q->grid_x = (q->svec + L * W - 1) / (L * W);
+    q->grid_y = (q->np + R - 1) / R;
+    q->smem = shared_bytes(q);
+    drop_graphs(q);
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (ms) *ms = q->kernel_ms;
+    if (launches) *launches = q->kernel_launches;
+    return QIEO_OK;
+}
+
+qieo_status qieo_philox(const uint32_t *ctr_key, uint32_t *out, int32_t n)
+{
+    if (n < 0 || (n > 0 && (!ctr_key || !out))) return fail(QIEO_ERR_INVALID, "bad arguments");
+    if (n == 0) return QIEO_OK;
+    uint32_t *d_in = nullptr, *d_out = nullptr;
+    CUDA_TRY(cudaMalloc(&d_in, (size_t)n * 6 * 4));
+    cudaError_t ce = cudaMalloc(&d_out, (size_t)n * 4 * 4);
+    if (ce == cudaSuccess) ce = cudaMemcpy(d_in, ctr_key, (size_t)n * 6 * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        qieo::philox_kernel<<<(n + 255) / 256, 256>>>(d_in, d_out, n);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpy(out, d_out, (size_t)n * 4 * 4, cudaMemcpyDeviceToHost);
+    cudaFree(d_in);
+    if (d_out) cudaFree(d_out);
+    if (ce != cudaSuccess) return fail(QIEO_ERR_CUDA, "philox: %s", cudaGetErrorString(ce));
+    return QIEO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of the C ABI in include/qieo.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but
+convert arguments and raise QieoError on a non-zero status. All computation runs in the
+CUDA library; if the library is missing this module raises instead of computing anything
+on the host.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QIEO_OK = 0
+QIEO_ERR_INVALID = 1
+QIEO_ERR_OOM = 2
+QIEO_ERR_CUDA = 3
+QIEO_ERR_TIMEOUT = 4
+QIEO_ERR_BUSY = 5
+
+QIEO_RULE_R1 = 0
+QIEO_RULE_R2 = 1
+
+QIEO_FLAG_NO_GRAPH = 0x1
+QIEO_FLAG_SYNC_RUN = 0x2
+QIEO_FLAG_FORCE_WIDE = 0x4
+QIEO_FLAG_TIME_KERNELS = 0x8
+
+# Every symbol include/qieo.h declares.
+EXPORTS = (
+    "qieo_default_params", "qieo_create_instance", "qieo_destroy_instance", "qieo_reset",
+    "qieo_run", "qieo_synchronize", "qieo_get_best", "qieo_get_state", "qieo_get_fitness",
+    "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
+    "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
+    "qieo_last_error",
+)
+
+
+class QieoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("qieo status %d: %s" % (status, msg))
+        self.status = status
+
+
+class qieo_problem(C.Structure):
+    _fields_ = [("ng", C.c_int32), ("weights", C.c_void_p), ("values", C.c_void_p),
+                ("capacity", C.c_int64)]
+
+
+class qieo_params(C.Structure):
+    _fields_ = [("np", C.c_int32), ("dtheta_den", C.c_int32), ("penalty_lambda", C.c_int64),
+                ("seed", C.c_uint32), ("instance_id", C.c_uint32), ("rotate_rule", C.c_int32),
+                ("elite_on_host", C.c_int32), ("flags", C.c_int32), ("stream", C.c_void_p)]
+
+
+class qieo_launch_shape(C.Structure):
+    _fields_ = [("lanes_per_row", C.c_int32), ("warps_per_row", C.c_int32),
+                ("rows_per_cta", C.c_int32), ("narrow", C.c_int32), ("grid_x", C.c_int32),
+                ("grid_y", C.c_int32)]
+
+
+_LIB: C.CDLL | None = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libqieo.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing and _build.stale():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("QIEO CUDA library not built: %s is missing" % _build.LIB)
+    L = C.CDLL(_build.LIB)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "qieo_default_params": ([P], None),
+        "qieo_create_instance": ([P, P, P], C.c_int),
+        "qieo_destroy_instance": ([P], C.c_int),
+        "qieo_reset": ([P], C.c_int),
+        "qieo_run": ([P, i32], C.c_int),
+        "qieo_synchronize": ([P], C.c_int),
+        "qieo_get_best": ([P, P, P, P, P], C.c_int),
+        "qieo_get_state": ([P, P, P], C.c_int),
+        "qieo_get_fitness": ([P, P], C.c_int),
+        "qieo_get_alleles": ([P, P], C.c_int),
+        "qieo_get_elite_history": ([P, i32, i32, P, P], C.c_int),
+        "qieo_get_threshold_table": ([P, P], C.c_int),
+        "qieo_get_launch_shape": ([P, P], C.c_int),
+        "qieo_set_launch_shape": ([P, P], C.c_int),
+        "qieo_get_kernel_time": ([P, P, P], C.c_int),
+        "qieo_philox": ([P, P, i32], C.c_int),
+        "qieo_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != QIEO_OK:
+        raise QieoError(status, load().qieo_last_error().decode("utf8", "replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def qieo_default_params() -> qieo_params:
+    p = qieo_params()
+    load().qieo_default_params(C.byref(p))
+    return p
+
+
+def qieo_create_instance(weights, values, capacity: int, params: qieo_params):
+    """Returns an opaque handle (c_void_p). weights/values: int32 host arrays."""
+    w = np.ascontiguousarray(weights, dtype=np.int32)
+    v = np.ascontiguousarray(values, dtype=np.int32)
+    if w.shape != v.shape or w.ndim != 1:
+        raise ValueError("weights and values must be 1-D arrays of equal length")
+    pr = qieo_problem(int(w.shape[0]), w.ctypes.data, v.ctypes.data, int(capacity))
+    h = C.c_void_p()
+    _check(load().qieo_create_instance(C.byref(pr), C.byref(params), C.byref(h)))
+    return h
+
+
+def qieo_destroy_instance(h) -> None:
+    _check(load().qieo_destroy_instance(h))
+
+
+def qieo_reset(h) -> None:
+    _check(load().qieo_reset(h))
+
+
+def qieo_run(h, generations: int) -> None:
+    _check(load().qieo_run(h, int(generations)))
+
+
+def qieo_synchronize(h) -> None:
+    _check(load().qieo_synchronize(h))
+
+
+def qieo_get_best(h, ng: int):
+    bits = np.zeros(ng, dtype=np.uint8)
+    f, g, c = C.c_int64(), C.c_int32(), C.c_int32()
+    _check(load().qieo_get_best(h, _ptr(bits), C.byref(f), C.byref(g), C.byref(c)))
+    return bits, int(f.value), int(g.value), int(c.value)
+
+
+def qieo_get_state(h, np_: int, ng: int):
+    k = np.zeros((np_, ng), dtype=np.int16)
+    t = C.c_int32()
+    _check(load().qieo_get_state(h, _ptr(k), C.byref(t)))
+    return k, int(t.value)
+
+
+def qieo_get_fitness(h, np_: int) -> np.ndarray:
+    f = np.zeros(np_, dtype=np.int64)
+    _check(load().qieo_get_fitness(h, _ptr(f)))
+    return f
+
+
+def qieo_get_alleles(h, np_: int, ng: int) -> np.ndarray:
+    x = np.zeros((np_, ng), dtype=np.uint8)
+    _check(load().qieo_get_alleles(h, _ptr(x)))
+    return x
+
+
+def qieo_get_elite_history(h, first: int, n: int):
+    e = np.zeros(n, dtype=np.int32)
+    f = np.zeros(n, dtype=np.int64)
+    _check(load().qieo_get_elite_history(h, int(first), int(n), _ptr(e), _ptr(f)))
+    return e, f
+
+
+def qieo_get_threshold_table(h, D: int) -> np.ndarray:
+    T = np.zeros(2 * (D // 4) + 1, dtype=np.uint64)
+    _check(load().qieo_get_threshold_table(h, _ptr(T)))
+    return T
+
+
+def qieo_get_launch_shape(h) -> qieo_launch_shape:
+    s = qieo_launch_shape()
+    _check(load().qieo_get_launch_shape(h, C.byref(s)))
+    return s
+
+
+def qieo_set_launch_shape(h, lanes_per_row: int, warps_per_row: int, rows_per_cta: int) -> None:
+    s = qieo_launch_shape(int(lanes_per_row), int(warps_per_row), int(rows_per_cta), 0, 0, 0)
+    _check(load().qieo_set_launch_shape(h, C.byref(s)))
+
+
+def qieo_get_kernel_time(h):
+    ms, n = C.c_double(), C.c_int64()
+    _check(load().qieo_get_kernel_time(h, C.byref(ms), C.byref(n)))
+    return float(ms.value), int(n.value)
+
+
+def qieo_philox(ctr_key) -> np.ndarray:
+    ck = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((ck.shape[0], 4), dtype=np.uint32)
+    _check(load().qieo_philox(_ptr(ck), _ptr(out), int(ck.shape[0])))
+    return out
+
+
+class Instance:
+    """Convenience owner of one instance handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, problem, np_: int, seed: int = 1, inst: int = 0, D: int = 100,
+                 lam: int = 1, rule: int = QIEO_RULE_R1, elite_on_host: int = 0,
+                 flags: int = 0, stream: int | None = None):
+        p = qieo_default_params()
+        p.np = int(np_)
+        p.dtheta_den = int(D)
+        p.penalty_lambda = int(lam)
+        p.seed = int(seed) & 0xFFFFFFFF
+        p.instance_id = int(inst) & 0xFFFFFFFF
+        p.rotate_rule = int(rule)
+        p.elite_on_host = int(elite_on_host)
+        p.flags = int(flags)
+        p.stream = stream
+        self.np_, self.ng, self.D = int(np_), int(problem.ng), int(D)
+        self.h = qieo_create_instance(problem.weights, problem.values, problem.capacity, p)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            qieo_destroy_instance(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, generations: int) -> None:
+        qieo_run(self.h, generations)
+
+    def reset(self) -> None:
+        qieo_reset(self.h)
+
+    def synchronize(self) -> None:
+        qieo_synchronize(self.h)
+
+    def best(self):
+        return qieo_get_best(self.h, self.ng)
+
+    def state(self):
+        return qieo_get_state(self.h, self.np_, self.ng)
+
+    def fitness(self) -> np.ndarray:
+        return qieo_get_fitness(self.h, self.np_)
+
+    def alleles(self) -> np.ndarray:
+        return qieo_get_alleles(self.h, self.np_, self.ng)
+
+    def history(self, first: int, n: int):
+        return qieo_get_elite_history(self.h, first, n)
+
+    def thresholds(self) -> np.ndarray:
+        return qieo_get_threshold_table(self.h, self.D)
+
+    def shape(self) -> qieo_launch_shape:
+        return qieo_get_launch_shape(self.h)
+
+    def set_shape(self, lanes_per_row: int, warps_per_row: int, rows_per_cta: int) -> None:
+        qieo_set_launch_shape(self.h, lanes_per_row, warps_per_row, rows_per_cta)
+
+    def kernel_time(self):
+        return qieo_get_kernel_time(self.h)

@@ -1,0 +1,102 @@
+"""The C-ABI library builds, loads and exports every entry point include/qieo.h declares,
+and the binding's structures match the header's layout (no GPU needed: nothing here
+launches a kernel)."""
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2609_30862_gb300 import build as B
+from paper_2609_30862_gb300 import qieo as Q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qieo.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qieo_[a-z_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(Q.EXPORTS)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc unavailable")
+    B.build()
+    return Q.load()
+
+
+def test_library_exports_every_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (qieo_\w+)", out))
+    for name in _declared():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_defaults_and_errors_without_gpu(lib):
+    p = Q.qieo_default_params()
+    assert (p.np, p.dtheta_den, p.penalty_lambda, p.seed, p.rotate_rule) == (64, 100, 1, 1, 0)
+    # invalid arguments are rejected on the host before any device call
+    with pytest.raises(Q.QieoError) as e:
+        Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, dtheta_den=30))
+    assert e.value.status == Q.QIEO_ERR_INVALID and "dtheta_den" in str(e.value)
+    with pytest.raises(Q.QieoError) as e:
+        Q.qieo_create_instance([1, -2], [3, 4], 2, p)
+    assert e.value.status == Q.QIEO_ERR_INVALID
+    with pytest.raises(Q.QieoError):
+        Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, np=0))
+    with pytest.raises(Q.QieoError):
+        Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, penalty_lambda=0))
+    with pytest.raises(Q.QieoError):
+        Q.qieo_create_instance([1, 2], [3, 4], -1, p)
+    with pytest.raises(Q.QieoError):
+        Q.qieo_create_instance([2**31 - 1] * 4, [1] * 4, 1, _params(p, penalty_lambda=2**32))
+    with pytest.raises(Q.QieoError) as e:
+        Q.qieo_run(None, 1)
+    assert e.value.status == Q.QIEO_ERR_INVALID
+
+
+def _params(p, **kw):
+    q = Q.qieo_params()
+    for name, _ in Q.qieo_params._fields_:
+        setattr(q, name, getattr(p, name))
+    for k, v in kw.items():
+        setattr(q, k, v)
+    return q
+
+
+_LAYOUT_PROG = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "qieo.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(qieo_problem), sizeof(qieo_params),
+         sizeof(qieo_launch_shape), offsetof(qieo_params, stream), offsetof(qieo_problem, capacity));
+  return 0;
+}
+"""
+
+
+def test_struct_layout_matches_header():
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc unavailable")
+    import ctypes as C
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "l.c")
+        open(src, "w").write(_LAYOUT_PROG)
+        exe = os.path.join(d, "l")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    want = [C.sizeof(Q.qieo_problem), C.sizeof(Q.qieo_params), C.sizeof(Q.qieo_launch_shape),
+            Q.qieo_params.stream.offset, Q.qieo_problem.capacity.offset]
+    assert got == want

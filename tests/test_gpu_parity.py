@@ -1,0 +1,179 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison is element by element: angle indices, alleles, fitness, elite index and
+fitness per generation, the best record and the threshold table must be identical (all
+are integers; the method has no floating point after the table).
+"""
+import numpy as np
+import pytest
+
+from paper_2609_30862_gb300 import qieo as Q
+from paper_2609_30862_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Q.load()
+
+
+def compare(prob, np_, chunks, seed=1, inst=0, D=100, lam=1, rule=0, flags=0, host=0,
+            shape=None, kind="serial", oracle_mod=None, check_alleles=True):
+    from oracle import oracle as O
+    gens = int(sum(chunks))
+    st = O.run(prob, np_, gens, seed=seed, inst=inst, D=D, lam=lam, rule=rule, kind=kind)
+    with Q.Instance(prob, np_, seed=seed, inst=inst, D=D, lam=lam, rule=rule,
+                    elite_on_host=host, flags=flags) as I:
+        if shape is not None:
+            I.set_shape(*shape)
+        for g in chunks:
+            I.run(g)
+        k, t = I.state()
+        assert t == gens == int(st.t[0])
+        assert np.array_equal(k, st.k), "angle indices differ"
+        e, f = I.history(0, gens)
+        assert np.array_equal(e, st.hist_e), "elite indices differ"
+        assert np.array_equal(f, st.hist_f), "elite fitness differs"
+        assert np.array_equal(I.fitness(), st.f), "fitness differs"
+        if check_alleles:
+            assert np.array_equal(I.alleles(), st.x), "alleles differ"
+        bits, bf, bg, bc = I.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in st.best)
+        assert np.array_equal(bits, st.best_x)
+        return I.shape()
+
+
+def test_threshold_table_matches_oracle():
+    from oracle import oracle as O
+    for D in (4, 12, 100, 1000, 4000):
+        with Q.Instance(W.knapsack(8, 1), 1, D=D) as I:
+            assert np.array_equal(I.thresholds(), O.threshold_table(D)), D
+
+
+def test_device_philox_matches_oracle():
+    from oracle import oracle as O
+    rng = np.random.default_rng(7)
+    ck = rng.integers(0, 2**32, size=(4096, 6), dtype=np.uint64).astype(np.uint32)
+    ck[0] = 0
+    ck[1] = 0xFFFFFFFF
+    out = Q.qieo_philox(ck)
+    for row, got in zip(ck[:512], out[:512]):
+        assert np.array_equal(got, O.philox4x32_10(row[:4], row[4:]))
+
+
+def test_c1_full_run():
+    """Ng = 100, Np = 64, 500 generations, Philox seed 1: the small named workload."""
+    c = W.WORKLOADS["c1"]
+    compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
+            inst=c["inst"])
+
+
+def test_c1_rule_r2():
+    c = W.WORKLOADS["c1"]
+    compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [300], seed=3, rule=1)
+
+
+@pytest.mark.parametrize("flags", [Q.QIEO_FLAG_NO_GRAPH, Q.QIEO_FLAG_FORCE_WIDE,
+                                   Q.QIEO_FLAG_SYNC_RUN | Q.QIEO_FLAG_TIME_KERNELS])
+def test_flags_do_not_change_results(flags):
+    compare(W.knapsack(700, 5), 48, [60], seed=5, rule=0, flags=flags)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_host_determine_elite_variant(rule):
+    compare(W.knapsack(500, 2), 40, [25, 15], seed=2, rule=rule, host=1)
+
+
+def test_split_runs():
+    compare(W.knapsack(333, 8), 37, [1, 10, 29, 7], seed=8, rule=1)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_repeated_run_length_uses_graph(rule):
+    """The second and later runs of the same length replay a captured CUDA graph."""
+    compare(W.knapsack(1200, 6), 50, [6, 6, 6, 6, 3, 6], seed=6, rule=rule)
+
+
+@pytest.mark.parametrize("ng", [1, 7, 8, 9, 31, 33, 127, 255, 257, 2048, 2055, 4099])
+@pytest.mark.parametrize("np_", [1, 3, 19])
+def test_ragged_sizes(ng, np_):
+    compare(W.knapsack(ng, ng + np_), np_, [12], seed=ng, inst=np_, rule=(ng + np_) % 2)
+
+
+@pytest.mark.parametrize("shape", [(32, 8, 1), (32, 8, 3), (32, 4, 64), (32, 2, 8), (32, 1, 40),
+                                   (16, 1, 16), (8, 1, 32), (4, 1, 64), (2, 1, 128), (1, 1, 256),
+                                   (32, 8, 1024)])
+def test_launch_shape_independence(shape):
+    """Results do not depend on the block shape: integer sums are exact and every draw is
+    keyed by (gene, chromosome, generation), not by thread."""
+    compare(W.knapsack(1500, 4), 70, [15], seed=4, shape=shape)
+
+
+def test_wide_items_and_penalty():
+    """Weights/values outside the 16-bit packed range, negative values, lambda > 1."""
+    rng = np.random.default_rng(11)
+    w = rng.integers(0, 2**31 - 1, 300).astype(np.int32)
+    v = rng.integers(-2**31, 2**31 - 1, 300).astype(np.int32)
+    prob = W.custom_problem(w, v, int(w.astype(np.int64).sum() // 3))
+    shape = compare(prob, 24, [20], seed=9, lam=7)
+    assert shape.narrow == 0
+    prob2 = W.custom_problem(rng.integers(0, 1000, 900), rng.integers(0, 1000, 900), 20000)
+    compare(prob2, 33, [20], seed=10, lam=3, rule=1)
+
+
+def test_narrow_boundary_items():
+    """Largest items the packed 16-bit path accepts (255) and zero items."""
+    ng = 4096
+    w = np.full(ng, 255, dtype=np.int32)
+    v = np.full(ng, 255, dtype=np.int32)
+    w[::7] = 0
+    prob = W.custom_problem(w, v, int(w.sum()) // 2)
+    shape = compare(prob, 9, [10], seed=12)
+    assert shape.narrow == 1
+
+
+@pytest.mark.parametrize("D", [4, 12, 1000])
+def test_other_rotation_steps(D):
+    compare(W.knapsack(150, 3), 20, [80], seed=3, D=D, rule=D % 8 // 4)
+
+
+def test_degenerate_capacity():
+    """W = 0: every non-empty pack is infeasible; all-zero weights: every pack fits."""
+    compare(W.custom_problem([1, 2, 3, 4, 5], [1, 1, 1, 1, 1], 0), 6, [30], seed=1)
+    compare(W.custom_problem([0] * 20, list(range(20)), 0), 6, [30], seed=1)
+
+
+def test_reset_and_zero_generations():
+    prob = W.knapsack(100, 1)
+    with Q.Instance(prob, 16) as I:
+        I.run(0)
+        bits, f, g, c = I.best()
+        assert (f, g, c) == (0, -1, -1)
+        k, t = I.state()
+        assert t == 0 and not k.any()
+        I.run(17)
+        I.reset()
+        k, t = I.state()
+        assert t == 0 and not k.any()
+        assert I.best()[2] == -1
+    compare(prob, 16, [17], seed=1)
+
+
+def test_c2_full_size():
+    """Ng = 10,000, Np = 1,024, 1,000 generations: bit-exact against the OpenMP build of
+    the oracle (identical to the serial one by construction and by test)."""
+    c = W.WORKLOADS["c2"]
+    compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
+            inst=c["inst"], kind="omp")
+
+
+def test_c3_full_size_first_generations():
+    """Ng = 100,000, Np = 4,096 (the HBM-resident workload) in the launch shape the
+    benchmark uses: the first 3 generations bit-exact against the OpenMP oracle."""
+    c = W.WORKLOADS["c3"]
+    compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [2, 1], seed=c["seed"],
+            inst=c["inst"], kind="omp")
