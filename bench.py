@@ -320,7 +320,7 @@ def run_gpu(a):
     # read the best record back, destroy -- every step
     e2e_times = []
     with torch.cuda.stream(stream):
-        for i in range(a.e2e_steps + 1):
+        for i in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
             barrier()
             t0 = time.perf_counter()
             h = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
@@ -334,7 +334,8 @@ def run_gpu(a):
     e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * genes_per_step * len(e2e_times) / float(e2e_t[0])
+    e2e_value = (world * genes_per_step * len(e2e_times) / float(e2e_t[0])
+                 if e2e_times else None)
     svec = (ng + 7) // 8
     h2d = svec * 8 * 4 * (1 if shape.narrow else 2) + 4 * (2 * 25 + 1)
     d2h = ((svec + 15) // 16) * 16 + 24
@@ -347,9 +348,10 @@ def run_gpu(a):
                        l2="flushed between steps (512 MB write)" if flush
                        else "state larger than L2 (no flush)",
                        parallelism="one independent instance per GPU",
-                       launch_shape="%dx%d lanes/warps per row, %d rows per block, grid %dx%d" % (
-                           shape.lanes_per_row, shape.warps_per_row, shape.rows_per_cta,
-                           shape.grid_x, shape.grid_y)),
+                       launch_shape="%d lanes x %d warps per row tile, %d tiles per row, "
+                                    "%d persistent blocks, <= %d tile-rows per block" % (
+                           shape.lanes_per_row, shape.warps_per_row, shape.tiles,
+                           shape.grid_ctas, shape.rows_per_cta)),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

@@ -67,6 +67,8 @@ typedef struct {
 #define QIEO_FLAG_SYNC_RUN      0x2   /* qieo_run waits (bounded) for the device */
 #define QIEO_FLAG_FORCE_WIDE    0x4   /* use 64-bit item sums even for small items */
 #define QIEO_FLAG_TIME_KERNELS  0x8   /* time the generation kernels with CUDA events */
+#define QIEO_FLAG_PER_GENERATION 0x10 /* one kernel launch per generation instead of one
+                                         cooperative launch per run */
 
 typedef struct {
     int32_t np;              /* chromosomes, >= 1 */
@@ -100,11 +102,20 @@ qieo_status qieo_reset(qieo_instance *inst);
 
 /* Runs `generations` >= 0 generations from the current one (Fig. 1: QIP, Evaluation,
  * DetermineElite, CIP, per generation; the CIP of the last generation is applied before
- * returning, so run(a) followed by run(b) equals run(a + b)). Stream-ordered: returns
- * after enqueueing unless QIEO_FLAG_SYNC_RUN is set or elite_on_host is 1. */
+ * returning, so run(a) followed by run(b) equals run(a + b)). By default the whole run is
+ * one cooperative kernel launch whose blocks meet at a bounded grid barrier after each
+ * generation; QIEO_FLAG_PER_GENERATION (and elite_on_host) launch one kernel per
+ * generation instead. Stream-ordered: returns after enqueueing unless QIEO_FLAG_SYNC_RUN
+ * is set or elite_on_host is 1. A barrier wait that runs out is reported as
+ * QIEO_ERR_TIMEOUT by the next call that waits for the device; the state is then
+ * undefined until qieo_reset. */
 qieo_status qieo_run(qieo_instance *inst, int32_t generations);
 
-/* Waits (bounded) until every operation enqueued for the instance has finished. */
+/* Bound of one grid-barrier wait inside a run, in nanoseconds (default 10 s; >= 1). */
+qieo_status qieo_set_wait_timeout(qieo_instance *inst, int64_t ns);
+
+/* Waits (bounded) until every operation enqueued for the instance has finished; reports
+ * a device-side wait that ran out as QIEO_ERR_TIMEOUT. */
 qieo_status qieo_synchronize(qieo_instance *inst);
 
 /* The best-so-far record (the first generation elite of largest fitness): its alleles as
@@ -131,13 +142,16 @@ qieo_status qieo_get_elite_history(qieo_instance *inst, int32_t first, int32_t n
 qieo_status qieo_get_threshold_table(qieo_instance *inst, uint64_t *t_out);
 
 /* Launch shape of the fused generation kernel. Results do not depend on it (all sums are
- * exact integers and every draw is keyed by gene, chromosome and generation). */
+ * exact integers and every draw is keyed by gene, chromosome and generation). A row is cut
+ * into tiles of lanes_per_row * warps_per_row vectors of 8 genes; a persistent grid of
+ * grid_ctas blocks splits the ntile * np tile-rows into equal contiguous shares. */
 typedef struct {
-    int32_t lanes_per_row;   /* 1, 2, 4, 8, 16 or 32 threads of a warp on one row */
+    int32_t lanes_per_row;   /* 1, 2, 4, 8, 16 or 32 threads of a warp on one row tile */
     int32_t warps_per_row;   /* 1, 2, 4 or 8 warps on one row tile (lanes_per_row 32 only) */
-    int32_t rows_per_cta;    /* chromosomes per thread block, 1 .. 1024 */
+    int32_t grid_ctas;       /* thread blocks; 0 = one per resident slot of the device */
     int32_t narrow;          /* out: 1 when 16-bit packed item sums are in use */
-    int32_t grid_x, grid_y;  /* out: gene tiles, row chunks */
+    int32_t tiles;           /* out: gene tiles per row */
+    int32_t rows_per_cta;    /* out: most tile-rows one block sums in shared memory at once */
 } qieo_launch_shape;
 
 qieo_status qieo_get_launch_shape(qieo_instance *inst, qieo_launch_shape *shape);

@@ -1,11 +1,15 @@
 // qieo_api.cu -- host side of the C ABI declared in include/qieo.h.
 //
-// An instance owns one device allocation holding the qubit state, the packed alleles, the
-// items, the elite and best rows, the row accumulators and the per-generation records.
-// qieo_run enqueues one fused generation kernel per generation (replayed from a cached
-// CUDA graph) plus one final CIP launch; with elite_on_host it instead copies the row sums
-// to the host after each generation, picks the elite there and records it with a
-// one-block kernel (the host DetermineElite variant of Sec. III-C / Sec. VII P4).
+// An instance owns one device allocation holding the qubit state, the two allele planes,
+// the items (packed and wide form), the best row, the row accumulators and counters, the
+// elite key and index, the grid-barrier words and the per-generation records. qieo_run
+// launches the whole run as one cooperative kernel (blocks meet at a bounded grid barrier
+// after each generation). The per-generation path enqueues one fused generation kernel per
+// generation plus one final CIP launch, chained with programmatic dependent launch (each
+// kernel's prologue overlaps the previous kernel's tail) and replayed from a cached CUDA
+// graph when a run length repeats. With elite_on_host it copies the fitness array to the
+// host after each generation, picks the elite there and records it with a one-block
+// kernel (the host DetermineElite variant the paper recommends, Sec. III-C, Sec. VII P4).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,8 +54,9 @@ qieo_status fail(qieo_status st, const char *fmt, ...)
                         __LINE__);                                                         \
     } while (0)
 
-constexpr int32_t kMaxD = 4000;
+constexpr int32_t kMaxD = 4 * qieo::kMaxK;
 constexpr double kWaitSeconds = 600.0;
+constexpr uint64_t kDefaultBarrierWaitNs = 10ull * 1000 * 1000 * 1000;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -66,17 +71,22 @@ int pow2_ceil(int x)
 
 struct qieo_instance {
     int32_t np = 0, ng = 0, svec = 0, xstride = 0, K = 0, D = 0;
-    int32_t rule = 0, host_de = 0, flags = 0, narrow = 0;
+    int32_t rule = 0, host_de = 0, flags = 0;
     int64_t capacity = 0, lambda = 1;
     uint32_t seed = 0, inst_id = 0;
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
 
+    // problem bounds that decide the sum and elite-key modes
+    bool narrow_items = false;     // 0 <= w, v <= 255
+    int64_t sum_w = 0, sum_v = 0, sum_absv = 0;
+    bool key_ok = false;
+
     // device memory
     void *block = nullptr;
-    size_t block_bytes = 0;
     qieo::GenParams gp{};
+    const uint4 *items_narrow = nullptr;
     int32_t *hist_e = nullptr;
     int64_t *hist_f = nullptr;
     int32_t hist_cap = 0;
@@ -85,8 +95,9 @@ struct qieo_instance {
     int32_t t = 0;
 
     // launch shape
-    int32_t lanes = 32, warps = 8, rows_per_cta = 1, grid_x = 1, grid_y = 1;
+    int32_t lanes = 32, warps = 8, grid = 1, grid_override = 0, narrow = 0;
     size_t smem = 0;
+    bool coop = false;             // the run fits one cooperative launch
 
     // CUDA graphs keyed by the number of generations of a run; a graph is captured the
     // second time a run length is seen (a one-off run is cheaper to launch directly)
@@ -99,7 +110,7 @@ struct qieo_instance {
     int64_t kernel_launches = 0;
 
     // host DetermineElite
-    unsigned long long *h_acc = nullptr;
+    int64_t *h_fit = nullptr;
 };
 
 namespace {
@@ -110,7 +121,76 @@ void drop_graphs(qieo_instance *q)
     q->graphs.clear();
 }
 
-void choose_shape(qieo_instance *q)
+template <bool N, int R>
+const void *gen_kernel_ptr()
+{
+    return reinterpret_cast<const void *>(&qieo::generation_kernel<N, R>);
+}
+
+const void *gen_kernel_of(const qieo_instance *q)
+{
+    if (q->narrow) return q->rule ? gen_kernel_ptr<true, 1>() : gen_kernel_ptr<true, 0>();
+    return q->rule ? gen_kernel_ptr<false, 1>() : gen_kernel_ptr<false, 0>();
+}
+
+template <bool N, int R>
+const void *run_kernel_ptr()
+{
+    return reinterpret_cast<const void *>(&qieo::run_kernel<N, R>);
+}
+
+const void *run_kernel_of(const qieo_instance *q)
+{
+    if (q->narrow) return q->rule ? run_kernel_ptr<true, 1>() : run_kernel_ptr<true, 0>();
+    return q->rule ? run_kernel_ptr<false, 1>() : run_kernel_ptr<false, 0>();
+}
+
+// Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
+// fills the launch fields of gp.
+qieo_status configure(qieo_instance *q)
+{
+    const int tile = q->lanes * q->warps;
+    const int rpp = qieo::kThreads / tile;
+    const int ntile = (q->svec + tile - 1) / tile;
+    // 16-bit packed sums inside a warp need items <= 255 (256 genes * 255 < 2^16); the
+    // packed row word needs row sums < 2^28 and at most 255 tiles per row.
+    q->narrow = (!(q->flags & QIEO_FLAG_FORCE_WIDE) && q->narrow_items &&
+                 q->sum_w < (1ll << 28) && q->sum_v < (1ll << 28) && ntile <= 255) ? 1 : 0;
+    const int64_t units = (int64_t)ntile * q->np;
+    const size_t row_bytes = q->narrow ? 8 : 16;
+
+    // Blocks resident at once, for the larger of the shared-memory sizes used.
+    const size_t smem0 = (size_t)qieo::kMaxSegRows * row_bytes;
+    int bps_gen = 0, bps_run = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_gen, gen_kernel_of(q),
+                                                           qieo::kThreads, smem0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_run, run_kernel_of(q),
+                                                           qieo::kThreads, smem0));
+    const int64_t resident = (int64_t)q->sm_count * std::max(1, std::min(bps_gen, bps_run));
+    int grid = q->grid_override;
+    if (grid <= 0) {
+        const int64_t by_work = (units + rpp - 1) / rpp;
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, by_work));
+    }
+    const int64_t share = (units + grid - 1) / grid;
+    const int seg_max = (int)std::max<int64_t>(1, std::min<int64_t>(qieo::kMaxSegRows, share));
+    q->grid = grid;
+    q->smem = (size_t)seg_max * row_bytes;
+    q->coop = bps_run > 0 && grid <= (int64_t)q->sm_count * bps_run;
+
+    qieo::GenParams &g = q->gp;
+    g.items_narrow = q->items_narrow;
+    g.ntile = ntile;
+    g.units = units;
+    g.lanes = q->lanes;
+    g.warps = q->warps;
+    g.seg_rows_max = seg_max;
+    g.key_mode = q->key_ok ? 1 : 0;
+    drop_graphs(q);
+    return QIEO_OK;
+}
+
+void default_tile(qieo_instance *q)
 {
     const int svec = q->svec;
     if (svec <= 16) {
@@ -120,62 +200,72 @@ void choose_shape(qieo_instance *q)
         q->lanes = 32;
         q->warps = std::min(8, pow2_ceil((svec + 31) / 32));
     }
-    const int tile = q->lanes * q->warps;
-    const int rpp = qieo::kThreads / tile;
-    q->grid_x = (svec + tile - 1) / tile;
-    const long target = 4L * std::max(q->sm_count, 1);
-    long rows = ((long)q->np * q->grid_x + target - 1) / target;
-    rows = std::max<long>(rows, 1);
-    rows = (rows + rpp - 1) / rpp * rpp;
-    rows = std::min<long>(rows, 1024 / rpp * rpp);
-    const long np_r = ((long)q->np + rpp - 1) / rpp * rpp;
-    rows = std::min(rows, np_r);
-    q->rows_per_cta = (int32_t)rows;
-    q->grid_y = (q->np + q->rows_per_cta - 1) / q->rows_per_cta;
 }
 
-size_t shared_bytes(const qieo_instance *q)
+cudaLaunchConfig_t launch_config(const qieo_instance *q, dim3 grid, size_t smem,
+                                 cudaLaunchAttribute *attr)
 {
-    const size_t thr = align_up((size_t)(2 * q->K + 1) * 4, 16);
-    return thr + (size_t)q->rows_per_cta * 2 * (q->narrow ? 4 : 8);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(qieo::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = q->stream;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
 template <bool N, int R>
-cudaError_t launch_gen_t(const qieo_instance *q, int apply_cip, int do_de)
+cudaError_t launch_gen_t(const qieo_instance *q, const qieo::GenParams &p)
 {
-    qieo::GenParams p = q->gp;
-    p.apply_cip = apply_cip;
-    p.do_de = do_de;
-    p.lanes = q->lanes;
-    p.warps = q->warps;
-    p.rows_per_cta = q->rows_per_cta;
-    qieo::generation_kernel<N, R>
-        <<<dim3(q->grid_x, q->grid_y), qieo::kThreads, q->smem, q->stream>>>(p);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = launch_config(q, dim3(q->grid), q->smem, attr);
+    return cudaLaunchKernelEx(&cfg, qieo::generation_kernel<N, R>, p);
 }
 
 cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de)
 {
-    if (q->narrow) {
-        return q->rule ? launch_gen_t<true, 1>(q, apply_cip, do_de)
-                       : launch_gen_t<true, 0>(q, apply_cip, do_de);
-    }
-    return q->rule ? launch_gen_t<false, 1>(q, apply_cip, do_de)
-                   : launch_gen_t<false, 0>(q, apply_cip, do_de);
+    qieo::GenParams p = q->gp;
+    p.apply_cip = apply_cip;
+    p.do_de = do_de;
+    if (q->narrow) return q->rule ? launch_gen_t<true, 1>(q, p) : launch_gen_t<true, 0>(q, p);
+    return q->rule ? launch_gen_t<false, 1>(q, p) : launch_gen_t<false, 0>(q, p);
+}
+
+template <bool N, int R>
+cudaError_t launch_run_t(const qieo_instance *q, int32_t G)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q->grid);
+    cfg.blockDim = dim3(qieo::kThreads);
+    cfg.dynamicSmemBytes = q->smem;
+    cfg.stream = q->stream;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, qieo::run_kernel<N, R>, q->gp, G);
+}
+
+cudaError_t launch_run(const qieo_instance *q, int32_t G)
+{
+    if (q->narrow) return q->rule ? launch_run_t<true, 1>(q, G) : launch_run_t<true, 0>(q, G);
+    return q->rule ? launch_run_t<false, 1>(q, G) : launch_run_t<false, 0>(q, G);
 }
 
 cudaError_t launch_final_cip(const qieo_instance *q)
 {
     const size_t total = (size_t)q->np * q->svec;
-    const int blocks = (int)std::min<size_t>((total + qieo::kThreads - 1) / qieo::kThreads,
-                                             (size_t)std::max(q->sm_count, 1) * 8);
-    if (q->rule)
-        qieo::cip_kernel<1><<<blocks, qieo::kThreads, 0, q->stream>>>(
-            q->gp.state, q->gp.xbits, q->gp.elite, q->np, q->svec, q->xstride, q->K);
-    else
-        qieo::cip_kernel<0><<<blocks, qieo::kThreads, 0, q->stream>>>(
-            q->gp.state, q->gp.xbits, q->gp.elite, q->np, q->svec, q->xstride, q->K);
-    return cudaGetLastError();
+    const int blocks = (int)std::max<size_t>(
+        1, std::min<size_t>((total + qieo::kThreads - 1) / qieo::kThreads,
+                            (size_t)std::max(q->sm_count, 1) * 8));
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = launch_config(q, dim3(blocks), 0, attr);
+    if (q->rule) return cudaLaunchKernelEx(&cfg, qieo::cip_kernel<1>, q->gp);
+    return cudaLaunchKernelEx(&cfg, qieo::cip_kernel<0>, q->gp);
 }
 
 qieo_status wait_stream(cudaStream_t s)
@@ -251,8 +341,26 @@ qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
     return QIEO_OK;
 }
 
+qieo_status run_cooperative(qieo_instance *q, int32_t G)
+{
+    const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
+    if (timing) CUDA_TRY(cudaEventRecord(q->ev0, q->stream));
+    CUDA_TRY(launch_run(q, G));
+    if (timing) {
+        CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
+        qieo_status st = wait_stream(q->stream);
+        if (st != QIEO_OK) return st;
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, q->ev0, q->ev1));
+        q->kernel_ms += ms;
+        q->kernel_launches += 1;
+    }
+    return QIEO_OK;
+}
+
 qieo_status run_device(qieo_instance *q, int32_t G)
 {
+    if (q->coop && !(q->flags & QIEO_FLAG_PER_GENERATION)) return run_cooperative(q, G);
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
     if ((q->flags & QIEO_FLAG_NO_GRAPH) || (first_time && !q->graphs.count(G))) {
@@ -292,43 +400,37 @@ qieo_status run_device(qieo_instance *q, int32_t G)
     return QIEO_OK;
 }
 
-template <bool N>
-cudaError_t launch_record(const qieo_instance *q, int32_t e)
-{
-    qieo::record_elite_kernel<N><<<1, qieo::kThreads, 0, q->stream>>>(q->gp, e);
-    return cudaGetLastError();
-}
-
 qieo_status run_host_de(qieo_instance *q, int32_t G)
 {
-    const size_t nacc = (size_t)q->np * (q->narrow ? 1 : 2);
     for (int32_t g = 0; g < G; ++g) {
         CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 0));
-        CUDA_TRY(cudaMemcpyAsync(q->h_acc, q->gp.acc, nacc * sizeof(unsigned long long),
+        CUDA_TRY(cudaMemcpyAsync(q->h_fit, q->gp.fitness, (size_t)q->np * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, q->stream));
         qieo_status st = wait_stream(q->stream);
         if (st != QIEO_OK) return st;
         int32_t e = 0;
-        int64_t bf = INT64_MIN;
-        for (int32_t c = 0; c < q->np; ++c) {
-            int64_t sw, sv;
-            if (q->narrow) {
-                sw = (int64_t)(q->h_acc[c] & 0xffffffffull);
-                sv = (int64_t)(q->h_acc[c] >> 32);
-            } else {
-                sw = (int64_t)q->h_acc[2 * (size_t)c];
-                sv = (int64_t)q->h_acc[2 * (size_t)c + 1];
-            }
-            const int64_t f = sw <= q->capacity ? sv : -q->lambda * (sw - q->capacity);
-            if (f > bf) {
-                bf = f;
-                e = c;
-            }
-        }
-        CUDA_TRY(q->narrow ? launch_record<true>(q, e) : launch_record<false>(q, e));
+        for (int32_t c = 1; c < q->np; ++c)
+            if (q->h_fit[c] > q->h_fit[e]) e = c;
+        qieo::record_elite_kernel<<<1, qieo::kThreads, 0, q->stream>>>(q->gp, e);
+        CUDA_TRY(cudaGetLastError());
     }
     CUDA_TRY(launch_final_cip(q));
     return wait_stream(q->stream);
+}
+
+// Waits for the instance's stream and reports a device-side wait that ran out.
+qieo_status wait_checked(qieo_instance *q)
+{
+    qieo_status st = wait_stream(q->stream);
+    if (st != QIEO_OK) return st;
+    int32_t err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, q->gp.error, sizeof err, cudaMemcpyDeviceToHost, q->stream));
+    st = wait_stream(q->stream);
+    if (st != QIEO_OK) return st;
+    if (err & qieo::kErrBarrierTimeout)
+        return fail(QIEO_ERR_TIMEOUT, "a grid-barrier wait inside the run ran out (%.3f s bound); "
+                    "the instance state is undefined until qieo_reset", (double)q->gp.wait_ns * 1e-9);
+    return QIEO_OK;
 }
 
 qieo_status check_inst(const qieo_instance *q)
@@ -382,11 +484,12 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
         return fail(QIEO_ERR_INVALID, "elite_on_host must be 0 or 1");
     if (pr->capacity < 0) return fail(QIEO_ERR_INVALID, "capacity must be >= 0");
 
-    int64_t sum_w = 0, sum_absv = 0;
+    int64_t sum_w = 0, sum_v = 0, sum_absv = 0;
     int32_t max_w = 0, max_v = 0, min_v = 0;
     for (int32_t j = 0; j < pr->ng; ++j) {
         if (pr->weights[j] < 0) return fail(QIEO_ERR_INVALID, "weight %d is negative", j);
         sum_w += pr->weights[j];
+        sum_v += pr->values[j];
         sum_absv += std::llabs((long long)pr->values[j]);
         max_w = std::max(max_w, pr->weights[j]);
         max_v = std::max(max_v, pr->values[j]);
@@ -411,10 +514,13 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
     q->lambda = pa->penalty_lambda;
     q->seed = pa->seed;
     q->inst_id = pa->instance_id;
-    // 16-bit packed sums: a warp sums at most 256 genes, 256 * 255 < 2^16; a row at most
-    // 2^24 genes, 2^24 * 255 < 2^32.
-    q->narrow = (!(pa->flags & QIEO_FLAG_FORCE_WIDE) && max_w <= 255 && max_v <= 255 &&
-                 min_v >= 0 && pr->ng <= (1 << 24)) ? 1 : 0;
+    q->narrow_items = max_w <= 255 && max_v <= 255 && min_v >= 0;
+    q->sum_w = sum_w;
+    q->sum_v = sum_v;
+    q->sum_absv = sum_absv;
+    // elite key: fitness in [-lambda sum(w), sum(|v|)] must fit 40 bits, index 24 bits
+    q->key_ok = sum_w < (((int64_t)1 << 39) / pa->penalty_lambda) &&
+                sum_absv < ((int64_t)1 << 39) && q->np <= (1 << 24);
 
     auto bail = [&](qieo_status st) {
         qieo_destroy_instance(q);
@@ -436,20 +542,30 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
     if (ce == cudaSuccess) ce = cudaEventCreate(&q->ev1);
     if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "events: %s", cudaGetErrorString(ce)));
 
-    // One device block: state | xbits | items | elite | best_row | acc | fitness | best |
-    // gen | ticket | thresholds, each 256-byte aligned.
-    const size_t n_state = (size_t)q->np * q->svec * sizeof(uint4);
-    const size_t n_x = (size_t)q->np * q->xstride;
-    const size_t n_items = q->narrow ? (size_t)q->svec * 8 * 4 : (size_t)q->svec * 8 * 4 * 2;
-    const size_t n_row = (size_t)q->xstride;
-    const size_t n_acc = (size_t)q->np * 2 * sizeof(unsigned long long);
-    const size_t n_fit = (size_t)q->np * sizeof(int64_t);
-    const size_t n_thr = (size_t)(2 * q->K + 1) * sizeof(uint32_t);
-    size_t off[11];
-    size_t sizes[11] = {n_state, n_x, n_items, n_row, n_row, n_acc, n_fit, 3 * sizeof(int64_t),
-                        sizeof(int32_t), sizeof(unsigned int), n_thr};
+    // One device block, every part 256-byte aligned:
+    //  0 state | 1 xbits (2 planes) | 2 packed items | 3 wide items | 4 best row | 5 acc |
+    //  6 cnt | 7 fitness | 8 best[3] | 9 gen | 10 ticket | 11 key | 12 elite idx | 13 thr |
+    //  14 barrier generation | 15 error word
+    const size_t ngp = (size_t)q->svec * 8;
+    const size_t sizes[16] = {(size_t)q->np * q->svec * sizeof(uint4),
+                              2 * (size_t)q->np * q->xstride,
+                              ngp * 4,
+                              ngp * 8,
+                              (size_t)q->xstride,
+                              (size_t)q->np * 2 * sizeof(unsigned long long),
+                              (size_t)q->np * sizeof(unsigned int),
+                              (size_t)q->np * sizeof(int64_t),
+                              3 * sizeof(int64_t),
+                              sizeof(int32_t),
+                              sizeof(unsigned int),
+                              sizeof(unsigned long long),
+                              sizeof(int32_t),
+                              (size_t)(2 * q->K + 1) * sizeof(uint32_t),
+                              sizeof(int32_t),
+                              sizeof(int32_t)};
+    size_t off[16];
     size_t total = 0;
-    for (int i = 0; i < 11; ++i) {
+    for (int i = 0; i < 16; ++i) {
         off[i] = total;
         total = align_up(total + sizes[i], 256);
     }
@@ -457,62 +573,66 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
     if (ce != cudaSuccess)
         return bail(fail(ce == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA,
                          "device allocation of %zu bytes: %s", total, cudaGetErrorString(ce)));
-    q->block_bytes = total;
     char *b = (char *)q->block;
     qieo::GenParams &g = q->gp;
     g.state = (uint4 *)(b + off[0]);
     g.xbits = (uint8_t *)(b + off[1]);
-    g.elite = (uint8_t *)(b + off[3]);
+    q->items_narrow = (const uint4 *)(b + off[2]);
+    g.w4 = (const int4 *)(b + off[3]);
+    g.v4 = (const int4 *)(b + off[3] + ngp * 4);
     g.best_row = (uint8_t *)(b + off[4]);
     g.acc = (unsigned long long *)(b + off[5]);
-    g.fitness = (int64_t *)(b + off[6]);
-    g.best = (int64_t *)(b + off[7]);
-    g.gen = (int32_t *)(b + off[8]);
-    g.ticket = (unsigned int *)(b + off[9]);
-    g.thr = (const uint32_t *)(b + off[10]);
+    g.cnt = (unsigned int *)(b + off[6]);
+    g.fitness = (int64_t *)(b + off[7]);
+    g.best = (int64_t *)(b + off[8]);
+    g.gen = (int32_t *)(b + off[9]);
+    g.ticket = (unsigned int *)(b + off[10]);
+    g.key = (unsigned long long *)(b + off[11]);
+    g.elite_idx = (int32_t *)(b + off[12]);
+    g.thr = (const uint32_t *)(b + off[13]);
+    g.bar_gen = (int32_t *)(b + off[14]);
+    g.error = (int32_t *)(b + off[15]);
+    g.wait_ns = kDefaultBarrierWaitNs;
     g.np = q->np;
     g.svec = q->svec;
     g.xstride = q->xstride;
+    g.xplane = (size_t)q->np * q->xstride;
     g.K = q->K;
     g.capacity = q->capacity;
     g.lambda = q->lambda;
-    g.key0 = q->seed;
-    g.key1 = q->inst_id;
-
-    // Items, padded with zeros to whole vectors (padding genes add nothing).
-    const size_t ngp = (size_t)q->svec * 8;
-    std::vector<uint32_t> items(q->narrow ? ngp : 2 * ngp, 0u);
-    for (int32_t j = 0; j < q->ng; ++j) {
-        if (q->narrow) {
-            items[(size_t)j] = ((uint32_t)pr->values[j] << 16) | (uint32_t)pr->weights[j];
-        } else {
-            items[(size_t)j] = (uint32_t)pr->weights[j];
-            items[ngp + (size_t)j] = (uint32_t)pr->values[j];
-        }
+    for (int r = 0; r < 10; ++r) {   // Philox key schedule: key + r * (Weyl increments)
+        g.rk0[r] = q->seed + (uint32_t)r * qieo::kPhiloxW0;
+        g.rk1[r] = q->inst_id + (uint32_t)r * qieo::kPhiloxW1;
     }
-    if (q->narrow) {
-        g.items_narrow = (const uint4 *)(b + off[2]);
-    } else {
-        g.w4 = (const int4 *)(b + off[2]);
-        g.v4 = (const int4 *)(b + off[2] + ngp * 4);
+
+    // Items in both layouts, padded with zeros to whole vectors (padding adds nothing).
+    std::vector<uint32_t> packed(ngp, 0u), wide(2 * ngp, 0u);
+    for (int32_t j = 0; j < q->ng; ++j) {
+        if (q->narrow_items)
+            packed[(size_t)j] = ((uint32_t)pr->values[j] << 16) | (uint32_t)pr->weights[j];
+        wide[(size_t)j] = (uint32_t)pr->weights[j];
+        wide[ngp + (size_t)j] = (uint32_t)pr->values[j];
     }
     std::vector<uint64_t> T;
     build_thresholds(q->D, T);
     std::vector<uint32_t> T32(T.size());
     for (size_t i = 0; i < T.size(); ++i) T32[i] = (uint32_t)(T[i] & 0xffffffffull);
 
-    ce = cudaMemcpyAsync(b + off[2], items.data(), items.size() * 4, cudaMemcpyHostToDevice, q->stream);
+    ce = cudaMemcpyAsync(b + off[2], packed.data(), packed.size() * 4, cudaMemcpyHostToDevice, q->stream);
     if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(b + off[10], T32.data(), T32.size() * 4, cudaMemcpyHostToDevice, q->stream);
+        ce = cudaMemcpyAsync(b + off[3], wide.data(), wide.size() * 4, cudaMemcpyHostToDevice, q->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(b + off[13], T32.data(), T32.size() * 4, cudaMemcpyHostToDevice, q->stream);
     if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "upload: %s", cudaGetErrorString(ce)));
 
     if (q->host_de) {
-        ce = cudaMallocHost(&q->h_acc, (size_t)q->np * 2 * sizeof(unsigned long long));
+        ce = cudaMallocHost(&q->h_fit, (size_t)q->np * sizeof(int64_t));
         if (ce != cudaSuccess) return bail(fail(QIEO_ERR_OOM, "pinned host buffer: %s", cudaGetErrorString(ce)));
     }
-    choose_shape(q);
-    q->smem = shared_bytes(q);
-    qieo_status st = ensure_history(q, 1024);
+    default_tile(q);
+    qieo_status st = configure(q);
+    if (st != QIEO_OK) return bail(st);
+    st = ensure_history(q, 1024);
     if (st != QIEO_OK) return bail(st);
     st = qieo_reset(q);
     if (st != QIEO_OK) return bail(st);
@@ -531,7 +651,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->block) cudaFree(q->block);
     if (q->hist_e) cudaFree(q->hist_e);
     if (q->hist_f) cudaFree(q->hist_f);
-    if (q->h_acc) cudaFreeHost(q->h_acc);
+    if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
     if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
@@ -546,9 +666,10 @@ qieo_status qieo_reset(qieo_instance *q)
     st = set_device(q);
     if (st != QIEO_OK) return st;
     const size_t words = (size_t)q->np * q->svec * 4;
-    const size_t xbytes = (size_t)q->np * q->xstride;
+    const size_t xbytes = 2 * (size_t)q->np * q->xstride;
     const int blocks = std::max(1, std::min(q->sm_count * 4, (int)((words + 255) / 256)));
-    qieo::init_kernel<<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, words, xbytes);
+    qieo::init_kernel<<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, words, xbytes,
+                                                               (size_t)q->np * 2);
     CUDA_TRY(cudaGetLastError());
     q->t = 0;
     if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
@@ -569,7 +690,17 @@ qieo_status qieo_run(qieo_instance *q, int32_t G)
     st = q->host_de ? run_host_de(q, G) : run_device(q, G);
     if (st != QIEO_OK) return st;
     q->t += G;
-    if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
+    if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_checked(q);
+    return QIEO_OK;
+}
+
+qieo_status qieo_set_wait_timeout(qieo_instance *q, int64_t ns)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (ns < 1) return fail(QIEO_ERR_INVALID, "wait timeout must be >= 1 ns");
+    q->gp.wait_ns = (uint64_t)ns;
+    drop_graphs(q);
     return QIEO_OK;
 }
 
@@ -579,13 +710,15 @@ qieo_status qieo_synchronize(qieo_instance *q)
     if (st != QIEO_OK) return st;
     st = set_device(q);
     if (st != QIEO_OK) return st;
-    return wait_stream(q->stream);
+    return wait_checked(q);
 }
 
 namespace {
 
 qieo_status fetch(qieo_instance *q, void *dst, const void *src, size_t bytes)
 {
+    qieo_status st = wait_checked(q);
+    if (st != QIEO_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, q->stream));
     return wait_stream(q->stream);
 }
@@ -632,7 +765,7 @@ qieo_status qieo_get_state(qieo_instance *q, int16_t *k_out, int32_t *t_out)
         for (int32_t c = 0; c < q->np; ++c)
             for (int32_t j = 0; j < q->ng; ++j)
                 k_out[(size_t)c * q->ng + j] =
-                    (int16_t)((int32_t)s[(size_t)c * q->svec * 8 + j] - q->K);
+                    (int16_t)((int32_t)(s[(size_t)c * q->svec * 8 + j] >> 2) - q->K);
     }
     if (t_out) {
         int32_t t = 0;
@@ -661,7 +794,8 @@ qieo_status qieo_get_alleles(qieo_instance *q, uint8_t *x_out)
     st = set_device(q);
     if (st != QIEO_OK) return st;
     std::vector<uint8_t> x((size_t)q->np * q->xstride);
-    st = fetch(q, x.data(), q->gp.xbits, x.size());
+    const uint8_t *plane = q->gp.xbits + (size_t)((q->t + 1) & 1) * q->gp.xplane;
+    st = fetch(q, x.data(), plane, x.size());
     if (st != QIEO_OK) return st;
     for (int32_t c = 0; c < q->np; ++c)
         unpack_row(x.data() + (size_t)c * q->xstride, q->ng, x_out + (size_t)c * q->ng);
@@ -711,10 +845,10 @@ qieo_status qieo_get_launch_shape(qieo_instance *q, qieo_launch_shape *s)
     if (!s) return fail(QIEO_ERR_INVALID, "shape is NULL");
     s->lanes_per_row = q->lanes;
     s->warps_per_row = q->warps;
-    s->rows_per_cta = q->rows_per_cta;
+    s->grid_ctas = q->grid;
     s->narrow = q->narrow;
-    s->grid_x = q->grid_x;
-    s->grid_y = q->grid_y;
+    s->tiles = q->gp.ntile;
+    s->rows_per_cta = q->gp.seg_rows_max;
     return QIEO_OK;
 }
 
@@ -723,22 +857,19 @@ qieo_status qieo_set_launch_shape(qieo_instance *q, const qieo_launch_shape *s)
     qieo_status st = check_inst(q);
     if (st != QIEO_OK) return st;
     if (!s) return fail(QIEO_ERR_INVALID, "shape is NULL");
-    const int L = s->lanes_per_row, W = s->warps_per_row, R = s->rows_per_cta;
+    const int L = s->lanes_per_row, W = s->warps_per_row;
     if (L < 1 || L > 32 || (L & (L - 1)))
         return fail(QIEO_ERR_INVALID, "lanes_per_row must be a power of two in [1, 32]");
     if (W < 1 || W > 8 || (W & (W - 1)) || (W > 1 && L != 32))
         return fail(QIEO_ERR_INVALID, "warps_per_row must be 1, 2, 4 or 8 (>1 needs 32 lanes)");
-    const int rpp = qieo::kThreads / (L * W);
-    if (R < 1 || R > 1024 || R % rpp != 0)
-        return fail(QIEO_ERR_INVALID, "rows_per_cta must be a multiple of %d in [1, 1024]", rpp);
+    if (s->grid_ctas < 0 || s->grid_ctas > (1 << 20))
+        return fail(QIEO_ERR_INVALID, "grid_ctas must be in [0, 2^20]");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
     q->lanes = L;
     q->warps = W;
-    q->rows_per_cta = R;
-    q->grid_x = (q->svec + L * W - 1) / (L * W);
-    q->grid_y = (q->np + R - 1) / R;
-    q->smem = shared_bytes(q);
-    drop_graphs(q);
-    return QIEO_OK;
+    q->grid_override = s->grid_ctas;
+    return configure(q);
 }
 
 qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches)

@@ -1,19 +1,35 @@
 // qieo_kernels.cuh -- device code of the GB300 QIEO library.
 //
-// One fused kernel per generation (Sec. III-B, Fig. 1 of arxiv 2609.30862):
+// One generation (Sec. III-B, Fig. 1 of arxiv 2609.30862) is one fused pass over the qubit
+// grid:
 //   CIP(t-1)  rotate every qubit one step toward the previous elite's allele,
 //   QIP(t)    observe every qubit against a Philox draw,
 //   FE(t)     eq. (1) weight/value sums per chromosome (segmented reduction over genes),
-//   DE(t)     the last thread block to finish picks the generation-best chromosome.
+//   DE(t)     the block that completes a chromosome's sums evaluates eq. (1) and folds
+//             (fitness, -index) into one 64-bit atomic maximum; the last block to finish
+//             the generation turns that maximum into the elite and the records.
 // The CIP of generation t is applied at the top of generation t+1 because the elite is a
-// grid-wide result; qieo_run applies the CIP of its last generation with cip_kernel.
+// grid-wide result, and once more after the last generation of a run.
+//
+// Two drivers of the same generation body:
+//   run_kernel         one cooperative launch per run: all generations, a bounded grid
+//                      barrier between them, and the final CIP (default path);
+//   generation_kernel  one launch per generation (host DetermineElite variant, and runs
+//                      that cannot be launched cooperatively), with cip_kernel at the end.
 //
 // Data layout in device memory (row c = chromosome c, gene-fastest, Sec. V-D):
-//   state  uint16 n = k + K in [0, 2K], rows padded to a multiple of 8 genes; one uint4
-//          ("vector") holds 8 genes, and a uint32 lane of it holds 2 genes (pair).
-//   xbits  one byte per vector: bit i = allele of gene 8v + i; rows padded to 16 bytes.
+//   state  uint16 4n, n = k + K in [0, 2K] (scaled by 4 so that it is the byte offset of
+//          T[n] in the shared threshold table); rows padded to 8 genes; one uint4
+//          ("vector") = 8 genes.
+//   xbits  [2][np][xstride]: alleles of generation t in plane t & 1; bit i of byte v is
+//          gene 8v + i; rows padded to 16 bytes.
 //   items  narrow: uint32 (v << 16 | w) per gene; wide: int32 w[], int32 v[].
-//   acc    narrow: uint64 (SV << 32 | SW) per row; wide: int64 SW, SV per row.
+//   acc    narrow: uint64 (count << 56 | SV << 28 | SW) per row; wide: int64 SW, SV per row
+//          plus a uint32 count per row.
+//
+// Work split: a generation is ntile * np tile-rows (tile = lanes*warps vectors of one row).
+// Each block of the grid owns a contiguous, equal share of them in tile-major order, so it
+// reloads items only at a tile change and keeps the same share in every generation.
 #pragma once
 
 #include <cstdint>
@@ -22,11 +38,14 @@
 namespace qieo {
 
 constexpr int kThreads = 256;
+constexpr int kMaxSegRows = 2048;          // tile-rows summed in shared memory at once
+constexpr int kMaxK = 1000;                // D <= 4000
+constexpr int kMaxThr = 2 * kMaxK + 1;
 
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC 2011). One round maps (c0, c1, c2, c3)
 // to (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key advances by
-// the Weyl increments between rounds. The 32x32->64 products map to one wide multiply.
+// the Weyl increments between rounds.
 // ---------------------------------------------------------------------------------------
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
 constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
@@ -56,115 +75,232 @@ __device__ __forceinline__ Draw4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     return {c0, c1, c2, c3};
 }
 
+// The same rounds with the ten round keys precomputed (kernel parameters, so each xor
+// takes its key straight from the constant bank).
+__device__ __forceinline__ Draw4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                  uint32_t c3, const uint32_t (&rk0)[10],
+                                                  const uint32_t (&rk1)[10])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)c0;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+    }
+    return {c0, c1, c2, c3};
+}
+
 // ---------------------------------------------------------------------------------------
-// CIP on a pair of biased angle indices held in one uint32 (gene 2i low, 2i+1 high).
-// d per half: 2 = step toward allele 1, 0 = step toward allele 0, 1 = no move.
-// n' = min(max(n + d, 1) - 1, 2K): saturates theta at 0 and pi/2 (the bounds of the
-// angle index). No half can carry into the other: n + d <= 2K + 2 < 2^16.
+// CIP on a pair of scaled angle indices (4n) held in one uint32 (gene 2i low, 2i+1 high).
+// d per half: 8 = step toward allele 1, 0 = step toward allele 0, 4 = no move.
+// 4n' = min(max(4n + d, 4) - 4, 8K): saturates theta at 0 and pi/2 (the bounds of the
+// angle index). No half can carry into the other: 4n + d <= 8K + 8 < 2^16.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t delta_pair(uint32_t e2, uint32_t m2)
 {
     // e2: elite alleles of the two genes (bit 0, bit 1); m2: which of them move.
-    const uint32_t lo = 1u - (m2 & 1u) + ((m2 & e2 & 1u) << 1);
-    const uint32_t hi = 1u - ((m2 >> 1) & 1u) + ((((m2 & e2) >> 1) & 1u) << 1);
+    const uint32_t lo = 4u - ((m2 & 1u) << 2) + ((m2 & e2 & 1u) << 3);
+    const uint32_t hi = 4u - (((m2 >> 1) & 1u) << 2) + ((((m2 & e2) >> 1) & 1u) << 3);
     return lo | (hi << 16);
 }
 
-__device__ __forceinline__ uint32_t rotate_pair(uint32_t s, uint32_t d, uint32_t kk2)
+__device__ __forceinline__ uint32_t rotate_pair(uint32_t s, uint32_t d, uint32_t k8)
 {
-    return __vminu2(__vmaxu2(s + d, 0x00010001u) - 0x00010001u, kk2);
+    return __vminu2(__vmaxu2(s + d, 0x00040004u) - 0x00040004u, k8);
 }
 
-__device__ __forceinline__ uint4 rotate_vec(uint4 s, uint32_t e8, uint32_t m8, uint32_t kk2)
+__device__ __forceinline__ uint4 rotate_vec(uint4 s, uint32_t e8, uint32_t m8, uint32_t k8)
 {
-    s.x = rotate_pair(s.x, delta_pair(e8 & 3u, m8 & 3u), kk2);
-    s.y = rotate_pair(s.y, delta_pair((e8 >> 2) & 3u, (m8 >> 2) & 3u), kk2);
-    s.z = rotate_pair(s.z, delta_pair((e8 >> 4) & 3u, (m8 >> 4) & 3u), kk2);
-    s.w = rotate_pair(s.w, delta_pair((e8 >> 6) & 3u, (m8 >> 6) & 3u), kk2);
+    s.x = rotate_pair(s.x, delta_pair(e8 & 3u, m8 & 3u), k8);
+    s.y = rotate_pair(s.y, delta_pair((e8 >> 2) & 3u, (m8 >> 2) & 3u), k8);
+    s.z = rotate_pair(s.z, delta_pair((e8 >> 4) & 3u, (m8 >> 4) & 3u), k8);
+    s.w = rotate_pair(s.w, delta_pair((e8 >> 6) & 3u, (m8 >> 6) & 3u), k8);
     return s;
 }
 
+// ---------------------------------------------------------------------------------------
+// Small PTX helpers: programmatic dependent launch, acquire/release accesses, the clock.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p)
+{
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t *p, int32_t v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Elite key: larger fitness wins, then the lower chromosome index.
+constexpr int64_t kKeyBias = (int64_t)1 << 39;
+
+__device__ __forceinline__ unsigned long long elite_key(int64_t f, int32_t c)
+{
+    return ((unsigned long long)(f + kKeyBias) << 24) | (unsigned long long)(0xffffffu - (uint32_t)c);
+}
+
+// Error bits reported through GenParams::error.
+constexpr int32_t kErrBarrierTimeout = 1;
+
 struct GenParams {
-    uint4 *state;                 // [np][svec]
-    uint8_t *xbits;               // [np][xstride]
+    uint4 *state;                 // [np][svec] scaled angle indices
+    uint8_t *xbits;               // [2][np][xstride]
     const uint4 *items_narrow;    // [2 svec] packed (v << 16 | w), 4 genes per uint4
     const int4 *w4;               // wide: [2 svec] weights
     const int4 *v4;               // wide: [2 svec] values
-    uint8_t *elite;               // [xstride] alleles of the last elite
     unsigned long long *acc;      // narrow [np]; wide [2 np]
+    unsigned int *cnt;            // wide: [np]
     int64_t *fitness;             // [np] of the last generation
+    unsigned long long *key;      // [1] elite key of the running generation
+    int32_t *elite_idx;           // [1] elite of the last completed generation
     int32_t *hist_e;              // [capacity] elite index per generation
     int64_t *hist_f;              // [capacity] elite fitness per generation
     int64_t *best;                // [3] fitness, generation (-1 none), chromosome
     uint8_t *best_row;            // [xstride]
     int32_t *gen;                 // number of the generation to run next
     unsigned int *ticket;         // blocks finished in this generation
+    int32_t *bar_gen;             // grid barrier: generations released so far
+    int32_t *error;               // kErr* bits
     const uint32_t *thr;          // [2K+1] low 32 bits of T[n] (T[2K] = 2^32 -> 0)
-    int32_t np, svec, xstride, K;
     int64_t capacity, lambda;
-    uint32_t key0, key1;
-    int32_t lanes, warps, rows_per_cta;
+    int64_t units;                // ntile * np tile-rows
+    size_t xplane;                // np * xstride
+    uint64_t wait_ns;             // bound of one grid-barrier wait
+    int32_t np, svec, xstride, K, ntile;
+    int32_t lanes, warps, seg_rows_max, key_mode;
     int32_t apply_cip, do_de;
+    uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
-// Row-wise DetermineElite, run by the last block of a generation: eq. (1) from the row
-// sums, lowest-index argmax, elite/best records, and the accumulators cleared for the next
-// generation.
+// Eq. (1) of a finished row; records the fitness and offers the row to the elite key.
+__device__ __forceinline__ void finish_row(const GenParams &p, int32_t c, int64_t sw, int64_t sv)
+{
+    const int64_t f = sw <= p.capacity ? sv : -p.lambda * (sw - p.capacity);
+    p.fitness[c] = f;
+    if (p.key_mode) atomicMax(p.key, elite_key(f, c));
+}
+
+// Adds one block's sums of a tile-row to the row; the block that adds the last of the
+// ntile contributions evaluates the row.
 template <bool kNarrow>
-__device__ void determine_elite(const GenParams &p, int32_t t)
+__device__ __forceinline__ void combine_row(const GenParams &p, int32_t c, uint64_t sw, uint64_t sv)
+{
+    if (kNarrow) {
+        const unsigned long long add = (1ull << 56) | (sv << 28) | sw;
+        const unsigned long long old = atomicAdd(p.acc + c, add);
+        if ((int32_t)(old >> 56) == p.ntile - 1) {
+            const unsigned long long full = old + add;
+            p.acc[c] = 0ull;
+            finish_row(p, c, (int64_t)(full & 0xfffffffull), (int64_t)((full >> 28) & 0xfffffffull));
+        }
+    } else {
+        atomicAdd(p.acc + 2 * (size_t)c, (unsigned long long)sw);
+        atomicAdd(p.acc + 2 * (size_t)c + 1, (unsigned long long)sv);
+        if ((int32_t)atom_add_acq_rel(p.cnt + c, 1u) == p.ntile - 1) {
+            const int64_t w = (int64_t)ld_relaxed(p.acc + 2 * (size_t)c);
+            const int64_t v = (int64_t)ld_relaxed(p.acc + 2 * (size_t)c + 1);
+            p.acc[2 * (size_t)c] = 0ull;
+            p.acc[2 * (size_t)c + 1] = 0ull;
+            p.cnt[c] = 0u;
+            finish_row(p, c, w, v);
+        }
+    }
+}
+
+// Closes generation t (one block, all threads): elite from the key (or a lowest-index
+// argmax over the fitness array when fitness values do not fit the key), records.
+__device__ void close_generation(const GenParams &p, int32_t t)
 {
     __shared__ int64_t s_f[kThreads / 32];
     __shared__ int32_t s_c[kThreads / 32];
     __shared__ int32_t s_e;
     __shared__ int32_t s_improved;
     const int tid = threadIdx.x;
-
     int64_t bf = INT64_MIN;
     int32_t bc = 0x7fffffff;
-    for (int c = tid; c < p.np; c += kThreads) {
-        int64_t sw, sv;
-        if (kNarrow) {
-            const unsigned long long a = __ldcg(p.acc + c);
-            sw = (int64_t)(a & 0xffffffffull);
-            sv = (int64_t)(a >> 32);
-            p.acc[c] = 0ull;
-        } else {
-            sw = (int64_t)__ldcg(p.acc + 2 * (size_t)c);
-            sv = (int64_t)__ldcg(p.acc + 2 * (size_t)c + 1);
-            p.acc[2 * (size_t)c] = 0ull;
-            p.acc[2 * (size_t)c + 1] = 0ull;
+    if (p.key_mode) {
+        if (tid == 0) {
+            const unsigned long long k = __ldcg(p.key);
+            bc = (int32_t)(0xffffffu - (uint32_t)(k & 0xffffffull));
+            bf = (int64_t)(k >> 24) - kKeyBias;
+            *p.key = 0ull;
         }
-        const int64_t f = sw <= p.capacity ? sv : -p.lambda * (sw - p.capacity);
-        p.fitness[c] = f;
-        if (f > bf) {   // c grows within a thread: the first maximum is kept
-            bf = f;
-            bc = c;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int64_t of = __shfl_xor_sync(0xffffffffu, bf, o);
-        const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        if (of > bf || (of == bf && oc < bc)) {
-            bf = of;
-            bc = oc;
-        }
-    }
-    if ((tid & 31) == 0) {
-        s_f[tid >> 5] = bf;
-        s_c[tid >> 5] = bc;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < kThreads / 32; ++w) {
-            if (s_f[w] > bf || (s_f[w] == bf && s_c[w] < bc)) {
-                bf = s_f[w];
-                bc = s_c[w];
+    } else {
+        for (int c = tid; c < p.np; c += kThreads) {
+            const int64_t f = __ldcg(p.fitness + c);
+            if (f > bf) {   // c grows within a thread: the first maximum is kept
+                bf = f;
+                bc = c;
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t of = __shfl_xor_sync(0xffffffffu, bf, o);
+            const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            if (of > bf || (of == bf && oc < bc)) {
+                bf = of;
+                bc = oc;
+            }
+        }
+        if ((tid & 31) == 0) {
+            s_f[tid >> 5] = bf;
+            s_c[tid >> 5] = bc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kThreads / 32; ++w) {
+                if (s_f[w] > bf || (s_f[w] == bf && s_c[w] < bc)) {
+                    bf = s_f[w];
+                    bc = s_c[w];
+                }
+            }
+        }
+    }
+    if (tid == 0) {
         p.hist_e[t] = bc;
         p.hist_f[t] = bf;
-        const int improved = (p.best[1] < 0 || bf > p.best[0]) ? 1 : 0;
+        *p.elite_idx = bc;
+        const int64_t best_f = __ldcg(p.best), best_g = __ldcg(p.best + 1);
+        const int improved = (best_g < 0 || bf > best_f) ? 1 : 0;
         if (improved) {
             p.best[0] = bf;
             p.best[1] = t;
@@ -174,205 +310,365 @@ __device__ void determine_elite(const GenParams &p, int32_t t)
         s_improved = improved;
     }
     __syncthreads();
-    const int32_t e = s_e;
-    const int improved = s_improved;
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.xbits + (size_t)e * p.xstride);
-    uint4 *dst = reinterpret_cast<uint4 *>(p.elite);
-    uint4 *bdst = reinterpret_cast<uint4 *>(p.best_row);
-    for (int i = tid; i < p.xstride / 16; i += kThreads) {
-        const uint4 v = __ldcg(src + i);
-        dst[i] = v;
-        if (improved) bdst[i] = v;
+    if (s_improved) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(
+            p.xbits + (size_t)(t & 1) * p.xplane + (size_t)s_e * p.xstride);
+        uint4 *dst = reinterpret_cast<uint4 *>(p.best_row);
+        for (int i = tid; i < p.xstride / 16; i += kThreads) dst[i] = __ldcg(src + i);
     }
-    if (tid == 0) {
-        *p.gen = t + 1;
-        *p.ticket = 0u;
-    }
+    __syncthreads();
 }
 
-// ---------------------------------------------------------------------------------------
-// The fused generation kernel. Grid: x = gene tiles of lanes*warps vectors, y = chunks of
-// rows_per_cta chromosomes. Thread (r_sub, v_in) of a block handles vector v_in of rows
-// r_sub, r_sub + rows_per_pass, ... of its chunk; its 8 items stay in registers for all
-// of them. Row sums are reduced over the lanes of a segment by shuffles, over the warps of
-// a tile in shared memory, and over tiles by one 64-bit atomic per row and block.
-// ---------------------------------------------------------------------------------------
-template <bool kNarrow, int kRule>
-__global__ void __launch_bounds__(kThreads, 2) generation_kernel(const GenParams p)
+// Per-block constants of the work split.
+struct BlockShare {
+    int tile_vecs, rows_per_pass, r_sub, v_in;
+    bool leader;                  // first lane of its row segment
+    int64_t u_begin, u_end;       // tile-rows [u_begin, u_end) of this block
+};
+
+__device__ __forceinline__ BlockShare block_share(const GenParams &p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_last;
-    const int n_thr = 2 * p.K + 1;
-    uint32_t *s_thr = reinterpret_cast<uint32_t *>(smem_raw);
-    unsigned long long *s_acc64 =
-        reinterpret_cast<unsigned long long *>(smem_raw + (((size_t)n_thr * 4 + 15) & ~(size_t)15));
-    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(s_acc64);
+    BlockShare b;
+    b.tile_vecs = p.lanes * p.warps;
+    b.rows_per_pass = kThreads / b.tile_vecs;
+    b.r_sub = threadIdx.x / b.tile_vecs;
+    b.v_in = threadIdx.x - b.r_sub * b.tile_vecs;
+    b.leader = (threadIdx.x & (p.lanes - 1)) == 0;
+    b.u_begin = (int64_t)blockIdx.x * p.units / gridDim.x;
+    b.u_end = (int64_t)(blockIdx.x + 1) * p.units / gridDim.x;
+    return b;
+}
 
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int tile_vecs = p.lanes * p.warps;
-    const int rows_per_pass = kThreads / tile_vecs;
-    const int r_sub = tid / tile_vecs;
-    const int v_in = tid - r_sub * tile_vecs;
-    const int vec = blockIdx.x * tile_vecs + v_in;
-    const bool active = vec < p.svec;
-    const int row0 = blockIdx.y * p.rows_per_cta;
-    const int rows_here = min(p.rows_per_cta, p.np - row0);
-    const int passes = (rows_here + rows_per_pass - 1) / rows_per_pass;
+__device__ __forceinline__ void load_thresholds(const GenParams &p, uint32_t *s_thr)
+{
+    for (int i = threadIdx.x; i < 2 * p.K + 1; i += kThreads) s_thr[i] = p.thr[i];
+}
 
-    for (int i = tid; i < n_thr; i += kThreads) s_thr[i] = p.thr[i];
-    for (int i = tid; i < 2 * rows_here; i += kThreads) {
-        if (kNarrow) s_acc32[i] = 0u;
-        else s_acc64[i] = 0ull;
-    }
-    const int32_t t = *p.gen;
-
-    // Items of this thread's 8 genes (zero outside the row: they add nothing).
-    uint32_t wv[8];
-    int32_t wi[8], vi[8];
+// Sum over the lanes of a row segment (p.lanes lanes, a power of two).
+template <bool kNarrow>
+__device__ __forceinline__ void segment_sum(const GenParams &p, uint32_t &accn, int64_t &acw,
+                                            int64_t &acv)
+{
     if (kNarrow) {
-        uint4 a = make_uint4(0, 0, 0, 0), b = a;
-        if (active) {
-            a = __ldg(p.items_narrow + 2 * (size_t)vec);
-            b = __ldg(p.items_narrow + 2 * (size_t)vec + 1);
-        }
-        wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
-        wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
-    } else {
-        int4 a = make_int4(0, 0, 0, 0), b = a, c = a, d = a;
-        if (active) {
-            a = __ldg(p.w4 + 2 * (size_t)vec);
-            b = __ldg(p.w4 + 2 * (size_t)vec + 1);
-            c = __ldg(p.v4 + 2 * (size_t)vec);
-            d = __ldg(p.v4 + 2 * (size_t)vec + 1);
-        }
-        wi[0] = a.x; wi[1] = a.y; wi[2] = a.z; wi[3] = a.w;
-        wi[4] = b.x; wi[5] = b.y; wi[6] = b.z; wi[7] = b.w;
-        vi[0] = c.x; vi[1] = c.y; vi[2] = c.z; vi[3] = c.w;
-        vi[4] = d.x; vi[5] = d.y; vi[6] = d.z; vi[7] = d.w;
-    }
-    const uint32_t e8 = (p.apply_cip && active) ? (uint32_t)p.elite[vec] : 0u;
-    const uint32_t kk2 = (uint32_t)(2 * p.K) * 0x00010001u;
-    const uint32_t n_top = (uint32_t)(2 * p.K);
-    __syncthreads();
-
-    for (int pass = 0; pass < passes; ++pass) {
-        const int rr = pass * rows_per_pass + r_sub;
-        const bool row_ok = rr < rows_here;
-        const bool live = active && row_ok;
-        const int c = row0 + rr;
-        const size_t sidx = (size_t)c * p.svec + vec;
-        const size_t xidx = (size_t)c * p.xstride + vec;
-
-        uint4 s = make_uint4(0, 0, 0, 0);
-        if (live) s = p.state[sidx];
-        if (p.apply_cip) {
-            uint32_t m8 = 0xffu;                               // R1: every qubit moves
-            if (kRule == 1) m8 = live ? (e8 ^ (uint32_t)p.xbits[xidx]) : 0u;
-            s = rotate_vec(s, e8, m8, kk2);
-        }
-
-        const uint32_t ctr0 = 2u * (uint32_t)vec;
-        const Draw4 r0 = philox4x32_10(ctr0, (uint32_t)c, (uint32_t)t, 0u, p.key0, p.key1);
-        const Draw4 r1 = philox4x32_10(ctr0 + 1u, (uint32_t)c, (uint32_t)t, 0u, p.key0, p.key1);
-        const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
-        const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
-
-        uint32_t xb = 0u;
-        uint32_t accn = 0u;
-        int64_t acw = 0, acv = 0;
+        if (p.lanes == 32) {
+            accn = __reduce_add_sync(0xffffffffu, accn);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t n = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
-            const bool x = (u[i] < s_thr[n]) || (n == n_top);
-            if (x) {
-                xb |= 1u << i;
-                if (kNarrow) {
-                    accn += wv[i];
-                } else {
-                    acw += wi[i];
-                    acv += vi[i];
-                }
-            }
+            for (int o = 16; o > 0; o >>= 1)
+                if (o < p.lanes) accn += __shfl_xor_sync(0xffffffffu, accn, o);
         }
-        if (live) {
-            p.state[sidx] = s;
-            p.xbits[xidx] = (uint8_t)xb;
-        }
-
-        // Segment (row) reduction over p.lanes lanes.
-        for (int o = p.lanes >> 1; o > 0; o >>= 1) {
-            if (kNarrow) {
-                accn += __shfl_xor_sync(0xffffffffu, accn, o);
-            } else {
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o < p.lanes) {
                 acw += __shfl_xor_sync(0xffffffffu, acw, o);
                 acv += __shfl_xor_sync(0xffffffffu, acv, o);
             }
         }
-        if (row_ok && (lane & (p.lanes - 1)) == 0) {
-            if (kNarrow) {
-                atomicAdd(s_acc32 + 2 * rr, accn & 0xffffu);
-                atomicAdd(s_acc32 + 2 * rr + 1, accn >> 16);
-            } else {
-                atomicAdd(s_acc64 + 2 * rr, (unsigned long long)acw);
-                atomicAdd(s_acc64 + 2 * rr + 1, (unsigned long long)acv);
-            }
-        }
     }
-    __syncthreads();
-    for (int i = tid; i < rows_here; i += kThreads) {
-        if (kNarrow) {
-            const unsigned long long v =
-                ((unsigned long long)s_acc32[2 * i + 1] << 32) | (unsigned long long)s_acc32[2 * i];
-            atomicAdd(p.acc + row0 + i, v);
-        } else {
-            atomicAdd(p.acc + 2 * (size_t)(row0 + i), s_acc64[2 * i]);
-            atomicAdd(p.acc + 2 * (size_t)(row0 + i) + 1, s_acc64[2 * i + 1]);
-        }
-    }
-    if (!p.do_de) return;
+}
 
-    // Last block to finish runs DetermineElite (no block waits for another).
+// ---------------------------------------------------------------------------------------
+// One generation over this block's share. Thread (r_sub, v_in) handles vector v_in of rows
+// r_sub, r_sub + rows_per_pass, ... of each tile segment; its 8 items stay in registers
+// for the whole segment, and the state of the next two rows is in flight while a row is
+// computed. Row sums are reduced over the lanes of a segment in the warp, over the warps
+// of a tile in shared memory, and over tiles by one atomic per tile-row.
+// ---------------------------------------------------------------------------------------
+template <bool kNarrow, int kRule, bool kCip>
+__device__ __forceinline__ void generation_body(const GenParams &p, const BlockShare &b,
+                                                int32_t t, int32_t e_prev,
+                                                const uint32_t *s_thr, uint32_t *s_acc32,
+                                                unsigned long long *s_acc64)
+{
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+    uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    const uint32_t off_top = (uint32_t)(8 * p.K);
+    const int rpp = b.rows_per_pass;
+
+    for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
+        const int tile = (int)(u0 / p.np);
+        const int ra = (int)(u0 - (int64_t)tile * p.np);
+        const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
+        u0 += seg_rows;
+        const int passes = (seg_rows + rpp - 1) / rpp;
+
+        const int vec = tile * b.tile_vecs + b.v_in;
+        const bool active = vec < p.svec;
+        const size_t row0 = (size_t)ra + b.r_sub;
+        uint4 *sptr = p.state + row0 * p.svec + vec;
+        const size_t sstep = (size_t)rpp * p.svec;
+        uint8_t *xptr = x_cur + row0 * p.xstride + vec;
+        const uint8_t *xoptr = x_prev + row0 * p.xstride + vec;
+        const size_t xstep = (size_t)rpp * p.xstride;
+
+        auto row_ok = [&](int pass) { return pass * rpp + b.r_sub < seg_rows; };
+        auto load_state = [&](int pass) -> uint4 {
+            uint4 s = make_uint4(0, 0, 0, 0);
+            if (active && row_ok(pass)) s = sptr[(size_t)pass * sstep];
+            return s;
+        };
+        auto load_xold = [&](int pass) -> uint32_t {
+            if (kRule != 1 || !kCip) return 0u;
+            if (!(active && row_ok(pass))) return 0u;
+            return (uint32_t)xoptr[(size_t)pass * xstep];
+        };
+
+        // Two rows in flight before anything else is waited on.
+        uint4 sa = load_state(0), sb = load_state(1), sc;
+        uint32_t xa = load_xold(0), xb1 = load_xold(1), xc = 0u;
+
+        uint32_t wv[8];
+        int32_t wi[8], vi[8];
+        if (kNarrow) {
+            uint4 a = make_uint4(0, 0, 0, 0), c = a;
+            if (active) {
+                a = __ldg(p.items_narrow + 2 * (size_t)vec);
+                c = __ldg(p.items_narrow + 2 * (size_t)vec + 1);
+            }
+            wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
+            wv[4] = c.x; wv[5] = c.y; wv[6] = c.z; wv[7] = c.w;
+        } else {
+            int4 a = make_int4(0, 0, 0, 0), c = a, d = a, e = a;
+            if (active) {
+                a = __ldg(p.w4 + 2 * (size_t)vec);
+                c = __ldg(p.w4 + 2 * (size_t)vec + 1);
+                d = __ldg(p.v4 + 2 * (size_t)vec);
+                e = __ldg(p.v4 + 2 * (size_t)vec + 1);
+            }
+            wi[0] = a.x; wi[1] = a.y; wi[2] = a.z; wi[3] = a.w;
+            wi[4] = c.x; wi[5] = c.y; wi[6] = c.z; wi[7] = c.w;
+            vi[0] = d.x; vi[1] = d.y; vi[2] = d.z; vi[3] = d.w;
+            vi[4] = e.x; vi[5] = e.y; vi[6] = e.z; vi[7] = e.w;
+        }
+        const uint32_t e8 = (kCip && active) ? (uint32_t)__ldcg(elite_row + vec) : 0u;
+        const uint32_t ctr0 = 2u * (uint32_t)vec;
+
+        for (int i = threadIdx.x; i < 2 * seg_rows; i += kThreads) {
+            if (kNarrow) s_acc32[i] = 0u;
+            else s_acc64[i] = 0ull;
+        }
+        __syncthreads();
+
+        auto process = [&](uint4 s, uint32_t xo, int pass) {
+            const int rr = pass * rpp + b.r_sub;
+            const bool ok = rr < seg_rows;
+            const int c = ra + rr;
+            if (kCip) s = rotate_vec(s, e8, kRule == 1 ? (e8 ^ xo) : 0xffu, k8);
+
+            const Draw4 r0 = philox4x32_10_rk(ctr0, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+            const Draw4 r1 = philox4x32_10_rk(ctr0 + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+            const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
+            const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
+
+            uint32_t xbits = 0u;
+            uint32_t accn = 0u;
+            int64_t acw = 0, acv = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
+                const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+                const bool x = (u[i] < thr) || (off == off_top);
+                if (x) {
+                    xbits |= 1u << i;
+                    if (kNarrow) {
+                        accn += wv[i];
+                    } else {
+                        acw += wi[i];
+                        acv += vi[i];
+                    }
+                }
+            }
+            if (active && ok) {
+                sptr[(size_t)pass * sstep] = s;
+                xptr[(size_t)pass * xstep] = (uint8_t)xbits;
+            }
+            segment_sum<kNarrow>(p, accn, acw, acv);
+            if (ok && b.leader) {
+                if (kNarrow) {
+                    atomicAdd(s_acc32 + 2 * rr, accn & 0xffffu);
+                    atomicAdd(s_acc32 + 2 * rr + 1, accn >> 16);
+                } else {
+                    atomicAdd(s_acc64 + 2 * rr, (unsigned long long)acw);
+                    atomicAdd(s_acc64 + 2 * rr + 1, (unsigned long long)acv);
+                }
+            }
+        };
+
+        // Three state buffers in rotation: two rows in flight while one is computed.
+        for (int pass = 0; pass < passes; pass += 3) {
+            sc = load_state(pass + 2);
+            xc = load_xold(pass + 2);
+            process(sa, xa, pass);
+            if (pass + 1 >= passes) break;
+            sa = load_state(pass + 3);
+            xa = load_xold(pass + 3);
+            process(sb, xb1, pass + 1);
+            if (pass + 2 >= passes) break;
+            sb = load_state(pass + 4);
+            xb1 = load_xold(pass + 4);
+            process(sc, xc, pass + 2);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < seg_rows; i += kThreads) {
+            if (kNarrow)
+                combine_row<true>(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1]);
+            else
+                combine_row<false>(p, ra + i, s_acc64[2 * i], s_acc64[2 * i + 1]);
+        }
+        __syncthreads();
+    }
+}
+
+// CIP with elite e of generation t over this block's share (the final rotation of a run).
+template <int kRule>
+__device__ __forceinline__ void final_cip_body(const GenParams &p, const BlockShare &b,
+                                               int32_t t, int32_t e)
+{
+    const uint8_t *xl = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint8_t *elite_row = xl + (size_t)e * p.xstride;
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
+        const int tile = (int)(u0 / p.np);
+        const int ra = (int)(u0 - (int64_t)tile * p.np);
+        const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
+        u0 += seg_rows;
+        const int vec = tile * b.tile_vecs + b.v_in;
+        if (vec >= p.svec) continue;
+        const uint32_t e8 = __ldcg(elite_row + vec);
+        for (int rr = b.r_sub; rr < seg_rows; rr += b.rows_per_pass) {
+            const size_t c = (size_t)ra + rr;
+            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
+            uint4 *sp = p.state + c * p.svec + vec;
+            *sp = rotate_vec(*sp, e8, m8, k8);
+        }
+    }
+}
+
+// Bounded grid barrier after generation t: the last block to arrive closes the generation
+// and releases the others. Returns false when the wait ran out or an error was raised
+// (the block then stops; the host reports QIEO_ERR_TIMEOUT).
+__device__ __forceinline__ bool generation_barrier(const GenParams &p, int32_t t)
+{
+    __shared__ int s_flag;
     __threadfence();
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         const unsigned int prev = atomicAdd(p.ticket, 1u);
-        s_last = (prev == gridDim.x * gridDim.y - 1u) ? 1 : 0;
+        s_flag = (prev == gridDim.x - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_flag) {
+        __threadfence();
+        close_generation(p, t);
+        if (threadIdx.x == 0) {
+            *p.ticket = 0u;
+            *p.gen = t + 1;
+            __threadfence();
+            st_release(p.bar_gen, t + 1);
+        }
+    } else if (threadIdx.x == 0) {
+        const uint64_t deadline = global_ns() + p.wait_ns;
+        int ok = 0;
+        for (uint32_t it = 0; it < (1u << 30); ++it) {
+            if (ld_acquire(p.bar_gen) >= t + 1) {
+                ok = 1;
+                break;
+            }
+            if (ld_acquire(p.error) != 0 || global_ns() > deadline) break;
+            __nanosleep(64);
+        }
+        if (!ok) atomicOr(p.error, kErrBarrierTimeout);
+        s_flag = ok ? 2 : 0;
+    }
+    __syncthreads();
+    return s_flag != 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// run_kernel: generations t0 .. t0+G-1 and the final CIP in one cooperative launch. The
+// first generation applies no CIP (a run starts from a rotated state or from t = 0).
+// ---------------------------------------------------------------------------------------
+template <bool kNarrow, int kRule>
+__global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) run_kernel(const GenParams p, int32_t G)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *s_acc64 = reinterpret_cast<unsigned long long *>(smem_raw);
+    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(smem_raw);
+
+    load_thresholds(p, s_thr);
+    grid_dependency_wait();
+    const BlockShare b = block_share(p);
+    const int32_t t0 = *p.gen;
+    int32_t e = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        const int32_t t = t0 + g;
+        if (g == 0) generation_body<kNarrow, kRule, false>(p, b, t, 0, s_thr, s_acc32, s_acc64);
+        else generation_body<kNarrow, kRule, true>(p, b, t, e, s_thr, s_acc32, s_acc64);
+        if (!generation_barrier(p, t)) return;
+        e = __ldcg(p.elite_idx);
+    }
+    final_cip_body<kRule>(p, b, t0 + G - 1, e);
+}
+
+// ---------------------------------------------------------------------------------------
+// generation_kernel: one generation per launch. The last block to finish closes the
+// generation (no block waits for another).
+// ---------------------------------------------------------------------------------------
+template <bool kNarrow, int kRule>
+__global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) generation_kernel(const GenParams p)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    __shared__ int s_last;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *s_acc64 = reinterpret_cast<unsigned long long *>(smem_raw);
+    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(smem_raw);
+
+    load_thresholds(p, s_thr);
+    grid_dependency_wait();
+    const BlockShare b = block_share(p);
+    const int32_t t = *p.gen;
+    const int32_t e_prev = *p.elite_idx;
+    if (p.apply_cip) generation_body<kNarrow, kRule, true>(p, b, t, e_prev, s_thr, s_acc32, s_acc64);
+    else generation_body<kNarrow, kRule, false>(p, b, t, e_prev, s_thr, s_acc32, s_acc64);
+
+    // The next generation's blocks may start their prologue now.
+    allow_dependent_launch();
+    if (!p.do_de) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(p.ticket, 1u);
+        s_last = (prev == gridDim.x - 1u) ? 1 : 0;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    determine_elite<kNarrow>(p, t);
+    close_generation(p, t);
+    if (threadIdx.x == 0) {
+        *p.gen = t + 1;
+        *p.ticket = 0u;
+        *p.bar_gen = t + 1;
+    }
 }
 
-// DetermineElite for the host variant: the elite index e comes from the host; this kernel
-// writes the records exactly as the fused path does (one block).
-template <bool kNarrow>
+// Records of a generation whose elite e was picked on the host (host DetermineElite).
 __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams p, int32_t e)
 {
     __shared__ int s_improved;
     const int tid = threadIdx.x;
+    grid_dependency_wait();
     const int32_t t = *p.gen;
-    for (int c = tid; c < p.np; c += kThreads) {
-        int64_t sw, sv;
-        if (kNarrow) {
-            const unsigned long long a = p.acc[c];
-            sw = (int64_t)(a & 0xffffffffull);
-            sv = (int64_t)(a >> 32);
-            p.acc[c] = 0ull;
-        } else {
-            sw = (int64_t)p.acc[2 * (size_t)c];
-            sv = (int64_t)p.acc[2 * (size_t)c + 1];
-            p.acc[2 * (size_t)c] = 0ull;
-            p.acc[2 * (size_t)c + 1] = 0ull;
-        }
-        p.fitness[c] = sw <= p.capacity ? sv : -p.lambda * (sw - p.capacity);
-    }
-    __syncthreads();
     if (tid == 0) {
         const int64_t fe = p.fitness[e];
         p.hist_e[t] = e;
         p.hist_f[t] = fe;
+        *p.elite_idx = e;
+        *p.key = 0ull;
         const int improved = (p.best[1] < 0 || fe > p.best[0]) ? 1 : 0;
         if (improved) {
             p.best[0] = fe;
@@ -382,53 +678,63 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
         s_improved = improved;
     }
     __syncthreads();
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.xbits + (size_t)e * p.xstride);
-    for (int i = tid; i < p.xstride / 16; i += kThreads) {
-        const uint4 v = src[i];
-        reinterpret_cast<uint4 *>(p.elite)[i] = v;
-        if (s_improved) reinterpret_cast<uint4 *>(p.best_row)[i] = v;
+    if (s_improved) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(
+            p.xbits + (size_t)(t & 1) * p.xplane + (size_t)e * p.xstride);
+        for (int i = tid; i < p.xstride / 16; i += kThreads)
+            reinterpret_cast<uint4 *>(p.best_row)[i] = src[i];
     }
-    if (tid == 0) *p.gen = t + 1;
+    if (tid == 0) {
+        *p.gen = t + 1;
+        *p.bar_gen = t + 1;
+    }
 }
 
-// CIP of the last generation of a run (the same rotation the next generation would fuse).
+// CIP of the last generation of a run launched generation by generation.
 template <int kRule>
-__global__ void __launch_bounds__(kThreads) cip_kernel(uint4 *state, const uint8_t *xbits,
-                                                       const uint8_t *elite, int32_t np,
-                                                       int32_t svec, int32_t xstride, int32_t K)
+__global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
 {
-    const uint32_t kk2 = (uint32_t)(2 * K) * 0x00010001u;
-    const size_t total = (size_t)np * svec;
+    grid_dependency_wait();
+    const int32_t t_last = *p.gen - 1;
+    const int32_t e = *p.elite_idx;
+    const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
+    const uint8_t *elite = xl + (size_t)e * p.xstride;
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    const size_t total = (size_t)p.np * p.svec;
     for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
          i += (size_t)gridDim.x * kThreads) {
-        const size_t c = i / (size_t)svec;
-        const size_t v = i - c * (size_t)svec;
+        const size_t c = i / (size_t)p.svec;
+        const size_t v = i - c * (size_t)p.svec;
         const uint32_t e8 = elite[v];
-        const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xbits[c * xstride + v]) : 0xffu;
-        state[i] = rotate_vec(state[i], e8, m8, kk2);
+        const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
+        p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
     }
 }
 
 // Generation 0 state: every qubit at theta = pi/4 (n = K), no elite, no best record.
 __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t state_words,
-                                                        size_t xbytes)
+                                                        size_t xbytes, size_t acc_words)
 {
-    const uint32_t kk = (uint32_t)p.K * 0x00010001u;
+    grid_dependency_wait();
+    const uint32_t kk = (uint32_t)(4 * p.K) * 0x00010001u;
     uint32_t *s = reinterpret_cast<uint32_t *>(p.state);
     const size_t stride = (size_t)gridDim.x * kThreads;
     const size_t i0 = (size_t)blockIdx.x * kThreads + threadIdx.x;
     for (size_t i = i0; i < state_words; i += stride) s[i] = kk;
     for (size_t i = i0; i < xbytes; i += stride) p.xbits[i] = 0;
-    for (size_t i = i0; i < (size_t)p.xstride; i += stride) {
-        p.elite[i] = 0;
-        p.best_row[i] = 0;
+    for (size_t i = i0; i < (size_t)p.xstride; i += stride) p.best_row[i] = 0;
+    for (size_t i = i0; i < acc_words; i += stride) p.acc[i] = 0ull;
+    for (size_t i = i0; i < (size_t)p.np; i += stride) {
+        p.fitness[i] = 0;
+        p.cnt[i] = 0u;
     }
-    const size_t nacc = (size_t)p.np * 2;
-    for (size_t i = i0; i < nacc; i += stride) p.acc[i] = 0ull;
-    for (size_t i = i0; i < (size_t)p.np; i += stride) p.fitness[i] = 0;
     if (i0 == 0) {
         *p.gen = 0;
         *p.ticket = 0u;
+        *p.key = 0ull;
+        *p.elite_idx = 0;
+        *p.bar_gen = 0;
+        *p.error = 0;
         p.best[0] = 0;
         p.best[1] = -1;
         p.best[2] = -1;

@@ -28,11 +28,13 @@ QIEO_FLAG_NO_GRAPH = 0x1
 QIEO_FLAG_SYNC_RUN = 0x2
 QIEO_FLAG_FORCE_WIDE = 0x4
 QIEO_FLAG_TIME_KERNELS = 0x8
+QIEO_FLAG_PER_GENERATION = 0x10
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
     "qieo_default_params", "qieo_create_instance", "qieo_destroy_instance", "qieo_reset",
-    "qieo_run", "qieo_synchronize", "qieo_get_best", "qieo_get_state", "qieo_get_fitness",
+    "qieo_run", "qieo_set_wait_timeout", "qieo_synchronize", "qieo_get_best",
+    "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
     "qieo_last_error",
@@ -58,8 +60,8 @@ class qieo_params(C.Structure):
 
 class qieo_launch_shape(C.Structure):
     _fields_ = [("lanes_per_row", C.c_int32), ("warps_per_row", C.c_int32),
-                ("rows_per_cta", C.c_int32), ("narrow", C.c_int32), ("grid_x", C.c_int32),
-                ("grid_y", C.c_int32)]
+                ("grid_ctas", C.c_int32), ("narrow", C.c_int32), ("tiles", C.c_int32),
+                ("rows_per_cta", C.c_int32)]
 
 
 _LIB: C.CDLL | None = None
@@ -86,6 +88,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_destroy_instance": ([P], C.c_int),
         "qieo_reset": ([P], C.c_int),
         "qieo_run": ([P, i32], C.c_int),
+        "qieo_set_wait_timeout": ([P, i64], C.c_int),
         "qieo_synchronize": ([P], C.c_int),
         "qieo_get_best": ([P, P, P, P, P], C.c_int),
         "qieo_get_state": ([P, P, P], C.c_int),
@@ -146,6 +149,10 @@ def qieo_run(h, generations: int) -> None:
     _check(load().qieo_run(h, int(generations)))
 
 
+def qieo_set_wait_timeout(h, ns: int) -> None:
+    _check(load().qieo_set_wait_timeout(h, int(ns)))
+
+
 def qieo_synchronize(h) -> None:
     _check(load().qieo_synchronize(h))
 
@@ -195,8 +202,8 @@ def qieo_get_launch_shape(h) -> qieo_launch_shape:
     return s
 
 
-def qieo_set_launch_shape(h, lanes_per_row: int, warps_per_row: int, rows_per_cta: int) -> None:
-    s = qieo_launch_shape(int(lanes_per_row), int(warps_per_row), int(rows_per_cta), 0, 0, 0)
+def qieo_set_launch_shape(h, lanes_per_row: int, warps_per_row: int, grid_ctas: int = 0) -> None:
+    s = qieo_launch_shape(int(lanes_per_row), int(warps_per_row), int(grid_ctas), 0, 0, 0)
     _check(load().qieo_set_launch_shape(h, C.byref(s)))
 
 
@@ -258,6 +265,9 @@ class Instance:
     def synchronize(self) -> None:
         qieo_synchronize(self.h)
 
+    def set_wait_timeout(self, ns: int) -> None:
+        qieo_set_wait_timeout(self.h, ns)
+
     def best(self):
         return qieo_get_best(self.h, self.ng)
 
@@ -279,8 +289,8 @@ class Instance:
     def shape(self) -> qieo_launch_shape:
         return qieo_get_launch_shape(self.h)
 
-    def set_shape(self, lanes_per_row: int, warps_per_row: int, rows_per_cta: int) -> None:
-        qieo_set_launch_shape(self.h, lanes_per_row, warps_per_row, rows_per_cta)
+    def set_shape(self, lanes_per_row: int, warps_per_row: int, grid_ctas: int = 0) -> None:
+        qieo_set_launch_shape(self.h, lanes_per_row, warps_per_row, grid_ctas)
 
     def kernel_time(self):
         return qieo_get_kernel_time(self.h)

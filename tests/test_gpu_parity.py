@@ -84,6 +84,14 @@ def test_flags_do_not_change_results(flags):
 
 
 @pytest.mark.parametrize("rule", [0, 1])
+def test_per_generation_launches(rule):
+    """One kernel per generation (programmatic dependent launch, graph replay on repeated
+    run lengths) gives the same results as the one cooperative launch per run."""
+    compare(W.knapsack(2500, 15), 60, [7, 7, 7, 4], seed=15, rule=rule,
+            flags=Q.QIEO_FLAG_PER_GENERATION)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
 def test_host_determine_elite_variant(rule):
     compare(W.knapsack(500, 2), 40, [25, 15], seed=2, rule=rule, host=1)
 
@@ -104,9 +112,9 @@ def test_ragged_sizes(ng, np_):
     compare(W.knapsack(ng, ng + np_), np_, [12], seed=ng, inst=np_, rule=(ng + np_) % 2)
 
 
-@pytest.mark.parametrize("shape", [(32, 8, 1), (32, 8, 3), (32, 4, 64), (32, 2, 8), (32, 1, 40),
-                                   (16, 1, 16), (8, 1, 32), (4, 1, 64), (2, 1, 128), (1, 1, 256),
-                                   (32, 8, 1024)])
+@pytest.mark.parametrize("shape", [(32, 8, 0), (32, 8, 1), (32, 8, 7), (32, 4, 3), (32, 2, 50),
+                                   (32, 1, 0), (16, 1, 9), (8, 1, 0), (4, 1, 33), (2, 1, 0),
+                                   (1, 1, 5), (1, 1, 0), (32, 8, 100000)])
 def test_launch_shape_independence(shape):
     """Results do not depend on the block shape: integer sums are exact and every draw is
     keyed by (gene, chromosome, generation), not by thread."""
@@ -123,6 +131,21 @@ def test_wide_items_and_penalty():
     assert shape.narrow == 0
     prob2 = W.custom_problem(rng.integers(0, 1000, 900), rng.integers(0, 1000, 900), 20000)
     compare(prob2, 33, [20], seed=10, lam=3, rule=1)
+
+
+def test_scan_mode_elite():
+    """lambda * sum(w) beyond the 40-bit elite key: the elite comes from a lowest-index
+    argmax over the fitness array instead of the key."""
+    prob = W.knapsack(300, 13)
+    compare(prob, 45, [25], seed=13, lam=2**30)
+
+
+def test_many_tiles_force_wide_sums():
+    """One lane per row tile and 263 tiles per row: more tiles than the packed row word
+    counts, so the 64-bit row sums are used."""
+    prob = W.knapsack(2100, 14)
+    shape = compare(prob, 12, [8], seed=14, shape=(1, 1, 0))
+    assert shape.tiles == 263 and shape.narrow == 0
 
 
 def test_narrow_boundary_items():
@@ -177,3 +200,23 @@ def test_c3_full_size_first_generations():
     c = W.WORKLOADS["c3"]
     compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [2, 1], seed=c["seed"],
             inst=c["inst"], kind="omp")
+
+
+def test_barrier_wait_timeout_is_reported():
+    """A grid-barrier wait that runs out ends the run with QIEO_ERR_TIMEOUT (no trap, no
+    hang); after qieo_reset the instance runs correctly again."""
+    from oracle import oracle as O
+    prob = W.knapsack(6000, 16)
+    with Q.Instance(prob, 300, seed=16) as I:
+        assert I.shape().grid_ctas > 1
+        I.set_wait_timeout(1)
+        I.run(5)
+        with pytest.raises(Q.QieoError) as e:
+            I.synchronize()
+        assert e.value.status == Q.QIEO_ERR_TIMEOUT
+        I.set_wait_timeout(10 * 10**9)
+        I.reset()
+        I.run(5)
+        k, t = I.state()
+        ref = O.run(prob, 300, 5, seed=16)
+        assert t == 5 and np.array_equal(k, ref.k)
