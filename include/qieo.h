@@ -165,6 +165,39 @@ qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launc
  * (c0 c1 c2 c3 k0 k1), out is n*4 host uint32. Uses the library's default stream. */
 qieo_status qieo_philox(const uint32_t *ctr_key, uint32_t *out, int32_t n);
 
+/* Largest population qieo_generation_noalloc accepts (the size of its static array). */
+#define QIEO_NOALLOC_MAX_NP 65536
+
+/* One generation (observe, evaluate, pick the elite, rotate toward it) on buffers the
+ * caller already owns in device memory, allocating nothing. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc where they need a
+ * generation -- code that runs while its memory pool is locked or being torn down,
+ * latency-critical loops in which an allocation may stall, and hosts whose own allocator
+ * owns all of device memory.
+ *
+ * Arguments: problem->weights and problem->values are DEVICE pointers (ng int32 each);
+ * params supplies np (1 .. QIEO_NOALLOC_MAX_NP), dtheta_den, penalty_lambda, seed,
+ * instance_id, rotate_rule and stream (elite_on_host and flags are ignored); t is the
+ * absolute generation number (it keys the Philox draws). k (np*ng int16, in/out) holds
+ * the angle indices before the generation and receives them after its rotation; x
+ * (np*ng uint8) receives the alleles, fitness (np int64) the eq. (1) values and elite (one
+ * int32) the lowest-index best chromosome. All four are device pointers, row c =
+ * chromosome c. Called with t = 0, 1, 2, ... on k starting at 0 it produces what
+ * qieo_run(inst, 1) produces for each generation.
+ *
+ * Working memory: the per-chromosome sums and a block counter live in one file-scope
+ * device array of 256 + 16 * QIEO_NOALLOC_MAX_NP bytes (about 1 MB) that every GPU which
+ * loads the library holds until the process exits. Every call uses that same array and
+ * clears what it needs at its start, so calls whose GPU work overlaps (two streams, or two
+ * host threads) race and give wrong results: serialise them. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture. Sizes beyond the limits return QIEO_ERR_INVALID with a message; no
+ * cudaMalloc, cudaFree or other allocating call is made. Stream-ordered: returns after
+ * enqueueing. */
+qieo_status qieo_generation_noalloc(const qieo_problem *problem, const qieo_params *params,
+                                    int32_t t, int16_t *k, uint8_t *x, int64_t *fitness,
+                                    int32_t *elite);
+
 /* Message of the last failure on this thread ("" if none). */
 const char *qieo_last_error(void);
 

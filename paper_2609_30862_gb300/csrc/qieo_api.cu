@@ -69,6 +69,11 @@ int pow2_ceil(int x)
 
 }  // namespace
 
+namespace qieo_internal {
+// Lets the library's other translation units report through qieo_last_error().
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace qieo_internal
+
 struct qieo_instance {
     int32_t np = 0, ng = 0, svec = 0, xstride = 0, K = 0, D = 0;
     int32_t rule = 0, host_de = 0, flags = 0;

@@ -37,8 +37,10 @@ EXPORTS = (
     "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
-    "qieo_last_error",
+    "qieo_generation_noalloc", "qieo_last_error",
 )
+
+QIEO_NOALLOC_MAX_NP = 65536
 
 
 class QieoError(RuntimeError):
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_set_launch_shape": ([P, P], C.c_int),
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
         "qieo_philox": ([P, P, i32], C.c_int),
+        "qieo_generation_noalloc": ([P, P, i32, P, P, P, P], C.c_int),
         "qieo_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -218,6 +221,16 @@ def qieo_philox(ctr_key) -> np.ndarray:
     out = np.zeros((ck.shape[0], 4), dtype=np.uint32)
     _check(load().qieo_philox(_ptr(ck), _ptr(out), int(ck.shape[0])))
     return out
+
+
+def qieo_generation_noalloc(d_weights: int, d_values: int, ng: int, capacity: int,
+                            params: qieo_params, t: int, d_k: int, d_x: int, d_fitness: int,
+                            d_elite: int) -> None:
+    """One generation on caller-owned device buffers (all pointer arguments are device
+    addresses, e.g. torch.Tensor.data_ptr()); allocates nothing."""
+    pr = qieo_problem(int(ng), int(d_weights), int(d_values), int(capacity))
+    _check(load().qieo_generation_noalloc(C.byref(pr), C.byref(params), int(t), int(d_k),
+                                          int(d_x), int(d_fitness), int(d_elite)))
 
 
 class Instance:
