@@ -67,8 +67,11 @@ typedef struct {
 #define QIEO_FLAG_SYNC_RUN      0x2   /* qieo_run waits (bounded) for the device */
 #define QIEO_FLAG_FORCE_WIDE    0x4   /* use 64-bit item sums even for small items */
 #define QIEO_FLAG_TIME_KERNELS  0x8   /* time the generation kernels with CUDA events */
-#define QIEO_FLAG_PER_GENERATION 0x10 /* one kernel launch per generation instead of one
-                                         cooperative launch per run */
+#define QIEO_FLAG_COOPERATIVE   0x10  /* one cooperative launch per run (a bounded grid
+                                         barrier between generations) instead of one launch
+                                         per generation */
+#define QIEO_FLAG_REGISTER_PREFETCH 0x20 /* stream the state with register prefetch instead
+                                            of asynchronous copies into shared memory */
 
 typedef struct {
     int32_t np;              /* chromosomes, >= 1 */
@@ -102,16 +105,17 @@ qieo_status qieo_reset(qieo_instance *inst);
 
 /* Runs `generations` >= 0 generations from the current one (Fig. 1: QIP, Evaluation,
  * DetermineElite, CIP, per generation; the CIP of the last generation is applied before
- * returning, so run(a) followed by run(b) equals run(a + b)). By default the whole run is
- * one cooperative kernel launch whose blocks meet at a bounded grid barrier after each
- * generation; QIEO_FLAG_PER_GENERATION (and elite_on_host) launch one kernel per
- * generation instead. Stream-ordered: returns after enqueueing unless QIEO_FLAG_SYNC_RUN
- * is set or elite_on_host is 1. A barrier wait that runs out is reported as
- * QIEO_ERR_TIMEOUT by the next call that waits for the device; the state is then
- * undefined until qieo_reset. */
+ * returning, so run(a) followed by run(b) equals run(a + b)). By default each generation
+ * is one kernel launch, chained to the next by programmatic dependent launch and replayed
+ * from a CUDA graph when a run length repeats; QIEO_FLAG_COOPERATIVE runs the whole run as
+ * one cooperative launch whose blocks meet at a bounded grid barrier after each
+ * generation. Stream-ordered: returns after enqueueing unless QIEO_FLAG_SYNC_RUN is set or
+ * elite_on_host is 1. A barrier wait that runs out is reported as QIEO_ERR_TIMEOUT by the
+ * next call that waits for the device; the state is then undefined until qieo_reset. */
 qieo_status qieo_run(qieo_instance *inst, int32_t generations);
 
-/* Bound of one grid-barrier wait inside a run, in nanoseconds (default 10 s; >= 1). */
+/* Bound of one grid-barrier wait inside a cooperative run, in nanoseconds (default 10 s;
+ * >= 1). */
 qieo_status qieo_set_wait_timeout(qieo_instance *inst, int64_t ns);
 
 /* Waits (bounded) until every operation enqueued for the instance has finished; reports

@@ -3,11 +3,11 @@
 // An instance owns one device allocation holding the qubit state, the two allele planes,
 // the items (packed and wide form), the best row, the row accumulators and counters, the
 // elite key and index, the grid-barrier words and the per-generation records. qieo_run
-// launches the whole run as one cooperative kernel (blocks meet at a bounded grid barrier
-// after each generation). The per-generation path enqueues one fused generation kernel per
-// generation plus one final CIP launch, chained with programmatic dependent launch (each
-// kernel's prologue overlaps the previous kernel's tail) and replayed from a cached CUDA
-// graph when a run length repeats. With elite_on_host it copies the fitness array to the
+// enqueues one fused generation kernel per generation plus one final CIP launch, chained
+// with programmatic dependent launch (each kernel's prologue overlaps the previous kernel's
+// tail) and replayed from a cached CUDA graph when a run length repeats; with
+// QIEO_FLAG_COOPERATIVE the whole run is one cooperative kernel whose blocks meet at a
+// bounded grid barrier after each generation. With elite_on_host it copies the fitness array to the
 // host after each generation, picks the elite there and records it with a one-block
 // kernel (the host DetermineElite variant the paper recommends, Sec. III-C, Sec. VII P4).
 #include <cuda_runtime.h>
@@ -126,28 +126,38 @@ void drop_graphs(qieo_instance *q)
     q->graphs.clear();
 }
 
-template <bool N, int R>
-const void *gen_kernel_ptr()
+// Kernel instantiation for (narrow sums, rotation rule, asynchronous-copy ring).
+template <template <bool, int, bool> class Pick>
+typename Pick<true, 0, true>::type kernel_of(const qieo_instance *q, bool ring)
 {
-    return reinterpret_cast<const void *>(&qieo::generation_kernel<N, R>);
+    if (q->narrow) {
+        if (q->rule) return ring ? Pick<true, 1, true>::get() : Pick<true, 1, false>::get();
+        return ring ? Pick<true, 0, true>::get() : Pick<true, 0, false>::get();
+    }
+    if (q->rule) return ring ? Pick<false, 1, true>::get() : Pick<false, 1, false>::get();
+    return ring ? Pick<false, 0, true>::get() : Pick<false, 0, false>::get();
 }
 
-const void *gen_kernel_of(const qieo_instance *q)
+template <bool N, int R, bool T>
+struct PickGen {
+    typedef void (*type)(qieo::GenParams);
+    static type get() { return &qieo::generation_kernel<N, R, T>; }
+};
+
+template <bool N, int R, bool T>
+struct PickRun {
+    typedef void (*type)(qieo::GenParams, int32_t);
+    static type get() { return &qieo::run_kernel<N, R, T>; }
+};
+
+const void *gen_kernel_of(const qieo_instance *q, bool ring)
 {
-    if (q->narrow) return q->rule ? gen_kernel_ptr<true, 1>() : gen_kernel_ptr<true, 0>();
-    return q->rule ? gen_kernel_ptr<false, 1>() : gen_kernel_ptr<false, 0>();
+    return reinterpret_cast<const void *>(kernel_of<PickGen>(q, ring));
 }
 
-template <bool N, int R>
-const void *run_kernel_ptr()
+const void *run_kernel_of(const qieo_instance *q, bool ring)
 {
-    return reinterpret_cast<const void *>(&qieo::run_kernel<N, R>);
-}
-
-const void *run_kernel_of(const qieo_instance *q)
-{
-    if (q->narrow) return q->rule ? run_kernel_ptr<true, 1>() : run_kernel_ptr<true, 0>();
-    return q->rule ? run_kernel_ptr<false, 1>() : run_kernel_ptr<false, 0>();
+    return reinterpret_cast<const void *>(kernel_of<PickRun>(q, ring));
 }
 
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
@@ -164,12 +174,19 @@ qieo_status configure(qieo_instance *q)
     const int64_t units = (int64_t)ntile * q->np;
     const size_t row_bytes = q->narrow ? 8 : 16;
 
+    // The state streams through the per-thread cp.async ring unless register prefetch is
+    // asked for.
+    const bool use_ring = !(q->flags & QIEO_FLAG_REGISTER_PREFETCH);
+    const size_t ring = use_ring ? qieo::kRingBytes : 0;
+
     // Blocks resident at once, for the larger of the shared-memory sizes used.
-    const size_t smem0 = (size_t)qieo::kMaxSegRows * row_bytes;
+    const size_t smem0 = ring + (size_t)qieo::kMaxSegRows * row_bytes;
+    for (const void *fn : {gen_kernel_of(q, use_ring), run_kernel_of(q, use_ring)})
+        CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0));
     int bps_gen = 0, bps_run = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_gen, gen_kernel_of(q),
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_gen, gen_kernel_of(q, use_ring),
                                                            qieo::kThreads, smem0));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_run, run_kernel_of(q),
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_run, run_kernel_of(q, use_ring),
                                                            qieo::kThreads, smem0));
     const int64_t resident = (int64_t)q->sm_count * std::max(1, std::min(bps_gen, bps_run));
     int grid = q->grid_override;
@@ -180,8 +197,9 @@ qieo_status configure(qieo_instance *q)
     const int64_t share = (units + grid - 1) / grid;
     const int seg_max = (int)std::max<int64_t>(1, std::min<int64_t>(qieo::kMaxSegRows, share));
     q->grid = grid;
-    q->smem = (size_t)seg_max * row_bytes;
+    q->smem = ring + (size_t)seg_max * row_bytes;
     q->coop = bps_run > 0 && grid <= (int64_t)q->sm_count * bps_run;
+    q->gp.ring = use_ring ? 1 : 0;
 
     qieo::GenParams &g = q->gp;
     g.items_narrow = q->items_narrow;
@@ -222,25 +240,17 @@ cudaLaunchConfig_t launch_config(const qieo_instance *q, dim3 grid, size_t smem,
     return cfg;
 }
 
-template <bool N, int R>
-cudaError_t launch_gen_t(const qieo_instance *q, const qieo::GenParams &p)
-{
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = launch_config(q, dim3(q->grid), q->smem, attr);
-    return cudaLaunchKernelEx(&cfg, qieo::generation_kernel<N, R>, p);
-}
-
 cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de)
 {
     qieo::GenParams p = q->gp;
     p.apply_cip = apply_cip;
     p.do_de = do_de;
-    if (q->narrow) return q->rule ? launch_gen_t<true, 1>(q, p) : launch_gen_t<true, 0>(q, p);
-    return q->rule ? launch_gen_t<false, 1>(q, p) : launch_gen_t<false, 0>(q, p);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = launch_config(q, dim3(q->grid), q->smem, attr);
+    return cudaLaunchKernelEx(&cfg, kernel_of<PickGen>(q, q->gp.ring != 0), p);
 }
 
-template <bool N, int R>
-cudaError_t launch_run_t(const qieo_instance *q, int32_t G)
+cudaError_t launch_run(const qieo_instance *q, int32_t G)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = {};
@@ -252,13 +262,7 @@ cudaError_t launch_run_t(const qieo_instance *q, int32_t G)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, qieo::run_kernel<N, R>, q->gp, G);
-}
-
-cudaError_t launch_run(const qieo_instance *q, int32_t G)
-{
-    if (q->narrow) return q->rule ? launch_run_t<true, 1>(q, G) : launch_run_t<true, 0>(q, G);
-    return q->rule ? launch_run_t<false, 1>(q, G) : launch_run_t<false, 0>(q, G);
+    return cudaLaunchKernelEx(&cfg, kernel_of<PickRun>(q, q->gp.ring != 0), q->gp, G);
 }
 
 cudaError_t launch_final_cip(const qieo_instance *q)
@@ -365,7 +369,7 @@ qieo_status run_cooperative(qieo_instance *q, int32_t G)
 
 qieo_status run_device(qieo_instance *q, int32_t G)
 {
-    if (q->coop && !(q->flags & QIEO_FLAG_PER_GENERATION)) return run_cooperative(q, G);
+    if (q->coop && (q->flags & QIEO_FLAG_COOPERATIVE)) return run_cooperative(q, G);
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
     if ((q->flags & QIEO_FLAG_NO_GRAPH) || (first_time && !q->graphs.count(G))) {

@@ -129,6 +129,7 @@ struct GenParams {
     int32_t np, svec, xstride, K, ntile;
     int32_t lanes, warps, seg_rows_max, key_mode;
     int32_t apply_cip, do_de;
+    int32_t ring;                 // 1: state streamed through the per-thread cp.async ring
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -289,12 +290,165 @@ __device__ __forceinline__ void segment_sum(const GenParams &p, uint32_t &accn, 
     }
 }
 
+// Per-segment constants of one thread: its vector of a tile, the 8 items of that vector
+// and the elite alleles of the previous generation for it.
+struct SegCtx {
+    uint32_t wv[8];               // narrow items (v << 16 | w)
+    int32_t wi[8], vi[8];         // wide items
+    uint32_t e8;                  // elite alleles of the previous generation (8 genes)
+    uint32_t ctr0;                // Philox counter word 0 of the first 4 genes
+    int vec;
+    bool active;                  // vec < svec
+};
+
+template <bool kNarrow, bool kCip>
+__device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int tile, int v_in,
+                                          int tile_vecs, const uint8_t *elite_row)
+{
+    g.vec = tile * tile_vecs + v_in;
+    g.active = g.vec < p.svec;
+    if (kNarrow) {
+        uint4 a = make_uint4(0, 0, 0, 0), c = a;
+        if (g.active) {
+            a = __ldg(p.items_narrow + 2 * (size_t)g.vec);
+            c = __ldg(p.items_narrow + 2 * (size_t)g.vec + 1);
+        }
+        g.wv[0] = a.x; g.wv[1] = a.y; g.wv[2] = a.z; g.wv[3] = a.w;
+        g.wv[4] = c.x; g.wv[5] = c.y; g.wv[6] = c.z; g.wv[7] = c.w;
+    } else {
+        int4 a = make_int4(0, 0, 0, 0), c = a, d = a, e = a;
+        if (g.active) {
+            a = __ldg(p.w4 + 2 * (size_t)g.vec);
+            c = __ldg(p.w4 + 2 * (size_t)g.vec + 1);
+            d = __ldg(p.v4 + 2 * (size_t)g.vec);
+            e = __ldg(p.v4 + 2 * (size_t)g.vec + 1);
+        }
+        g.wi[0] = a.x; g.wi[1] = a.y; g.wi[2] = a.z; g.wi[3] = a.w;
+        g.wi[4] = c.x; g.wi[5] = c.y; g.wi[6] = c.z; g.wi[7] = c.w;
+        g.vi[0] = d.x; g.vi[1] = d.y; g.vi[2] = d.z; g.vi[3] = d.w;
+        g.vi[4] = e.x; g.vi[5] = e.y; g.vi[6] = e.z; g.vi[7] = e.w;
+    }
+    g.e8 = (kCip && g.active) ? (uint32_t)__ldcg(elite_row + g.vec) : 0u;
+    g.ctr0 = 2u * (uint32_t)g.vec;
+}
+
+// One vector of one row: CIP(t-1), QIP(t), the row's partial sums, stores. Returns the
+// packed or wide sums through accn / acw, acv (before the segment reduction).
+template <bool kNarrow, int kRule, bool kCip>
+__device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const SegCtx &g, uint4 s,
+                                            uint32_t xo, int32_t c, int32_t t,
+                                            const unsigned char *thr_bytes, bool &check,
+                                            int &countdown, uint32_t &xbits, uint32_t &accn,
+                                            int64_t &acw, int64_t &acv)
+{
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    const uint32_t off_top = (uint32_t)(8 * p.K);
+    if (kCip) s = rotate_vec(s, g.e8, kRule == 1 ? (g.e8 ^ xo) : 0xffu, k8);
+    const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
+    xbits = 0u;
+    accn = 0u;
+    acw = 0;
+    acv = 0;
+
+    // A qubit at theta = 0 or pi/2 (n = 0 or 2K) has a fixed allele (T = 0 or 2^32), so
+    // when every qubit of the pass in the whole warp is there, no draw can change anything
+    // and the Philox calls are not needed. The test is skipped for 15 passes after it
+    // fails, which keeps its cost low while the population is still spread out.
+    bool sat = false;
+    if (countdown == 0) {
+        uint32_t z = 0u;   // per half h in [0, 8K]: min(h, 8K - h) == 0 iff h is 0 or 8K
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z |= __vminu2(sp[q], k8 - sp[q]);
+        sat = __all_sync(0xffffffffu, z == 0u);
+        if (!sat) countdown = 15;
+    } else {
+        --countdown;
+    }
+    (void)check;
+    if (sat) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
+            if (off != 0u) {
+                xbits |= 1u << i;
+                if (kNarrow) {
+                    accn += g.wv[i];
+                } else {
+                    acw += g.wi[i];
+                    acv += g.vi[i];
+                }
+            }
+        }
+    } else {
+        const Draw4 r0 = philox4x32_10_rk(g.ctr0, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r1 = philox4x32_10_rk(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
+            const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+            const bool x = (u[i] < thr) || (off == off_top);
+            if (x) {
+                xbits |= 1u << i;
+                if (kNarrow) {
+                    accn += g.wv[i];
+                } else {
+                    acw += g.wi[i];
+                    acv += g.vi[i];
+                }
+            }
+        }
+    }
+    return s;
+}
+
+template <bool kNarrow>
+__device__ __forceinline__ void add_row_sums(const GenParams &p, bool leader, bool ok, int rr,
+                                             uint32_t accn, int64_t acw, int64_t acv,
+                                             uint32_t *s_acc32, unsigned long long *s_acc64)
+{
+    uint32_t a = accn;
+    int64_t w = acw, v = acv;
+    segment_sum<kNarrow>(p, a, w, v);
+    if (ok && leader) {
+        if (kNarrow) {
+            atomicAdd(s_acc32 + 2 * rr, a & 0xffffu);
+            atomicAdd(s_acc32 + 2 * rr + 1, a >> 16);
+        } else {
+            atomicAdd(s_acc64 + 2 * rr, (unsigned long long)w);
+            atomicAdd(s_acc64 + 2 * rr + 1, (unsigned long long)v);
+        }
+    }
+}
+
+// Adds the block's tile-row sums of a segment to the rows (one atomic per tile-row) and
+// clears the shared accumulators. Called by the whole block.
+template <bool kNarrow>
+__device__ __forceinline__ void flush_segment(const GenParams &p, int ra, int seg_rows,
+                                              uint32_t *s_acc32, unsigned long long *s_acc64)
+{
+    __syncthreads();
+    for (int i = threadIdx.x; i < seg_rows; i += kThreads) {
+        if (kNarrow) {
+            combine_row<true>(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1]);
+            s_acc32[2 * i] = 0u;
+            s_acc32[2 * i + 1] = 0u;
+        } else {
+            combine_row<false>(p, ra + i, s_acc64[2 * i], s_acc64[2 * i + 1]);
+            s_acc64[2 * i] = 0ull;
+            s_acc64[2 * i + 1] = 0ull;
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------------
-// One generation over this block's share. Thread (r_sub, v_in) handles vector v_in of rows
-// r_sub, r_sub + rows_per_pass, ... of each tile segment; its 8 items stay in registers
-// for the whole segment, and the state of the next two rows is in flight while a row is
-// computed. Row sums are reduced over the lanes of a segment in the warp, over the warps
-// of a tile in shared memory, and over tiles by one atomic per tile-row.
+// One generation over this block's share, register-prefetch form (any tile shape).
+// Thread (r_sub, v_in) handles vector v_in of rows r_sub, r_sub + rows_per_pass, ... of
+// each tile segment; its 8 items stay in registers for the whole segment, and the state of
+// the next two rows is in flight while a row is computed. Row sums are reduced over the
+// lanes of a segment in the warp, over the warps of a tile in shared memory, and over tiles
+// by one atomic per tile-row.
 // ---------------------------------------------------------------------------------------
 template <bool kNarrow, int kRule, bool kCip>
 __device__ __forceinline__ void generation_body(const GenParams &p, const BlockShare &b,
@@ -306,9 +460,15 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
     const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
     uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
     const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
-    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
-    const uint32_t off_top = (uint32_t)(8 * p.K);
     const int rpp = b.rows_per_pass;
+    int countdown = 0;
+    bool check = true;
+
+    for (int i = threadIdx.x; i < 2 * p.seg_rows_max; i += kThreads) {
+        if (kNarrow) s_acc32[i] = 0u;
+        else s_acc64[i] = 0ull;
+    }
+    __syncthreads();
 
     for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
         const int tile = (int)(u0 / p.np);
@@ -317,109 +477,43 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
         u0 += seg_rows;
         const int passes = (seg_rows + rpp - 1) / rpp;
 
-        const int vec = tile * b.tile_vecs + b.v_in;
-        const bool active = vec < p.svec;
+        SegCtx g;
+        seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
         const size_t row0 = (size_t)ra + b.r_sub;
-        uint4 *sptr = p.state + row0 * p.svec + vec;
+        uint4 *sptr = p.state + row0 * p.svec + g.vec;
         const size_t sstep = (size_t)rpp * p.svec;
-        uint8_t *xptr = x_cur + row0 * p.xstride + vec;
-        const uint8_t *xoptr = x_prev + row0 * p.xstride + vec;
+        uint8_t *xptr = x_cur + row0 * p.xstride + g.vec;
+        const uint8_t *xoptr = x_prev + row0 * p.xstride + g.vec;
         const size_t xstep = (size_t)rpp * p.xstride;
 
         auto row_ok = [&](int pass) { return pass * rpp + b.r_sub < seg_rows; };
         auto load_state = [&](int pass) -> uint4 {
-            uint4 s = make_uint4(0, 0, 0, 0);
-            if (active && row_ok(pass)) s = sptr[(size_t)pass * sstep];
-            return s;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (g.active && row_ok(pass)) v = sptr[(size_t)pass * sstep];
+            return v;
         };
         auto load_xold = [&](int pass) -> uint32_t {
             if (kRule != 1 || !kCip) return 0u;
-            if (!(active && row_ok(pass))) return 0u;
+            if (!(g.active && row_ok(pass))) return 0u;
             return (uint32_t)xoptr[(size_t)pass * xstep];
         };
-
-        // Two rows in flight before anything else is waited on.
-        uint4 sa = load_state(0), sb = load_state(1), sc;
-        uint32_t xa = load_xold(0), xb1 = load_xold(1), xc = 0u;
-
-        uint32_t wv[8];
-        int32_t wi[8], vi[8];
-        if (kNarrow) {
-            uint4 a = make_uint4(0, 0, 0, 0), c = a;
-            if (active) {
-                a = __ldg(p.items_narrow + 2 * (size_t)vec);
-                c = __ldg(p.items_narrow + 2 * (size_t)vec + 1);
-            }
-            wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
-            wv[4] = c.x; wv[5] = c.y; wv[6] = c.z; wv[7] = c.w;
-        } else {
-            int4 a = make_int4(0, 0, 0, 0), c = a, d = a, e = a;
-            if (active) {
-                a = __ldg(p.w4 + 2 * (size_t)vec);
-                c = __ldg(p.w4 + 2 * (size_t)vec + 1);
-                d = __ldg(p.v4 + 2 * (size_t)vec);
-                e = __ldg(p.v4 + 2 * (size_t)vec + 1);
-            }
-            wi[0] = a.x; wi[1] = a.y; wi[2] = a.z; wi[3] = a.w;
-            wi[4] = c.x; wi[5] = c.y; wi[6] = c.z; wi[7] = c.w;
-            vi[0] = d.x; vi[1] = d.y; vi[2] = d.z; vi[3] = d.w;
-            vi[4] = e.x; vi[5] = e.y; vi[6] = e.z; vi[7] = e.w;
-        }
-        const uint32_t e8 = (kCip && active) ? (uint32_t)__ldcg(elite_row + vec) : 0u;
-        const uint32_t ctr0 = 2u * (uint32_t)vec;
-
-        for (int i = threadIdx.x; i < 2 * seg_rows; i += kThreads) {
-            if (kNarrow) s_acc32[i] = 0u;
-            else s_acc64[i] = 0ull;
-        }
-        __syncthreads();
-
-        auto process = [&](uint4 s, uint32_t xo, int pass) {
+        auto process = [&](uint4 sv, uint32_t xo, int pass) {
             const int rr = pass * rpp + b.r_sub;
             const bool ok = rr < seg_rows;
-            const int c = ra + rr;
-            if (kCip) s = rotate_vec(s, e8, kRule == 1 ? (e8 ^ xo) : 0xffu, k8);
-
-            const Draw4 r0 = philox4x32_10_rk(ctr0, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
-            const Draw4 r1 = philox4x32_10_rk(ctr0 + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
-            const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
-            const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
-
-            uint32_t xbits = 0u;
-            uint32_t accn = 0u;
-            int64_t acw = 0, acv = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
-                const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
-                const bool x = (u[i] < thr) || (off == off_top);
-                if (x) {
-                    xbits |= 1u << i;
-                    if (kNarrow) {
-                        accn += wv[i];
-                    } else {
-                        acw += wi[i];
-                        acv += vi[i];
-                    }
-                }
-            }
-            if (active && ok) {
-                sptr[(size_t)pass * sstep] = s;
+            uint32_t xbits, accn;
+            int64_t acw, acv;
+            sv = qubit_pass<kNarrow, kRule, kCip>(p, g, sv, xo, ra + rr, t, thr_bytes, check,
+                                                  countdown, xbits, accn, acw, acv);
+            if (g.active && ok) {
+                sptr[(size_t)pass * sstep] = sv;
                 xptr[(size_t)pass * xstep] = (uint8_t)xbits;
             }
-            segment_sum<kNarrow>(p, accn, acw, acv);
-            if (ok && b.leader) {
-                if (kNarrow) {
-                    atomicAdd(s_acc32 + 2 * rr, accn & 0xffffu);
-                    atomicAdd(s_acc32 + 2 * rr + 1, accn >> 16);
-                } else {
-                    atomicAdd(s_acc64 + 2 * rr, (unsigned long long)acw);
-                    atomicAdd(s_acc64 + 2 * rr + 1, (unsigned long long)acv);
-                }
-            }
+            add_row_sums<kNarrow>(p, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
         };
 
         // Three state buffers in rotation: two rows in flight while one is computed.
+        uint4 sa = load_state(0), sb = load_state(1), sc;
+        uint32_t xa = load_xold(0), xb1 = load_xold(1), xc = 0u;
         for (int pass = 0; pass < passes; pass += 3) {
             sc = load_state(pass + 2);
             xc = load_xold(pass + 2);
@@ -433,14 +527,133 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
             xb1 = load_xold(pass + 4);
             process(sc, xc, pass + 2);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < seg_rows; i += kThreads) {
-            if (kNarrow)
-                combine_row<true>(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1]);
-            else
-                combine_row<false>(p, ra + i, s_acc64[2 * i], s_acc64[2 * i + 1]);
+        flush_segment<kNarrow>(p, ra, seg_rows, s_acc32, s_acc64);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Asynchronous-copy form (any tile shape). Each thread streams its own 16-byte vectors
+// through a private ring of kRingStages shared-memory slots with cp.async: the copy for
+// pass P + kRingStages - 1 is issued before pass P is computed and the thread waits only
+// for its own copy groups, so kRingStages - 1 rows per thread are in flight without
+// registers and without any block-wide synchronisation.
+// ---------------------------------------------------------------------------------------
+constexpr int kRingStages = 8;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+// 16-byte global->shared copy; src_bytes = 0 writes zeros (nothing is read).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+
+template <bool kNarrow, int kRule, bool kCip>
+__device__ __forceinline__ void generation_body_ring(const GenParams &p, const BlockShare &b,
+                                                     int32_t t, int32_t e_prev, uint4 *ring,
+                                                     const uint32_t *s_thr, uint32_t *s_acc32,
+                                                     unsigned long long *s_acc64)
+{
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+    uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
+    const int rpp = b.rows_per_pass;
+    uint4 *slots = ring + threadIdx.x;           // slot s of this thread: slots[s * kThreads]
+    int countdown = 0;
+    bool check = true;
+
+    for (int i = threadIdx.x; i < 2 * p.seg_rows_max; i += kThreads) {
+        if (kNarrow) s_acc32[i] = 0u;
+        else s_acc64[i] = 0ull;
+    }
+    __syncthreads();
+
+    for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
+        const int tile = (int)(u0 / p.np);
+        const int ra = (int)(u0 - (int64_t)tile * p.np);
+        const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
+        u0 += seg_rows;
+        const int passes = (seg_rows + rpp - 1) / rpp;
+
+        SegCtx g;
+        seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
+        const size_t row0 = (size_t)ra + b.r_sub;
+        uint4 *sptr = p.state + row0 * p.svec + g.vec;
+        const size_t sstep = (size_t)rpp * p.svec;
+        uint8_t *xptr = x_cur + row0 * p.xstride + g.vec;
+        const uint8_t *xoptr = x_prev + row0 * p.xstride + g.vec;
+        const size_t xstep = (size_t)rpp * p.xstride;
+
+        // Incremental addressing (no multiplies in the pass loop): the copy cursor runs
+        // kRingStages - 1 rows ahead of the compute cursor.
+        const uint4 *ld_ptr = sptr;                 // next row to copy
+        int ld_rr = b.r_sub;                        // its row within the segment
+        uint32_t ld_slot = 0;                       // its slot
+        uint4 *st_ptr = sptr;                       // row being computed
+        uint8_t *xst_ptr = xptr;
+        const uint8_t *xo_ptr = xoptr;
+        int rr = b.r_sub;
+        uint32_t slot = 0;
+        auto issue = [&]() {
+            const bool v = g.active && ld_rr < seg_rows;
+            cp_async16(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
+                       v ? 16u : 0u);
+            cp_async_commit();
+            ld_ptr += sstep;
+            ld_rr += rpp;
+            ld_slot = (ld_slot + 1) & (kRingStages - 1);
+        };
+        auto load_xold = [&](const uint8_t *ptr, int r) -> uint32_t {
+            if (kRule != 1 || !kCip) return 0u;
+            if (!(g.active && r < seg_rows)) return 0u;
+            return (uint32_t)*ptr;
+        };
+
+#pragma unroll
+        for (int k = 0; k < kRingStages - 1; ++k) issue();
+        uint32_t xa = load_xold(xo_ptr, rr), xb1 = load_xold(xo_ptr + xstep, rr + rpp);
+        for (int pass = 0; pass < passes; ++pass) {
+            issue();
+            const uint32_t xo = xa;
+            xa = xb1;
+            xb1 = load_xold(xo_ptr + 2 * xstep, rr + 2 * rpp);
+            xo_ptr += xstep;
+            cp_async_wait<kRingStages - 1>();
+            uint4 sv = slots[(size_t)slot * kThreads];
+            slot = (slot + 1) & (kRingStages - 1);
+
+            const bool ok = rr < seg_rows;
+            uint32_t xbits, accn;
+            int64_t acw, acv;
+            sv = qubit_pass<kNarrow, kRule, kCip>(p, g, sv, xo, ra + rr, t, thr_bytes, check,
+                                                  countdown, xbits, accn, acw, acv);
+            if (g.active && ok) {
+                *st_ptr = sv;
+                *xst_ptr = (uint8_t)xbits;
+            }
+            add_row_sums<kNarrow>(p, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
+            st_ptr += sstep;
+            xst_ptr += xstep;
+            rr += rpp;
         }
-        __syncthreads();
+        cp_async_wait<0>();
+        flush_segment<kNarrow>(p, ra, seg_rows, s_acc32, s_acc64);
     }
 }
 
@@ -460,11 +673,25 @@ __device__ __forceinline__ void final_cip_body(const GenParams &p, const BlockSh
         const int vec = tile * b.tile_vecs + b.v_in;
         if (vec >= p.svec) continue;
         const uint32_t e8 = __ldcg(elite_row + vec);
-        for (int rr = b.r_sub; rr < seg_rows; rr += b.rows_per_pass) {
-            const size_t c = (size_t)ra + rr;
-            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
-            uint4 *sp = p.state + c * p.svec + vec;
-            *sp = rotate_vec(*sp, e8, m8, k8);
+        // four rows per step, loads first
+        for (int rr = b.r_sub; rr < seg_rows; rr += 4 * b.rows_per_pass) {
+            uint4 v[4];
+            uint32_t m8[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r2 = rr + k * b.rows_per_pass;
+                if (r2 < seg_rows) {
+                    const size_t c = (size_t)ra + r2;
+                    v[k] = p.state[c * p.svec + vec];
+                    m8[k] = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r2 = rr + k * b.rows_per_pass;
+                if (r2 < seg_rows)
+                    p.state[((size_t)ra + r2) * p.svec + vec] = rotate_vec(v[k], e8, m8[k], k8);
+            }
         }
     }
 }
@@ -509,27 +736,57 @@ __device__ __forceinline__ bool generation_barrier(const GenParams &p, int32_t t
     return s_flag != 0;
 }
 
+// Dynamic shared memory: [per-thread copy ring (kRingStages x kThreads x 16 B)] when the
+// asynchronous-copy form is used, then the per-row sums of a segment.
+constexpr size_t kRingBytes = (size_t)kRingStages * kThreads * 16;
+
+struct SmemParts {
+    uint4 *ring;
+    uint32_t *acc32;
+    unsigned long long *acc64;
+};
+
+template <bool kRing>
+__device__ __forceinline__ SmemParts carve_smem(unsigned char *raw)
+{
+    SmemParts m;
+    m.ring = reinterpret_cast<uint4 *>(raw);
+    unsigned char *acc = raw + (kRing ? kRingBytes : 0);
+    m.acc32 = reinterpret_cast<uint32_t *>(acc);
+    m.acc64 = reinterpret_cast<unsigned long long *>(acc);
+    return m;
+}
+
+template <bool kNarrow, int kRule, bool kCip, bool kRing>
+__device__ __forceinline__ void one_generation(const GenParams &p, const BlockShare &b, int32_t t,
+                                               int32_t e_prev, SmemParts &m, const uint32_t *s_thr)
+{
+    if (kRing)
+        generation_body_ring<kNarrow, kRule, kCip>(p, b, t, e_prev, m.ring, s_thr, m.acc32, m.acc64);
+    else
+        generation_body<kNarrow, kRule, kCip>(p, b, t, e_prev, s_thr, m.acc32, m.acc64);
+}
+
 // ---------------------------------------------------------------------------------------
 // run_kernel: generations t0 .. t0+G-1 and the final CIP in one cooperative launch. The
 // first generation applies no CIP (a run starts from a rotated state or from t = 0).
 // ---------------------------------------------------------------------------------------
-template <bool kNarrow, int kRule>
-__global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) run_kernel(const GenParams p, int32_t G)
+template <bool kNarrow, int kRule, bool kRing>
+__global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_kernel(const GenParams p, int32_t G)
 {
     __shared__ uint32_t s_thr[kMaxThr];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *s_acc64 = reinterpret_cast<unsigned long long *>(smem_raw);
-    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(smem_raw);
-
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemParts m = carve_smem<kRing>(smem_raw);
     load_thresholds(p, s_thr);
     grid_dependency_wait();
+    __syncthreads();
     const BlockShare b = block_share(p);
     const int32_t t0 = *p.gen;
     int32_t e = 0;
     for (int32_t g = 0; g < G; ++g) {
         const int32_t t = t0 + g;
-        if (g == 0) generation_body<kNarrow, kRule, false>(p, b, t, 0, s_thr, s_acc32, s_acc64);
-        else generation_body<kNarrow, kRule, true>(p, b, t, e, s_thr, s_acc32, s_acc64);
+        if (g == 0) one_generation<kNarrow, kRule, false, kRing>(p, b, t, 0, m, s_thr);
+        else one_generation<kNarrow, kRule, true, kRing>(p, b, t, e, m, s_thr);
         if (!generation_barrier(p, t)) return;
         e = __ldcg(p.elite_idx);
     }
@@ -540,22 +797,21 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) run_kernel(const Ge
 // generation_kernel: one generation per launch. The last block to finish closes the
 // generation (no block waits for another).
 // ---------------------------------------------------------------------------------------
-template <bool kNarrow, int kRule>
-__global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) generation_kernel(const GenParams p)
+template <bool kNarrow, int kRule, bool kRing>
+__global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) generation_kernel(const GenParams p)
 {
     __shared__ uint32_t s_thr[kMaxThr];
     __shared__ int s_last;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *s_acc64 = reinterpret_cast<unsigned long long *>(smem_raw);
-    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(smem_raw);
-
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemParts m = carve_smem<kRing>(smem_raw);
     load_thresholds(p, s_thr);
     grid_dependency_wait();
+    __syncthreads();
     const BlockShare b = block_share(p);
     const int32_t t = *p.gen;
     const int32_t e_prev = *p.elite_idx;
-    if (p.apply_cip) generation_body<kNarrow, kRule, true>(p, b, t, e_prev, s_thr, s_acc32, s_acc64);
-    else generation_body<kNarrow, kRule, false>(p, b, t, e_prev, s_thr, s_acc32, s_acc64);
+    if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing>(p, b, t, e_prev, m, s_thr);
+    else one_generation<kNarrow, kRule, false, kRing>(p, b, t, e_prev, m, s_thr);
 
     // The next generation's blocks may start their prologue now.
     allow_dependent_launch();

@@ -28,7 +28,8 @@ QIEO_FLAG_NO_GRAPH = 0x1
 QIEO_FLAG_SYNC_RUN = 0x2
 QIEO_FLAG_FORCE_WIDE = 0x4
 QIEO_FLAG_TIME_KERNELS = 0x8
-QIEO_FLAG_PER_GENERATION = 0x10
+QIEO_FLAG_COOPERATIVE = 0x10
+QIEO_FLAG_REGISTER_PREFETCH = 0x20
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (

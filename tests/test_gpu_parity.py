@@ -78,17 +78,20 @@ def test_c1_rule_r2():
 
 
 @pytest.mark.parametrize("flags", [Q.QIEO_FLAG_NO_GRAPH, Q.QIEO_FLAG_FORCE_WIDE,
-                                   Q.QIEO_FLAG_SYNC_RUN | Q.QIEO_FLAG_TIME_KERNELS])
+                                   Q.QIEO_FLAG_SYNC_RUN | Q.QIEO_FLAG_TIME_KERNELS,
+                                   Q.QIEO_FLAG_COOPERATIVE | Q.QIEO_FLAG_FORCE_WIDE])
 def test_flags_do_not_change_results(flags):
     compare(W.knapsack(700, 5), 48, [60], seed=5, rule=0, flags=flags)
 
 
 @pytest.mark.parametrize("rule", [0, 1])
-def test_per_generation_launches(rule):
-    """One kernel per generation (programmatic dependent launch, graph replay on repeated
-    run lengths) gives the same results as the one cooperative launch per run."""
+def test_cooperative_launch(rule):
+    """One cooperative launch per run (grid barrier between generations) gives the same
+    results as one launch per generation."""
     compare(W.knapsack(2500, 15), 60, [7, 7, 7, 4], seed=15, rule=rule,
-            flags=Q.QIEO_FLAG_PER_GENERATION)
+            flags=Q.QIEO_FLAG_COOPERATIVE)
+    compare(W.knapsack(2500, 15), 60, [7, 7], seed=15, rule=rule,
+            flags=Q.QIEO_FLAG_COOPERATIVE | Q.QIEO_FLAG_REGISTER_PREFETCH)
 
 
 @pytest.mark.parametrize("rule", [0, 1])
@@ -119,6 +122,26 @@ def test_launch_shape_independence(shape):
     """Results do not depend on the block shape: integer sums are exact and every draw is
     keyed by (gene, chromosome, generation), not by thread."""
     compare(W.knapsack(1500, 4), 70, [15], seed=4, shape=shape)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_async_ring_and_register_streaming_agree(rule):
+    """The state streams through the per-thread cp.async ring by default and through
+    register prefetch with QIEO_FLAG_REGISTER_PREFETCH. Both equal the oracle (also across
+    run boundaries and with one launch per generation)."""
+    prob = W.knapsack(5000, 17)
+    compare(prob, 90, [9, 9, 5], seed=17, rule=rule)
+    compare(prob, 90, [9, 9, 5], seed=17, rule=rule, flags=Q.QIEO_FLAG_REGISTER_PREFETCH)
+    compare(prob, 90, [6, 4], seed=17, rule=rule, flags=Q.QIEO_FLAG_COOPERATIVE)
+
+
+def test_long_shares_split_into_segments():
+    """Two blocks over 6000 rows x 2 tiles: each block's share crosses a tile boundary and
+    exceeds the 2048 tile-rows its shared memory sums at once."""
+    prob = W.knapsack(2050, 18)
+    shape = compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2))
+    assert shape.tiles == 2 and shape.rows_per_cta == 2048
+    compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2), flags=Q.QIEO_FLAG_REGISTER_PREFETCH)
 
 
 def test_wide_items_and_penalty():
@@ -207,7 +230,7 @@ def test_barrier_wait_timeout_is_reported():
     hang); after qieo_reset the instance runs correctly again."""
     from oracle import oracle as O
     prob = W.knapsack(6000, 16)
-    with Q.Instance(prob, 300, seed=16) as I:
+    with Q.Instance(prob, 300, seed=16, flags=Q.QIEO_FLAG_COOPERATIVE) as I:
         assert I.shape().grid_ctas > 1
         I.set_wait_timeout(1)
         I.run(5)
