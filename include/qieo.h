@@ -165,6 +165,36 @@ qieo_status qieo_set_launch_shape(qieo_instance *inst, const qieo_launch_shape *
  * number of generation-kernel launches it covers; qieo_reset clears neither. */
 qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launches);
 
+/* A batch: many instances advanced together, one persistent kernel launch per generation
+ * for all of them (survey-level "batching" of independent QIEO solves; the paper runs one
+ * problem at a time). The instances keep their own state, records and generation
+ * counters; qieo_batch_run(b, G) is equivalent to qieo_run(inst, G) on every member, bit for
+ * bit. The work of a generation (every member's tiles of rows) is cut into segments
+ * balanced over a grid of one block per resident slot; members are grouped by item-sum
+ * form and rotation rule, one launch per group and generation. Members must live on one
+ * device, must not use elite_on_host and must not be destroyed while the batch exists. */
+typedef struct qieo_batch qieo_batch;
+
+/* Creates a batch over instances[0 .. n-1] (n >= 1, distinct). The batch runs on the stream
+ * of instances[0]; it waits for work already enqueued on the members' streams and the
+ * members' streams wait for the batch's work. Uses each member's current launch shape. */
+qieo_status qieo_create_batch(qieo_instance *const *instances, int32_t n, qieo_batch **out);
+
+/* Runs `generations` >= 0 generations of every member (each from its own current
+ * generation, including the final CIP of the run). Stream-ordered. */
+qieo_status qieo_batch_run(qieo_batch *batch, int32_t generations);
+
+/* Frees the batch (not its members). NULL is accepted. */
+qieo_status qieo_destroy_batch(qieo_batch *batch);
+
+/* Picks the launch shape (tile of lanes x warps vectors) of an instance at generation 0 by
+ * timing `trial_generations` generations of each candidate shape, keeps the fastest, and
+ * records it in a process-wide table keyed by (ng, np, D, rule, sum form) so that
+ * instances created later with the same key start with it. The instance is left at
+ * generation 0 (qieo_reset). Results never depend on the shape. *shape_out may be NULL. */
+qieo_status qieo_autotune(qieo_instance *inst, int32_t trial_generations,
+                          qieo_launch_shape *shape_out);
+
 /* Philox4x32-10 on the device for n (counter, key) pairs: ctr_key is n*6 host uint32
  * (c0 c1 c2 c3 k0 k1), out is n*4 host uint32. Uses the library's default stream. */
 qieo_status qieo_philox(const uint32_t *ctr_key, uint32_t *out, int32_t n);

@@ -21,6 +21,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <thread>
@@ -73,6 +75,21 @@ namespace qieo_internal {
 // Lets the library's other translation units report through qieo_last_error().
 void set_last_error(const char *msg) { g_last_error = msg; }
 }  // namespace qieo_internal
+
+namespace {
+
+// Launch shapes chosen by qieo_autotune, keyed by (ng, np, D, rule, narrow items).
+struct TuneKey {
+    int32_t ng, np, D, rule, narrow;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(ng, np, D, rule, narrow) < std::tie(o.ng, o.np, o.D, o.rule, o.narrow);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int32_t, int32_t>> g_tuned;   // -> (lanes, warps)
+
+}  // namespace
 
 struct qieo_instance {
     int32_t np = 0, ng = 0, svec = 0, xstride = 0, K = 0, D = 0;
@@ -639,6 +656,14 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
         if (ce != cudaSuccess) return bail(fail(QIEO_ERR_OOM, "pinned host buffer: %s", cudaGetErrorString(ce)));
     }
     default_tile(q);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(TuneKey{q->ng, q->np, q->D, q->rule, q->narrow_items ? 1 : 0});
+        if (it != g_tuned.end()) {
+            q->lanes = it->second.first;
+            q->warps = it->second.second;
+        }
+    }
     qieo_status st = configure(q);
     if (st != QIEO_OK) return bail(st);
     st = ensure_history(q, 1024);
@@ -887,6 +912,396 @@ qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches
     if (st != QIEO_OK) return st;
     if (ms) *ms = q->kernel_ms;
     if (launches) *launches = q->kernel_launches;
+    return QIEO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------------------
+struct qieo_batch {
+    struct Group {
+        bool narrow = false;
+        int32_t rule = 0;
+        std::vector<qieo_instance *> members;
+        int32_t grid = 1;
+        size_t smem = 0;
+        int32_t seg_rows_max = 1;
+        void *dev = nullptr;                        // params | segs | block_begin | inst_segs
+        std::vector<qieo::GenParams> host_params;   // what is on the device
+        qieo::BatchArgs args{};
+    };
+    std::vector<qieo_instance *> members;
+    std::vector<Group> groups;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> other_streams;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::map<int32_t, cudaGraphExec_t> graphs;
+    std::map<int32_t, int32_t> run_lengths_seen;
+};
+
+namespace {
+
+void drop_batch_graphs(qieo_batch *b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+template <bool N, int R, bool C>
+struct PickBatch {
+    static void (*get())(qieo::BatchArgs) { return &qieo::batch_generation_kernel<N, R, C>; }
+};
+
+void (*batch_kernel_of(bool narrow, int rule, bool cip))(qieo::BatchArgs)
+{
+    if (narrow) {
+        if (rule) return cip ? PickBatch<true, 1, true>::get() : PickBatch<true, 1, false>::get();
+        return cip ? PickBatch<true, 0, true>::get() : PickBatch<true, 0, false>::get();
+    }
+    if (rule) return cip ? PickBatch<false, 1, true>::get() : PickBatch<false, 1, false>::get();
+    return cip ? PickBatch<false, 0, true>::get() : PickBatch<false, 0, false>::get();
+}
+
+// Cuts the members' tile-rows into segments and deals them to `grid` blocks by cost
+// (active vectors per row plus a fixed per-row and per-segment overhead).
+void partition(const std::vector<qieo_instance *> &members, int grid,
+               std::vector<qieo::BatchSeg> &segs, std::vector<int32_t> &block_begin,
+               std::vector<int32_t> &inst_segs, int32_t &seg_rows_max)
+{
+    struct Piece {
+        int32_t inst, tile, rows, np_rows, rpp;
+        double row_cost;
+    };
+    std::vector<Piece> pieces;
+    double total = 0.0;
+    for (size_t i = 0; i < members.size(); ++i) {
+        const qieo_instance *q = members[i];
+        const int tv = q->lanes * q->warps;
+        const int ntile = (q->svec + tv - 1) / tv;
+        const int rpp = qieo::kThreads / tv;
+        for (int tile = 0; tile < ntile; ++tile) {
+            const int active = std::min(tv, q->svec - tile * tv);
+            // one pass covers rpp rows; its cost is the block's 256 thread-slots
+            const double pass_cost = (double)qieo::kThreads * (0.25 + 0.75 * (double)active / tv);
+            const double row_cost = pass_cost / rpp;
+            pieces.push_back({(int32_t)i, tile, q->np, q->np, rpp, row_cost});
+            total += row_cost * q->np + 2048.0;
+        }
+    }
+    // Greedy packing of the pieces in order into blocks of at most `quota` cost (a segment
+    // costs its rows plus a fixed overhead); the smallest quota that fits the grid is found
+    // by bisection.
+    const double seg_overhead = 2048.0;
+    auto pack = [&](double quota, bool emit) -> int64_t {
+        int64_t blk = 0;
+        double used = 0.0;
+        if (emit) {
+            segs.clear();
+            block_begin.assign((size_t)grid + 1, 0);
+            inst_segs.assign(members.size(), 0);
+            seg_rows_max = 1;
+        }
+        for (const Piece &pc : pieces) {
+            int32_t ra = 0;
+            while (ra < pc.np_rows) {
+                int64_t fit = (int64_t)std::max(0.0, (quota - used - seg_overhead) / pc.row_cost);
+                fit = fit / pc.rpp * pc.rpp;
+                if (fit < pc.rpp && used > 0.0) {       // this block is full
+                    ++blk;
+                    if (emit && blk <= grid) block_begin[(size_t)blk] = (int32_t)segs.size();
+                    used = 0.0;
+                    continue;
+                }
+                int32_t rows = (int32_t)std::min<int64_t>(pc.np_rows - ra, std::max<int64_t>(fit, pc.rpp));
+                rows = std::min(rows, qieo::kMaxSegRows / pc.rpp * pc.rpp);
+                if (emit) {
+                    segs.push_back({pc.inst, pc.tile, ra, rows});
+                    inst_segs[(size_t)pc.inst] += 1;
+                    seg_rows_max = std::max(seg_rows_max, rows);
+                }
+                used += seg_overhead + rows * pc.row_cost;
+                ra += rows;
+            }
+        }
+        return blk + 1;
+    };
+    double lo = total / grid, hi = 2.0 * total + seg_overhead;
+    for (int it = 0; it < 60 && hi - lo > 1.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (pack(mid, false) <= grid) hi = mid;
+        else lo = mid;
+    }
+    const int64_t used_blocks = pack(hi, true);
+    for (int64_t b = used_blocks; b <= grid; ++b) block_begin[(size_t)b] = (int32_t)segs.size();
+}
+
+qieo_status upload_group(qieo_batch *bt, qieo_batch::Group &g)
+{
+    std::vector<qieo::GenParams> params;
+    for (qieo_instance *q : g.members) params.push_back(q->gp);
+    if (g.dev && params.size() == g.host_params.size() &&
+        std::memcmp(params.data(), g.host_params.data(), params.size() * sizeof(qieo::GenParams)) == 0)
+        return QIEO_OK;
+    CUDA_TRY(cudaMemcpyAsync(const_cast<qieo::GenParams *>(g.args.params), params.data(),
+                             params.size() * sizeof(qieo::GenParams), cudaMemcpyHostToDevice,
+                             bt->stream));
+    g.host_params = params;
+    drop_batch_graphs(bt);
+    return QIEO_OK;
+}
+
+qieo_status build_group(qieo_batch *bt, qieo_batch::Group &g)
+{
+    const qieo_instance *q0 = g.members[0];
+    const size_t row_bytes = g.narrow ? 8 : 16;
+    auto fn = batch_kernel_of(g.narrow, g.rule, true);
+    auto fn0 = batch_kernel_of(g.narrow, g.rule, false);
+    const size_t smem_max = qieo::kRingBytes + (size_t)qieo::kMaxSegRows * row_bytes;
+    for (auto f : {fn, fn0})
+        CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(f),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    int bps = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, reinterpret_cast<const void *>(fn),
+                                                           qieo::kThreads, smem_max));
+    g.grid = std::max(1, bps) * std::max(1, q0->sm_count);
+    std::vector<qieo::BatchSeg> segs;
+    std::vector<int32_t> block_begin, inst_segs;
+    partition(g.members, g.grid, segs, block_begin, inst_segs, g.seg_rows_max);
+    g.smem = qieo::kRingBytes + (size_t)g.seg_rows_max * row_bytes;
+    const size_t n = g.members.size();
+    size_t off[4], total = 0;
+    const size_t sizes[4] = {n * sizeof(qieo::GenParams), segs.size() * sizeof(qieo::BatchSeg),
+                             block_begin.size() * sizeof(int32_t), n * sizeof(int32_t)};
+    for (int i = 0; i < 4; ++i) {
+        off[i] = total;
+        total = align_up(total + sizes[i], 256);
+    }
+    CUDA_TRY(cudaMalloc(&g.dev, total));
+    char *d = (char *)g.dev;
+    g.args.params = (const qieo::GenParams *)(d + off[0]);
+    g.args.segs = (const qieo::BatchSeg *)(d + off[1]);
+    g.args.block_begin = (const int32_t *)(d + off[2]);
+    g.args.inst_segs = (const int32_t *)(d + off[3]);
+    g.args.seg_rows_max = g.seg_rows_max;
+    CUDA_TRY(cudaMemcpyAsync(d + off[1], segs.data(), sizes[1], cudaMemcpyHostToDevice, bt->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + off[2], block_begin.data(), sizes[2], cudaMemcpyHostToDevice, bt->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + off[3], inst_segs.data(), sizes[3], cudaMemcpyHostToDevice, bt->stream));
+    qieo_status st = upload_group(bt, g);
+    if (st != QIEO_OK) return st;
+    return wait_stream(bt->stream);
+}
+
+qieo_status enqueue_batch_run(qieo_batch *bt, int32_t G)
+{
+    for (int32_t gen = 0; gen < G; ++gen) {
+        for (auto &g : bt->groups) {
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(g.grid);
+            cfg.blockDim = dim3(qieo::kThreads);
+            cfg.dynamicSmemBytes = g.smem;
+            cfg.stream = bt->stream;
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CUDA_TRY(cudaLaunchKernelEx(&cfg, batch_kernel_of(g.narrow, g.rule, gen > 0), g.args));
+        }
+    }
+    for (auto &g : bt->groups) {
+        if (g.rule) qieo::batch_cip_kernel<1><<<g.grid, qieo::kThreads, 0, bt->stream>>>(g.args);
+        else qieo::batch_cip_kernel<0><<<g.grid, qieo::kThreads, 0, bt->stream>>>(g.args);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return QIEO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qieo_status qieo_create_batch(qieo_instance *const *instances, int32_t n, qieo_batch **out)
+{
+    if (out) *out = nullptr;
+    if (!instances || n < 1 || !out) return fail(QIEO_ERR_INVALID, "bad arguments");
+    std::vector<qieo_instance *> members(instances, instances + n);
+    for (int32_t i = 0; i < n; ++i) {
+        if (!members[(size_t)i]) return fail(QIEO_ERR_INVALID, "instance %d is NULL", i);
+        if (members[(size_t)i]->host_de)
+            return fail(QIEO_ERR_INVALID, "instance %d uses elite_on_host; batches pick the elite on the device", i);
+        if (members[(size_t)i]->device != members[0]->device)
+            return fail(QIEO_ERR_INVALID, "instance %d is on another device", i);
+        for (int32_t j = 0; j < i; ++j)
+            if (members[(size_t)j] == members[(size_t)i]) return fail(QIEO_ERR_INVALID, "instance %d repeats", i);
+    }
+    qieo_batch *bt = new (std::nothrow) qieo_batch();
+    if (!bt) return fail(QIEO_ERR_OOM, "host allocation failed");
+    bt->members = members;
+    bt->device = members[0]->device;
+    bt->stream = members[0]->stream;
+    for (qieo_instance *q : members)
+        if (q->stream != bt->stream &&
+            std::find(bt->other_streams.begin(), bt->other_streams.end(), q->stream) == bt->other_streams.end())
+            bt->other_streams.push_back(q->stream);
+    auto bail = [&](qieo_status st) {
+        qieo_destroy_batch(bt);
+        return st;
+    };
+    cudaError_t ce = cudaSetDevice(bt->device);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "batch setup: %s", cudaGetErrorString(ce)));
+    for (qieo_instance *q : members) {
+        auto it = std::find_if(bt->groups.begin(), bt->groups.end(), [&](const qieo_batch::Group &g) {
+            return g.narrow == (q->narrow != 0) && g.rule == q->rule;
+        });
+        if (it == bt->groups.end()) {
+            bt->groups.emplace_back();
+            bt->groups.back().narrow = q->narrow != 0;
+            bt->groups.back().rule = q->rule;
+            it = bt->groups.end() - 1;
+        }
+        it->members.push_back(q);
+    }
+    for (auto &g : bt->groups) {
+        qieo_status st = build_group(bt, g);
+        if (st != QIEO_OK) return bail(st);
+    }
+    *out = bt;
+    return QIEO_OK;
+}
+
+qieo_status qieo_destroy_batch(qieo_batch *bt)
+{
+    if (!bt) return QIEO_OK;
+    cudaSetDevice(bt->device);
+    if (bt->stream) cudaStreamSynchronize(bt->stream);
+    drop_batch_graphs(bt);
+    for (auto &g : bt->groups)
+        if (g.dev) cudaFree(g.dev);
+    if (bt->ev_in) cudaEventDestroy(bt->ev_in);
+    if (bt->ev_out) cudaEventDestroy(bt->ev_out);
+    delete bt;
+    return QIEO_OK;
+}
+
+qieo_status qieo_batch_run(qieo_batch *bt, int32_t G)
+{
+    if (!bt) return fail(QIEO_ERR_INVALID, "batch is NULL");
+    if (G < 0) return fail(QIEO_ERR_INVALID, "generations must be >= 0 (got %d)", G);
+    if (G == 0) return QIEO_OK;
+    CUDA_TRY(cudaSetDevice(bt->device));
+    for (qieo_instance *q : bt->members) {
+        if ((int64_t)q->t + G > INT32_MAX / 2) return fail(QIEO_ERR_INVALID, "generation counter overflow");
+        qieo_status st = ensure_history(q, q->t + G);
+        if (st != QIEO_OK) return st;
+    }
+    for (auto &g : bt->groups) {
+        qieo_status st = upload_group(bt, g);
+        if (st != QIEO_OK) return st;
+    }
+    for (cudaStream_t s : bt->other_streams) {   // pending work of the members' own streams
+        CUDA_TRY(cudaEventRecord(bt->ev_in, s));
+        CUDA_TRY(cudaStreamWaitEvent(bt->stream, bt->ev_in, 0));
+    }
+    const bool first_time = bt->run_lengths_seen[G]++ == 0;
+    if (first_time && !bt->graphs.count(G)) {
+        qieo_status st = enqueue_batch_run(bt, G);
+        if (st != QIEO_OK) return st;
+    } else {
+        auto it = bt->graphs.find(G);
+        cudaGraphExec_t exec = nullptr;
+        if (it == bt->graphs.end()) {
+            if (bt->graphs.size() >= 8) drop_batch_graphs(bt);
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
+            qieo_status st = enqueue_batch_run(bt, G);
+            cudaError_t ce = cudaStreamEndCapture(bt->stream, &graph);
+            if (st != QIEO_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ce != cudaSuccess) return fail(QIEO_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(QIEO_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            bt->graphs[G] = exec;
+        } else {
+            exec = it->second;
+        }
+        CUDA_TRY(cudaGraphLaunch(exec, bt->stream));
+    }
+    if (!bt->other_streams.empty()) {
+        CUDA_TRY(cudaEventRecord(bt->ev_out, bt->stream));
+        for (cudaStream_t s : bt->other_streams) CUDA_TRY(cudaStreamWaitEvent(s, bt->ev_out, 0));
+    }
+    for (qieo_instance *q : bt->members) q->t += G;
+    return QIEO_OK;
+}
+
+qieo_status qieo_autotune(qieo_instance *q, int32_t trials, qieo_launch_shape *shape_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (trials < 1 || trials > 1000) return fail(QIEO_ERR_INVALID, "trial_generations must be in [1, 1000]");
+    if (q->host_de) return fail(QIEO_ERR_INVALID, "autotune times the device path; elite_on_host is set");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    std::vector<std::pair<int, int>> cands;
+    const int span = pow2_ceil(q->svec);
+    for (int L = 1; L <= 16; L *= 2)
+        if (L <= 2 * span) cands.push_back({L, 1});
+    for (int W = 1; W <= 8; W *= 2)
+        if (32 * W <= 2 * span || W == 1) cands.push_back({32, W});
+    const int old_lanes = q->lanes, old_warps = q->warps, old_grid = q->grid_override;
+    const int old_flags = q->flags;
+    q->flags &= ~(QIEO_FLAG_TIME_KERNELS | QIEO_FLAG_SYNC_RUN);
+    float best_ms = 1e30f;
+    std::pair<int, int> best = {old_lanes, old_warps};
+    for (const auto &c : cands) {
+        q->lanes = c.first;
+        q->warps = c.second;
+        q->grid_override = 0;
+        st = configure(q);
+        if (st != QIEO_OK) break;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2 && st == QIEO_OK; ++rep) {
+            st = qieo_reset(q);
+            if (st != QIEO_OK) break;
+            CUDA_TRY(cudaEventRecord(q->ev0, q->stream));
+            st = run_device(q, trials);
+            if (st != QIEO_OK) break;
+            CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
+            st = wait_checked(q);
+            if (st != QIEO_OK) break;
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, q->ev0, q->ev1));
+            ms_min = std::min(ms_min, ms);
+        }
+        if (st != QIEO_OK) break;
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = c;
+        }
+    }
+    q->flags = old_flags;
+    q->lanes = best.first;
+    q->warps = best.second;
+    q->grid_override = old_grid;
+    qieo_status st2 = configure(q);
+    if (st == QIEO_OK) st = st2;
+    qieo_status st3 = qieo_reset(q);
+    if (st == QIEO_OK) st = st3;
+    q->run_lengths_seen.clear();
+    if (st != QIEO_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned[TuneKey{q->ng, q->np, q->D, q->rule, q->narrow_items ? 1 : 0}] = best;
+    }
+    if (shape_out) return qieo_get_launch_shape(q, shape_out);
     return QIEO_OK;
 }
 

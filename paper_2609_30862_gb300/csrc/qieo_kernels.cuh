@@ -243,19 +243,29 @@ __device__ void close_generation(const GenParams &p, int32_t t)
 
 // Per-block constants of the work split.
 struct BlockShare {
-    int tile_vecs, rows_per_pass, r_sub, v_in;
+    int tile_vecs, rows_per_pass, r_sub, v_in, lanes;
     bool leader;                  // first lane of its row segment
     int64_t u_begin, u_end;       // tile-rows [u_begin, u_end) of this block
 };
 
-__device__ __forceinline__ BlockShare block_share(const GenParams &p)
+// Thread geometry of a tile of lanes x warps vectors in a block of kThreads threads.
+__device__ __forceinline__ BlockShare tile_geometry(int lanes, int warps)
 {
     BlockShare b;
-    b.tile_vecs = p.lanes * p.warps;
+    b.lanes = lanes;
+    b.tile_vecs = lanes * warps;
     b.rows_per_pass = kThreads / b.tile_vecs;
     b.r_sub = threadIdx.x / b.tile_vecs;
     b.v_in = threadIdx.x - b.r_sub * b.tile_vecs;
-    b.leader = (threadIdx.x & (p.lanes - 1)) == 0;
+    b.leader = (threadIdx.x & (lanes - 1)) == 0;
+    b.u_begin = 0;
+    b.u_end = 0;
+    return b;
+}
+
+__device__ __forceinline__ BlockShare block_share(const GenParams &p)
+{
+    BlockShare b = tile_geometry(p.lanes, p.warps);
     b.u_begin = (int64_t)blockIdx.x * p.units / gridDim.x;
     b.u_end = (int64_t)(blockIdx.x + 1) * p.units / gridDim.x;
     return b;
@@ -266,23 +276,22 @@ __device__ __forceinline__ void load_thresholds(const GenParams &p, uint32_t *s_
     for (int i = threadIdx.x; i < 2 * p.K + 1; i += kThreads) s_thr[i] = p.thr[i];
 }
 
-// Sum over the lanes of a row segment (p.lanes lanes, a power of two).
+// Sum over the lanes of a row segment (lanes lanes, a power of two).
 template <bool kNarrow>
-__device__ __forceinline__ void segment_sum(const GenParams &p, uint32_t &accn, int64_t &acw,
-                                            int64_t &acv)
+__device__ __forceinline__ void segment_sum(int lanes, uint32_t &accn, int64_t &acw, int64_t &acv)
 {
     if (kNarrow) {
-        if (p.lanes == 32) {
+        if (lanes == 32) {
             accn = __reduce_add_sync(0xffffffffu, accn);
         } else {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
-                if (o < p.lanes) accn += __shfl_xor_sync(0xffffffffu, accn, o);
+                if (o < lanes) accn += __shfl_xor_sync(0xffffffffu, accn, o);
         }
     } else {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            if (o < p.lanes) {
+            if (o < lanes) {
                 acw += __shfl_xor_sync(0xffffffffu, acw, o);
                 acv += __shfl_xor_sync(0xffffffffu, acv, o);
             }
@@ -332,10 +341,29 @@ __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int til
     g.ctr0 = 2u * (uint32_t)g.vec;
 }
 
+// Philox key sources: the ten round keys of a single instance live in the kernel parameter
+// block (each xor reads its key from the constant bank); a batch computes the schedule of
+// the current instance's (block-uniform) key inline.
+struct ParamKeys {
+    const GenParams &p;
+    __device__ __forceinline__ Draw4 operator()(uint32_t c0, uint32_t c1, uint32_t c2) const
+    {
+        return philox4x32_10_rk(c0, c1, c2, 0u, p.rk0, p.rk1);
+    }
+};
+
+struct InlineKeys {
+    uint32_t k0, k1;
+    __device__ __forceinline__ Draw4 operator()(uint32_t c0, uint32_t c1, uint32_t c2) const
+    {
+        return philox4x32_10(c0, c1, c2, 0u, k0, k1);
+    }
+};
+
 // One vector of one row: CIP(t-1), QIP(t), the row's partial sums, stores. Returns the
 // packed or wide sums through accn / acw, acv (before the segment reduction).
-template <bool kNarrow, int kRule, bool kCip>
-__device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const SegCtx &g, uint4 s,
+template <bool kNarrow, int kRule, bool kCip, class Keys>
+__device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys, const SegCtx &g, uint4 s,
                                             uint32_t xo, int32_t c, int32_t t,
                                             const unsigned char *thr_bytes, bool &check,
                                             int &countdown, uint32_t &xbits, uint32_t &accn,
@@ -380,8 +408,8 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const SegCtx &g,
             }
         }
     } else {
-        const Draw4 r0 = philox4x32_10_rk(g.ctr0, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
-        const Draw4 r1 = philox4x32_10_rk(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r0 = keys(g.ctr0, (uint32_t)c, (uint32_t)t);
+        const Draw4 r1 = keys(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t);
         const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -403,13 +431,13 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const SegCtx &g,
 }
 
 template <bool kNarrow>
-__device__ __forceinline__ void add_row_sums(const GenParams &p, bool leader, bool ok, int rr,
+__device__ __forceinline__ void add_row_sums(int lanes, bool leader, bool ok, int rr,
                                              uint32_t accn, int64_t acw, int64_t acv,
                                              uint32_t *s_acc32, unsigned long long *s_acc64)
 {
     uint32_t a = accn;
     int64_t w = acw, v = acv;
-    segment_sum<kNarrow>(p, a, w, v);
+    segment_sum<kNarrow>(lanes, a, w, v);
     if (ok && leader) {
         if (kNarrow) {
             atomicAdd(s_acc32 + 2 * rr, a & 0xffffu);
@@ -502,13 +530,13 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
             const bool ok = rr < seg_rows;
             uint32_t xbits, accn;
             int64_t acw, acv;
-            sv = qubit_pass<kNarrow, kRule, kCip>(p, g, sv, xo, ra + rr, t, thr_bytes, check,
-                                                  countdown, xbits, accn, acw, acv);
+            sv = qubit_pass<kNarrow, kRule, kCip>(p, ParamKeys{p}, g, sv, xo, ra + rr, t, thr_bytes,
+                                                  check, countdown, xbits, accn, acw, acv);
             if (g.active && ok) {
                 sptr[(size_t)pass * sstep] = sv;
                 xptr[(size_t)pass * xstep] = (uint8_t)xbits;
             }
-            add_row_sums<kNarrow>(p, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
+            add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
         };
 
         // Three state buffers in rotation: two rows in flight while one is computed.
@@ -563,6 +591,96 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
+// One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation.
+template <bool kNarrow, int kRule, bool kCip, class Keys>
+__device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &keys, const BlockShare &b,
+                                             int tile, int ra, int seg_rows, int32_t t,
+                                             const uint8_t *x_prev, uint8_t *x_cur,
+                                             const uint8_t *elite_row,
+                                             const unsigned char *thr_bytes, uint4 *slots,
+                                             uint32_t *s_acc32, unsigned long long *s_acc64,
+                                             int &countdown)
+{
+    const int rpp = b.rows_per_pass;
+    const int passes = (seg_rows + rpp - 1) / rpp;
+    bool check = true;
+
+    SegCtx g;
+    seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
+    const size_t row0 = (size_t)ra + b.r_sub;
+    uint4 *sptr = p.state + row0 * p.svec + g.vec;
+    const size_t sstep = (size_t)rpp * p.svec;
+    uint8_t *xptr = x_cur + row0 * p.xstride + g.vec;
+    const uint8_t *xoptr = x_prev + row0 * p.xstride + g.vec;
+    const size_t xstep = (size_t)rpp * p.xstride;
+
+    // Incremental addressing (no multiplies in the pass loop): the copy cursor runs
+    // kRingStages - 1 rows ahead of the compute cursor.
+    const uint4 *ld_ptr = sptr;                 // next row to copy
+    int ld_rr = b.r_sub;                        // its row within the segment
+    uint32_t ld_slot = 0;                       // its slot
+    uint4 *st_ptr = sptr;                       // row being computed
+    uint8_t *xst_ptr = xptr;
+    const uint8_t *xo_ptr = xoptr;
+    int rr = b.r_sub;
+    uint32_t slot = 0;
+    auto issue = [&]() {
+        const bool v = g.active && ld_rr < seg_rows;
+        cp_async16(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
+                   v ? 16u : 0u);
+        cp_async_commit();
+        ld_ptr += sstep;
+        ld_rr += rpp;
+        ld_slot = (ld_slot + 1) & (kRingStages - 1);
+    };
+    auto load_xold = [&](const uint8_t *ptr, int r) -> uint32_t {
+        if (kRule != 1 || !kCip) return 0u;
+        if (!(g.active && r < seg_rows)) return 0u;
+        return (uint32_t)*ptr;
+    };
+
+#pragma unroll
+    for (int k = 0; k < kRingStages - 1; ++k) issue();
+    uint32_t xa = load_xold(xo_ptr, rr), xb1 = load_xold(xo_ptr + xstep, rr + rpp);
+    for (int pass = 0; pass < passes; ++pass) {
+        issue();
+        const uint32_t xo = xa;
+        xa = xb1;
+        xb1 = load_xold(xo_ptr + 2 * xstep, rr + 2 * rpp);
+        xo_ptr += xstep;
+        cp_async_wait<kRingStages - 1>();
+        uint4 sv = slots[(size_t)slot * kThreads];
+        slot = (slot + 1) & (kRingStages - 1);
+
+        const bool ok = rr < seg_rows;
+        uint32_t xbits, accn;
+        int64_t acw, acv;
+        sv = qubit_pass<kNarrow, kRule, kCip>(p, keys, g, sv, xo, ra + rr, t, thr_bytes, check,
+                                              countdown, xbits, accn, acw, acv);
+        if (g.active && ok) {
+            *st_ptr = sv;
+            *xst_ptr = (uint8_t)xbits;
+        }
+        add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
+        st_ptr += sstep;
+        xst_ptr += xstep;
+        rr += rpp;
+    }
+    cp_async_wait<0>();
+    flush_segment<kNarrow>(p, ra, seg_rows, s_acc32, s_acc64);
+}
+
+template <bool kNarrow>
+__device__ __forceinline__ void clear_row_sums(int seg_rows_max, uint32_t *s_acc32,
+                                               unsigned long long *s_acc64)
+{
+    for (int i = threadIdx.x; i < 2 * seg_rows_max; i += kThreads) {
+        if (kNarrow) s_acc32[i] = 0u;
+        else s_acc64[i] = 0ull;
+    }
+    __syncthreads();
+}
+
 template <bool kNarrow, int kRule, bool kCip>
 __device__ __forceinline__ void generation_body_ring(const GenParams &p, const BlockShare &b,
                                                      int32_t t, int32_t e_prev, uint4 *ring,
@@ -573,87 +691,16 @@ __device__ __forceinline__ void generation_body_ring(const GenParams &p, const B
     const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
     uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
     const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
-    const int rpp = b.rows_per_pass;
     uint4 *slots = ring + threadIdx.x;           // slot s of this thread: slots[s * kThreads]
     int countdown = 0;
-    bool check = true;
-
-    for (int i = threadIdx.x; i < 2 * p.seg_rows_max; i += kThreads) {
-        if (kNarrow) s_acc32[i] = 0u;
-        else s_acc64[i] = 0ull;
-    }
-    __syncthreads();
-
+    clear_row_sums<kNarrow>(p.seg_rows_max, s_acc32, s_acc64);
     for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
         const int tile = (int)(u0 / p.np);
         const int ra = (int)(u0 - (int64_t)tile * p.np);
         const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
         u0 += seg_rows;
-        const int passes = (seg_rows + rpp - 1) / rpp;
-
-        SegCtx g;
-        seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
-        const size_t row0 = (size_t)ra + b.r_sub;
-        uint4 *sptr = p.state + row0 * p.svec + g.vec;
-        const size_t sstep = (size_t)rpp * p.svec;
-        uint8_t *xptr = x_cur + row0 * p.xstride + g.vec;
-        const uint8_t *xoptr = x_prev + row0 * p.xstride + g.vec;
-        const size_t xstep = (size_t)rpp * p.xstride;
-
-        // Incremental addressing (no multiplies in the pass loop): the copy cursor runs
-        // kRingStages - 1 rows ahead of the compute cursor.
-        const uint4 *ld_ptr = sptr;                 // next row to copy
-        int ld_rr = b.r_sub;                        // its row within the segment
-        uint32_t ld_slot = 0;                       // its slot
-        uint4 *st_ptr = sptr;                       // row being computed
-        uint8_t *xst_ptr = xptr;
-        const uint8_t *xo_ptr = xoptr;
-        int rr = b.r_sub;
-        uint32_t slot = 0;
-        auto issue = [&]() {
-            const bool v = g.active && ld_rr < seg_rows;
-            cp_async16(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
-                       v ? 16u : 0u);
-            cp_async_commit();
-            ld_ptr += sstep;
-            ld_rr += rpp;
-            ld_slot = (ld_slot + 1) & (kRingStages - 1);
-        };
-        auto load_xold = [&](const uint8_t *ptr, int r) -> uint32_t {
-            if (kRule != 1 || !kCip) return 0u;
-            if (!(g.active && r < seg_rows)) return 0u;
-            return (uint32_t)*ptr;
-        };
-
-#pragma unroll
-        for (int k = 0; k < kRingStages - 1; ++k) issue();
-        uint32_t xa = load_xold(xo_ptr, rr), xb1 = load_xold(xo_ptr + xstep, rr + rpp);
-        for (int pass = 0; pass < passes; ++pass) {
-            issue();
-            const uint32_t xo = xa;
-            xa = xb1;
-            xb1 = load_xold(xo_ptr + 2 * xstep, rr + 2 * rpp);
-            xo_ptr += xstep;
-            cp_async_wait<kRingStages - 1>();
-            uint4 sv = slots[(size_t)slot * kThreads];
-            slot = (slot + 1) & (kRingStages - 1);
-
-            const bool ok = rr < seg_rows;
-            uint32_t xbits, accn;
-            int64_t acw, acv;
-            sv = qubit_pass<kNarrow, kRule, kCip>(p, g, sv, xo, ra + rr, t, thr_bytes, check,
-                                                  countdown, xbits, accn, acw, acv);
-            if (g.active && ok) {
-                *st_ptr = sv;
-                *xst_ptr = (uint8_t)xbits;
-            }
-            add_row_sums<kNarrow>(p, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
-            st_ptr += sstep;
-            xst_ptr += xstep;
-            rr += rpp;
-        }
-        cp_async_wait<0>();
-        flush_segment<kNarrow>(p, ra, seg_rows, s_acc32, s_acc64);
+        ring_segment<kNarrow, kRule, kCip>(p, ParamKeys{p}, b, tile, ra, seg_rows, t, x_prev, x_cur,
+                                           elite_row, thr_bytes, slots, s_acc32, s_acc64, countdown);
     }
 }
 
@@ -885,6 +932,108 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
         const uint32_t e8 = elite[v];
         const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
         p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched form: many independent instances in one persistent launch per generation. The
+// host cuts every instance's ntile * np tile-rows into segments (one tile, at most
+// kMaxSegRows rows each) and gives each block a contiguous run of segments of about
+// equal cost. A block switches instance between segments (parameters, threshold table,
+// tile geometry); each instance's ticket counts its finished segments, and the block that
+// finishes an instance's last segment closes that instance's generation. Instances of one
+// launch share the item-sum form and the rotation rule (the host groups them).
+// ---------------------------------------------------------------------------------------
+struct BatchSeg {
+    int32_t inst, tile, ra, rows;
+};
+
+struct BatchArgs {
+    const GenParams *params;      // [n] per-instance parameters
+    const BatchSeg *segs;         // segments, block-major
+    const int32_t *block_begin;   // [grid + 1] first segment of each block
+    const int32_t *inst_segs;     // [n] segments per instance
+    int32_t seg_rows_max;
+};
+
+template <bool kNarrow, int kRule, bool kCip>
+__global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_kernel(const BatchArgs a)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    __shared__ int s_last;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemParts m = carve_smem<true>(smem_raw);
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    uint4 *slots = m.ring + threadIdx.x;
+    grid_dependency_wait();
+    clear_row_sums<kNarrow>(a.seg_rows_max, m.acc32, m.acc64);
+    int countdown = 0;
+    int32_t cur_inst = -1;
+    int32_t table_K = -1;
+    for (int32_t si = a.block_begin[blockIdx.x]; si < a.block_begin[blockIdx.x + 1]; ++si) {
+        const BatchSeg sg = a.segs[si];
+        const GenParams &p = a.params[sg.inst];
+        if (sg.inst != cur_inst) {
+            cur_inst = sg.inst;
+            if (p.K != table_K) {           // table of this instance's D (row sums are clear)
+                table_K = p.K;
+                for (int i = threadIdx.x; i < 2 * p.K + 1; i += kThreads) s_thr[i] = p.thr[i];
+                __syncthreads();
+            }
+        }
+        const int32_t t = *p.gen;
+        const int32_t e_prev = *p.elite_idx;
+        const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+        uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+        const BlockShare b = tile_geometry(p.lanes, p.warps);
+        ring_segment<kNarrow, kRule, kCip>(p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra,
+                                           sg.rows, t, x_prev, x_cur,
+                                           x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots,
+                                           m.acc32, m.acc64, countdown);
+        // the block that finishes an instance's last segment closes its generation
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned int prev = atomicAdd(p.ticket, 1u);
+            s_last = (prev == (unsigned int)a.inst_segs[sg.inst] - 1u) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            close_generation(p, t);
+            if (threadIdx.x == 0) {
+                *p.gen = t + 1;
+                *p.ticket = 0u;
+                *p.bar_gen = t + 1;
+            }
+            __syncthreads();
+        }
+    }
+    allow_dependent_launch();
+}
+
+// Final rotation of a batched run over the same segments.
+template <int kRule>
+__global__ void __launch_bounds__(kThreads) batch_cip_kernel(const BatchArgs a)
+{
+    grid_dependency_wait();
+    for (int32_t si = a.block_begin[blockIdx.x]; si < a.block_begin[blockIdx.x + 1]; ++si) {
+        const BatchSeg sg = a.segs[si];
+        const GenParams &p = a.params[sg.inst];
+        const int32_t t_last = *p.gen - 1;
+        const int32_t e = *p.elite_idx;
+        const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
+        const BlockShare b = tile_geometry(p.lanes, p.warps);
+        const int vec = sg.tile * b.tile_vecs + b.v_in;
+        if (vec >= p.svec) continue;
+        const uint32_t e8 = __ldcg(xl + (size_t)e * p.xstride + vec);
+        const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+        for (int rr = b.r_sub; rr < sg.rows; rr += b.rows_per_pass) {
+            const size_t c = (size_t)sg.ra + rr;
+            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
+            uint4 *sp = p.state + c * p.svec + vec;
+            *sp = rotate_vec(*sp, e8, m8, k8);
+        }
     }
 }
 

@@ -38,7 +38,8 @@ EXPORTS = (
     "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
-    "qieo_generation_noalloc", "qieo_last_error",
+    "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
+    "qieo_autotune", "qieo_last_error",
 )
 
 QIEO_NOALLOC_MAX_NP = 65536
@@ -104,6 +105,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
         "qieo_philox": ([P, P, i32], C.c_int),
         "qieo_generation_noalloc": ([P, P, i32, P, P, P, P], C.c_int),
+        "qieo_create_batch": ([P, i32, P], C.c_int),
+        "qieo_batch_run": ([P, i32], C.c_int),
+        "qieo_destroy_batch": ([P], C.c_int),
+        "qieo_autotune": ([P, i32, P], C.c_int),
         "qieo_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -234,6 +239,55 @@ def qieo_generation_noalloc(d_weights: int, d_values: int, ng: int, capacity: in
                                           int(d_x), int(d_fitness), int(d_elite)))
 
 
+def qieo_create_batch(handles) -> C.c_void_p:
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    b = C.c_void_p()
+    _check(load().qieo_create_batch(arr, len(handles), C.byref(b)))
+    return b
+
+
+def qieo_batch_run(b, generations: int) -> None:
+    _check(load().qieo_batch_run(b, int(generations)))
+
+
+def qieo_destroy_batch(b) -> None:
+    _check(load().qieo_destroy_batch(b))
+
+
+def qieo_autotune(h, trial_generations: int) -> qieo_launch_shape:
+    s = qieo_launch_shape()
+    _check(load().qieo_autotune(h, int(trial_generations), C.byref(s)))
+    return s
+
+
+class Batch:
+    """Owner of a batch handle over Instance objects (which must outlive it)."""
+
+    def __init__(self, instances):
+        self.instances = list(instances)
+        self.h = qieo_create_batch([i.h for i in self.instances])
+
+    def run(self, generations: int) -> None:
+        qieo_batch_run(self.h, generations)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            qieo_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Instance:
     """Convenience owner of one instance handle (destroyed on close / garbage collection)."""
 
@@ -308,3 +362,6 @@ class Instance:
 
     def kernel_time(self):
         return qieo_get_kernel_time(self.h)
+
+    def autotune(self, trial_generations: int = 8) -> qieo_launch_shape:
+        return qieo_autotune(self.h, trial_generations)
