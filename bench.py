@@ -48,7 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WL.WORKLOADS) + ["c4"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WL.WORKLOADS) + ["c4", "c5"])
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="c5 arrivals per second (0: 0.8 x the measured batched capacity)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -454,8 +457,93 @@ def run_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def run_served(a):
+    """c5: a Poisson stream of solve requests (sizes as in c4, seeds r+1, 300 generations)
+    through the continuous-batching server, against serial per-request launches (one
+    instance at a time in arrival order). Reports solves/s and p50/p99 latency."""
+    import numpy as np
+    import torch
+    from paper_2609_30862_gb300 import qieo as Q
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(0)
+    Q.load()
+    G, n = 300, a.requests
+    specs = WL.batch_manifest(n, first_seed=1)
+    probs = [WL.knapsack(sp.ng, sp.seed) for sp in specs]
+    rate = a.rate
+    if rate <= 0:   # capacity of the batched form on a 256-request sample
+        insts = [Q.Instance(probs[i], specs[i].np_, seed=specs[i].seed, inst=specs[i].seed)
+                 for i in range(min(256, n))]
+        b = Q.Batch(insts)
+        b.run(G)
+        torch.cuda.synchronize()
+        for i in insts:
+            i.reset()
+        t0 = time.perf_counter()
+        b.run(G)
+        for i in insts:
+            i.synchronize()
+        cap = len(insts) / (time.perf_counter() - t0)
+        b.close()
+        for i in insts:
+            i.close()
+        rate = 0.8 * cap
+    arrivals = WL.poisson_arrivals(n, rate)
+
+    def latency_stats(lat, span):
+        lat = np.asarray(lat)
+        return {"solves_per_s": len(lat) / span, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean())}
+
+    # continuous batching
+    srv = Q.Server(gens_per_step=25)
+    ids = []
+    t_start = time.perf_counter()
+    for i, sp in enumerate(specs):
+        delay = arrivals[i] - (time.perf_counter() - t_start)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(probs[i], sp.np_, G, seed=sp.seed, inst=sp.seed))
+    results = [srv.poll(rid, wait_ms=600000)[0] for rid in ids]
+    assert all(r.state == Q.QIEO_SOLVE_DONE for r in results)
+    lat = [r.done_s - r.submit_s for r in results]
+    span = max(r.done_s for r in results) - min(r.submit_s for r in results)
+    served = latency_stats(lat, span)
+    srv.close()
+
+    # serial per-request launches: one instance at a time, in arrival order
+    m = min(n, max(200, n // 10))
+    lat_s = []
+    t_start = time.perf_counter()
+    for i in range(m):
+        now = time.perf_counter() - t_start
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        with Q.Instance(probs[i], specs[i].np_, seed=specs[i].seed, inst=specs[i].seed) as inst:
+            inst.run(G)
+            inst.best()
+        lat_s.append(time.perf_counter() - t_start - arrivals[i])
+    serial = latency_stats(lat_s, time.perf_counter() - t_start)
+    line = {
+        "metric": "served solves/s and p50/p99 latency (Poisson arrivals, 300 generations)",
+        "value": served["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "c5: %d requests, sizes as c4, Poisson arrivals at %.1f/s" % (n, rate),
+                   "parallelism": "continuous batching, 25 generations per step"},
+        "served": served,
+        "serial_per_request": dict(serial, requests=m),
+        "arrival_rate_per_s": rate,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.impl != "reference" and a.workload == "c5":
+        run_served(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "c4":

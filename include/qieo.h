@@ -195,6 +195,59 @@ qieo_status qieo_destroy_batch(qieo_batch *batch);
 qieo_status qieo_autotune(qieo_instance *inst, int32_t trial_generations,
                           qieo_launch_shape *shape_out);
 
+/* Serving (continuous batching of solve requests; the paper solves one problem per run).
+ * A server reserves one device arena for resident populations and runs a worker thread:
+ * submitted requests queue in arrival order and are admitted, as arena memory and the
+ * active-solve limit allow, into the set of resident solves; every scheduling step runs
+ * gens_per_step generations of all resident solves with the batched kernel (one launch per
+ * generation), and a solve that reaches its generation count leaves, freeing its memory
+ * for the next arrivals. Each result is bit-identical to qieo_run on the same problem and
+ * params alone. */
+typedef struct qieo_server qieo_server;
+
+typedef struct {
+    int64_t memory_bytes;     /* device arena for resident solves; 0: half of the free memory */
+    int32_t max_active;       /* most resident solves at once; 0: 1024 */
+    int32_t gens_per_step;    /* generations per scheduling step; 0: 25 */
+} qieo_server_config;
+
+#define QIEO_SOLVE_QUEUED 0
+#define QIEO_SOLVE_RUNNING 1
+#define QIEO_SOLVE_DONE 2
+#define QIEO_SOLVE_CANCELLED 3
+#define QIEO_SOLVE_FAILED 4
+
+typedef struct {
+    int32_t state;            /* QIEO_SOLVE_* */
+    int32_t status;           /* qieo_status of a failed solve */
+    int64_t fitness;          /* best-so-far record of the solve (see qieo_get_best) */
+    int32_t generation, chromosome;
+    double submit_s, admit_s, done_s;   /* seconds on the server's clock */
+} qieo_solve_result;
+
+/* Creates a server on the current device. QIEO_ERR_OOM if the arena cannot be reserved. */
+qieo_status qieo_server_create(const qieo_server_config *config, qieo_server **out);
+
+/* Queues one solve: `generations` generations of problem (host arrays, copied) with params
+ * (np, D, lambda, seed, instance_id, rotate_rule; stream, flags and elite_on_host are
+ * ignored). *id_out receives the request id. QIEO_ERR_OOM when the solve needs more device
+ * memory than the whole arena (it could never be admitted); QIEO_ERR_INVALID for bad
+ * arguments. Thread-safe. */
+qieo_status qieo_server_submit(qieo_server *server, const qieo_problem *problem,
+                               const qieo_params *params, int32_t generations, int64_t *id_out);
+
+/* Result of request `id`; waits up to wait_ms milliseconds for it to finish (0: do not
+ * wait). bits_out (ng bytes, may be NULL) receives the best alleles once done. */
+qieo_status qieo_server_poll(qieo_server *server, int64_t id, int32_t wait_ms, uint8_t *bits_out,
+                             qieo_solve_result *result);
+
+/* Cancels a request that is still queued (QIEO_ERR_BUSY once it runs). */
+qieo_status qieo_server_cancel(qieo_server *server, int64_t id);
+
+/* Cancels queued requests, waits (bounded) for running ones, stops the worker, frees the
+ * arena. NULL is accepted. */
+qieo_status qieo_server_destroy(qieo_server *server);
+
 /* Philox4x32-10 on the device for n (counter, key) pairs: ctr_key is n*6 host uint32
  * (c0 c1 c2 c3 k0 k1), out is n*4 host uint32. Uses the library's default stream. */
 qieo_status qieo_philox(const uint32_t *ctr_key, uint32_t *out, int32_t n);

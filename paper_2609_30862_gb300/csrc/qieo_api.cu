@@ -20,8 +20,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <unordered_map>
 #include <tuple>
 #include <new>
 #include <string>
@@ -105,8 +109,10 @@ struct qieo_instance {
     int64_t sum_w = 0, sum_v = 0, sum_absv = 0;
     bool key_ok = false;
 
-    // device memory
+    // device memory (owned unless it was placed in a server's arena)
     void *block = nullptr;
+    bool owns_block = true;
+    bool fixed_history = false;     // history lives inside an arena block of fixed capacity
     qieo::GenParams gp{};
     const uint4 *items_narrow = nullptr;
     int32_t *hist_e = nullptr;
@@ -330,6 +336,9 @@ void build_thresholds(int32_t D, std::vector<uint64_t> &T)
 qieo_status ensure_history(qieo_instance *q, int32_t need)
 {
     if (need <= q->hist_cap) return QIEO_OK;
+    if (q->fixed_history)
+        return fail(QIEO_ERR_INVALID, "generation %d beyond the %d generations reserved for this solve",
+                    need, q->hist_cap);
     int32_t cap = std::max<int32_t>(need, std::max<int32_t>(1024, q->hist_cap * 2));
     int32_t *e = nullptr;
     int64_t *f = nullptr;
@@ -492,8 +501,57 @@ void qieo_default_params(qieo_params *p)
 
 const char *qieo_last_error(void) { return g_last_error.c_str(); }
 
-qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
-                                 qieo_instance **out)
+}  // extern "C"
+
+namespace {
+
+// Device memory of one instance, every part 256-byte aligned:
+//  0 state | 1 xbits (2 planes) | 2 packed items | 3 wide items | 4 best row | 5 acc |
+//  6 cnt | 7 fitness | 8 best[3] | 9 gen | 10 ticket | 11 key | 12 elite idx | 13 thr |
+//  14 barrier generation | 15 error word | 16, 17 elite history (only when placed in a
+//  server arena with a fixed number of generations)
+constexpr int kParts = 18;
+
+size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size_t *off)
+{
+    const size_t svec = (size_t)(ng + 7) / 8;
+    const size_t xstride = align_up(svec, 16);
+    const size_t ngp = svec * 8;
+    const size_t sizes[kParts] = {(size_t)np * svec * sizeof(uint4),
+                                  2 * (size_t)np * xstride,
+                                  ngp * 4,
+                                  ngp * 8,
+                                  xstride,
+                                  (size_t)np * 2 * sizeof(unsigned long long),
+                                  (size_t)np * sizeof(unsigned int),
+                                  (size_t)np * sizeof(int64_t),
+                                  3 * sizeof(int64_t),
+                                  sizeof(int32_t),
+                                  sizeof(unsigned int),
+                                  sizeof(unsigned long long),
+                                  sizeof(int32_t),
+                                  (size_t)(D / 2 + 1) * sizeof(uint32_t),
+                                  sizeof(int32_t),
+                                  sizeof(int32_t),
+                                  (size_t)hist_cap * sizeof(int32_t),
+                                  (size_t)hist_cap * sizeof(int64_t)};
+    size_t total = 0;
+    for (int i = 0; i < kParts; ++i) {
+        off[i] = total;
+        total = align_up(total + sizes[i], 256);
+    }
+    return total;
+}
+
+// An instance placed in memory the caller reserved (a server arena).
+struct Placement {
+    void *block;
+    size_t bytes;
+    int32_t hist_cap;
+};
+
+qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
+                                 const Placement *ext, bool sync, qieo_instance **out)
 {
     if (out) *out = nullptr;
     if (!pr || !pa || !out) return fail(QIEO_ERR_INVALID, "NULL argument");
@@ -568,37 +626,19 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
     if (ce == cudaSuccess) ce = cudaEventCreate(&q->ev1);
     if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "events: %s", cudaGetErrorString(ce)));
 
-    // One device block, every part 256-byte aligned:
-    //  0 state | 1 xbits (2 planes) | 2 packed items | 3 wide items | 4 best row | 5 acc |
-    //  6 cnt | 7 fitness | 8 best[3] | 9 gen | 10 ticket | 11 key | 12 elite idx | 13 thr |
-    //  14 barrier generation | 15 error word
     const size_t ngp = (size_t)q->svec * 8;
-    const size_t sizes[16] = {(size_t)q->np * q->svec * sizeof(uint4),
-                              2 * (size_t)q->np * q->xstride,
-                              ngp * 4,
-                              ngp * 8,
-                              (size_t)q->xstride,
-                              (size_t)q->np * 2 * sizeof(unsigned long long),
-                              (size_t)q->np * sizeof(unsigned int),
-                              (size_t)q->np * sizeof(int64_t),
-                              3 * sizeof(int64_t),
-                              sizeof(int32_t),
-                              sizeof(unsigned int),
-                              sizeof(unsigned long long),
-                              sizeof(int32_t),
-                              (size_t)(2 * q->K + 1) * sizeof(uint32_t),
-                              sizeof(int32_t),
-                              sizeof(int32_t)};
-    size_t off[16];
-    size_t total = 0;
-    for (int i = 0; i < 16; ++i) {
-        off[i] = total;
-        total = align_up(total + sizes[i], 256);
+    size_t off[kParts];
+    const size_t total = instance_layout(q->ng, q->np, q->D, ext ? ext->hist_cap : 0, off);
+    if (ext) {
+        if (!ext->block || ext->bytes < total) return bail(fail(QIEO_ERR_INVALID, "placement too small"));
+        q->block = ext->block;
+        q->owns_block = false;
+    } else {
+        ce = cudaMalloc(&q->block, total);
+        if (ce != cudaSuccess)
+            return bail(fail(ce == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA,
+                             "device allocation of %zu bytes: %s", total, cudaGetErrorString(ce)));
     }
-    ce = cudaMalloc(&q->block, total);
-    if (ce != cudaSuccess)
-        return bail(fail(ce == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA,
-                         "device allocation of %zu bytes: %s", total, cudaGetErrorString(ce)));
     char *b = (char *)q->block;
     qieo::GenParams &g = q->gp;
     g.state = (uint4 *)(b + off[0]);
@@ -666,14 +706,35 @@ qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
     }
     qieo_status st = configure(q);
     if (st != QIEO_OK) return bail(st);
-    st = ensure_history(q, 1024);
-    if (st != QIEO_OK) return bail(st);
+    if (ext) {
+        q->hist_e = (int32_t *)(b + off[16]);
+        q->hist_f = (int64_t *)(b + off[17]);
+        q->hist_cap = ext->hist_cap;
+        q->fixed_history = true;
+        q->gp.hist_e = q->hist_e;
+        q->gp.hist_f = q->hist_f;
+    } else {
+        st = ensure_history(q, 1024);
+        if (st != QIEO_OK) return bail(st);
+    }
     st = qieo_reset(q);
     if (st != QIEO_OK) return bail(st);
-    st = wait_stream(q->stream);
-    if (st != QIEO_OK) return bail(st);
+    if (sync) {
+        st = wait_stream(q->stream);
+        if (st != QIEO_OK) return bail(st);
+    }
     *out = q;
     return QIEO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qieo_status qieo_create_instance(const qieo_problem *pr, const qieo_params *pa,
+                                 qieo_instance **out)
+{
+    return create_instance_impl(pr, pa, nullptr, true, out);
 }
 
 qieo_status qieo_destroy_instance(qieo_instance *q)
@@ -1302,6 +1363,488 @@ qieo_status qieo_autotune(qieo_instance *q, int32_t trials, qieo_launch_shape *s
         g_tuned[TuneKey{q->ng, q->np, q->D, q->rule, q->narrow_items ? 1 : 0}] = best;
     }
     if (shape_out) return qieo_get_launch_shape(q, shape_out);
+    return QIEO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Serving
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// First-fit allocator over the arena (byte offsets) with a coalescing free list.
+class ArenaAlloc {
+  public:
+    void init(size_t bytes)
+    {
+        free_.clear();
+        free_[0] = bytes;
+        total_ = bytes;
+    }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            const size_t rest = it->second - bytes, noff = it->first + bytes;
+            free_.erase(it);
+            if (rest) free_[noff] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t total() const { return total_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t total_ = 0;
+};
+
+struct SolveRequest {
+    int64_t id = 0;
+    std::vector<int32_t> w, v;
+    qieo_problem prob{};
+    qieo_params params{};
+    int32_t gens = 0;
+    int32_t state = QIEO_SOLVE_QUEUED;
+    int32_t status = QIEO_OK;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    qieo_instance *inst = nullptr;
+    size_t off = 0, bytes = 0;
+    int32_t remaining = 0;
+    int64_t best[3] = {0, -1, -1};
+    std::vector<uint8_t> best_row;
+};
+
+struct StepRecord {
+    cudaEvent_t done = nullptr;
+    std::vector<SolveRequest *> finishing;
+};
+
+constexpr size_t kWorkListBytes = 16u << 20;   // per region: params, segments, block starts
+
+}  // namespace
+
+struct qieo_server {
+    qieo_server_config cfg{};
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    char *arena = nullptr;
+    ArenaAlloc alloc;
+    char *wl_dev[2] = {nullptr, nullptr};
+    char *wl_host[2] = {nullptr, nullptr};
+    int wl_next = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::deque<SolveRequest *> queue;
+    std::vector<SolveRequest *> active;
+    std::unordered_map<int64_t, std::unique_ptr<SolveRequest>> all;
+    std::deque<StepRecord> inflight;
+    std::vector<cudaEvent_t> spare_events;
+    int64_t next_id = 1;
+    std::chrono::steady_clock::time_point t0;
+    std::thread worker;
+    int bps[2] = {1, 1};                 // batch kernel blocks per SM: [wide, narrow]
+};
+
+namespace {
+
+double server_now(const qieo_server *S)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
+}
+
+void destroy_instance_nosync(qieo_instance *q)
+{
+    drop_graphs(q);
+    if (q->ev0) cudaEventDestroy(q->ev0);
+    if (q->ev1) cudaEventDestroy(q->ev1);
+    delete q;
+}
+
+// Enqueues `G` generations (+ the final rotation) of every member on the server stream
+// with the batched kernel; the work list goes through the next double-buffered region.
+qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance *> &members, int32_t G)
+{
+    const int r = S->wl_next;
+    S->wl_next ^= 1;
+    char *host = S->wl_host[r];
+    char *dev = S->wl_dev[r];
+    size_t used = 0;
+    struct Launch {
+        bool narrow;
+        int rule;
+        int grid;
+        size_t smem;
+        qieo::BatchArgs args;
+    };
+    std::vector<Launch> launches;
+    for (int narrow = 0; narrow < 2; ++narrow) {
+        for (int rule = 0; rule < 2; ++rule) {
+            std::vector<qieo_instance *> grp;
+            for (qieo_instance *q : members)
+                if (q->narrow == narrow && q->rule == rule) grp.push_back(q);
+            if (grp.empty()) continue;
+            const int grid = S->bps[narrow] * S->sm_count;
+            std::vector<qieo::BatchSeg> segs;
+            std::vector<int32_t> block_begin, inst_segs;
+            int32_t seg_rows_max = 1;
+            partition(grp, grid, segs, block_begin, inst_segs, seg_rows_max);
+            const size_t sizes[4] = {grp.size() * sizeof(qieo::GenParams), segs.size() * sizeof(qieo::BatchSeg),
+                                     block_begin.size() * sizeof(int32_t), inst_segs.size() * sizeof(int32_t)};
+            size_t off[4];
+            for (int i = 0; i < 4; ++i) {
+                off[i] = used;
+                used = align_up(used + sizes[i], 256);
+            }
+            if (used > kWorkListBytes)
+                return fail(QIEO_ERR_INVALID, "too many resident solves for one work list");
+            for (size_t i = 0; i < grp.size(); ++i)
+                std::memcpy(host + off[0] + i * sizeof(qieo::GenParams), &grp[i]->gp, sizeof(qieo::GenParams));
+            std::memcpy(host + off[1], segs.data(), sizes[1]);
+            std::memcpy(host + off[2], block_begin.data(), sizes[2]);
+            std::memcpy(host + off[3], inst_segs.data(), sizes[3]);
+            Launch L;
+            L.narrow = narrow != 0;
+            L.rule = rule;
+            L.grid = grid;
+            L.smem = qieo::kRingBytes + (size_t)seg_rows_max * (narrow ? 8 : 16);
+            L.args.params = (const qieo::GenParams *)(dev + off[0]);
+            L.args.segs = (const qieo::BatchSeg *)(dev + off[1]);
+            L.args.block_begin = (const int32_t *)(dev + off[2]);
+            L.args.inst_segs = (const int32_t *)(dev + off[3]);
+            L.args.seg_rows_max = seg_rows_max;
+            launches.push_back(L);
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(dev, host, used, cudaMemcpyHostToDevice, S->stream));
+    for (int32_t gen = 0; gen < G; ++gen) {
+        for (const Launch &L : launches) {
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(L.grid);
+            cfg.blockDim = dim3(qieo::kThreads);
+            cfg.dynamicSmemBytes = L.smem;
+            cfg.stream = S->stream;
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CUDA_TRY(cudaLaunchKernelEx(&cfg, batch_kernel_of(L.narrow, L.rule, gen > 0), L.args));
+        }
+    }
+    for (const Launch &L : launches) {
+        if (L.rule) qieo::batch_cip_kernel<1><<<L.grid, qieo::kThreads, 0, S->stream>>>(L.args);
+        else qieo::batch_cip_kernel<0><<<L.grid, qieo::kThreads, 0, S->stream>>>(L.args);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return QIEO_OK;
+}
+
+// Results of the solves that finished with the oldest step in flight.
+void retire_oldest_step(qieo_server *S)
+{
+    StepRecord rec = S->inflight.front();
+    S->inflight.pop_front();
+    const auto t_wait = std::chrono::steady_clock::now();
+    cudaError_t ce;
+    while ((ce = cudaEventQuery(rec.done)) == cudaErrorNotReady) {
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t_wait).count() > kWaitSeconds)
+            break;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    const qieo_status step_st = ce == cudaSuccess ? QIEO_OK : (ce == cudaErrorNotReady ? QIEO_ERR_TIMEOUT : QIEO_ERR_CUDA);
+    for (SolveRequest *R : rec.finishing) {
+        qieo_instance *q = R->inst;
+        int32_t st = step_st;
+        if (st == QIEO_OK) {
+            R->best_row.resize((size_t)q->xstride);
+            if (cudaMemcpyAsync(R->best, q->gp.best, sizeof R->best, cudaMemcpyDeviceToHost, S->copy_stream) != cudaSuccess ||
+                cudaMemcpyAsync(R->best_row.data(), q->gp.best_row, R->best_row.size(), cudaMemcpyDeviceToHost,
+                                S->copy_stream) != cudaSuccess ||
+                cudaStreamSynchronize(S->copy_stream) != cudaSuccess)
+                st = QIEO_ERR_CUDA;
+        }
+        destroy_instance_nosync(q);
+        std::lock_guard<std::mutex> lock(S->mu);
+        R->inst = nullptr;
+        if (st == QIEO_OK) S->alloc.release(R->off, R->bytes);   // a failed step keeps its memory
+        R->status = st;
+        R->state = st == QIEO_OK ? QIEO_SOLVE_DONE : QIEO_SOLVE_FAILED;
+        R->t_done = server_now(S);
+    }
+    S->spare_events.push_back(rec.done);
+    S->cv_done.notify_all();
+}
+
+void server_loop(qieo_server *S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<SolveRequest *> admit;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            while (!S->queue.empty() &&
+                   (int64_t)(S->active.size() + admit.size()) < (int64_t)S->cfg.max_active) {
+                SolveRequest *R = S->queue.front();
+                size_t off = 0;
+                if (!S->alloc.alloc(R->bytes, &off)) break;
+                R->off = off;
+                S->queue.pop_front();
+                admit.push_back(R);
+            }
+            if (admit.empty() && S->active.empty() && S->inflight.empty()) {
+                if (S->stop) break;
+                S->cv_work.wait(lock);
+                continue;
+            }
+        }
+        for (SolveRequest *R : admit) {
+            qieo_params pa = R->params;
+            pa.stream = S->stream;
+            pa.flags = 0;
+            pa.elite_on_host = 0;
+            Placement pl{S->arena + R->off, R->bytes, R->gens};
+            qieo_instance *q = nullptr;
+            const qieo_status st = create_instance_impl(&R->prob, &pa, &pl, false, &q);
+            std::lock_guard<std::mutex> lock(S->mu);
+            R->t_admit = server_now(S);
+            if (st == QIEO_OK) {
+                R->inst = q;
+                R->remaining = R->gens;
+                R->state = QIEO_SOLVE_RUNNING;
+                S->active.push_back(R);
+            } else {
+                S->alloc.release(R->off, R->bytes);
+                R->status = st;
+                R->state = QIEO_SOLVE_FAILED;
+                R->t_done = R->t_admit;
+                S->cv_done.notify_all();
+            }
+        }
+        if (!S->active.empty() && S->inflight.size() < 2) {
+            int32_t G = S->cfg.gens_per_step;
+            std::vector<qieo_instance *> members;
+            for (SolveRequest *R : S->active) {
+                G = std::min(G, R->remaining);
+                members.push_back(R->inst);
+            }
+            StepRecord rec;
+            qieo_status st = enqueue_server_step(S, members, G);
+            if (st == QIEO_OK) {
+                if (S->spare_events.empty()) {
+                    cudaEvent_t ev = nullptr;
+                    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) st = QIEO_ERR_CUDA;
+                    S->spare_events.push_back(ev);
+                }
+            }
+            if (st == QIEO_OK) {
+                rec.done = S->spare_events.back();
+                S->spare_events.pop_back();
+                if (cudaEventRecord(rec.done, S->stream) != cudaSuccess) st = QIEO_ERR_CUDA;
+            }
+            std::lock_guard<std::mutex> lock(S->mu);
+            std::vector<SolveRequest *> still;
+            for (SolveRequest *R : S->active) {
+                if (st != QIEO_OK) {
+                    R->status = st;
+                    R->state = QIEO_SOLVE_FAILED;
+                    R->t_done = server_now(S);
+                    continue;
+                }
+                R->remaining -= G;
+                R->inst->t += G;
+                if (R->remaining == 0) rec.finishing.push_back(R);
+                else still.push_back(R);
+            }
+            S->active.swap(still);
+            if (st == QIEO_OK) S->inflight.push_back(rec);
+            else S->cv_done.notify_all();
+        } else if (!S->inflight.empty()) {
+            retire_oldest_step(S);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+qieo_status qieo_server_create(const qieo_server_config *config, qieo_server **out)
+{
+    if (out) *out = nullptr;
+    if (!out) return fail(QIEO_ERR_INVALID, "out is NULL");
+    qieo_server_config cfg{};
+    if (config) cfg = *config;
+    if (cfg.memory_bytes < 0 || cfg.max_active < 0 || cfg.gens_per_step < 0)
+        return fail(QIEO_ERR_INVALID, "negative server configuration");
+    if (cfg.max_active == 0) cfg.max_active = 1024;
+    if (cfg.gens_per_step == 0) cfg.gens_per_step = 25;
+    qieo_server *S = new (std::nothrow) qieo_server();
+    if (!S) return fail(QIEO_ERR_OOM, "host allocation failed");
+    S->t0 = std::chrono::steady_clock::now();
+    auto bail = [&](qieo_status st) {
+        qieo_server_destroy(S);
+        return st;
+    };
+    cudaError_t ce = cudaGetDevice(&S->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "server setup: %s", cudaGetErrorString(ce)));
+    if (cfg.memory_bytes == 0) {
+        size_t free_b = 0, total_b = 0;
+        ce = cudaMemGetInfo(&free_b, &total_b);
+        if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(ce)));
+        cfg.memory_bytes = (int64_t)(free_b / 2);
+    }
+    S->cfg = cfg;
+    ce = cudaMalloc(&S->arena, (size_t)cfg.memory_bytes);
+    if (ce != cudaSuccess)
+        return bail(fail(QIEO_ERR_OOM, "arena of %lld bytes: %s", (long long)cfg.memory_bytes, cudaGetErrorString(ce)));
+    S->alloc.init((size_t)cfg.memory_bytes);
+    for (int r = 0; r < 2; ++r) {
+        ce = cudaMalloc(&S->wl_dev[r], kWorkListBytes);
+        if (ce == cudaSuccess) ce = cudaMallocHost(&S->wl_host[r], kWorkListBytes);
+        if (ce != cudaSuccess) return bail(fail(QIEO_ERR_OOM, "work lists: %s", cudaGetErrorString(ce)));
+    }
+    for (int narrow = 0; narrow < 2; ++narrow) {
+        const size_t smem_max = qieo::kRingBytes + (size_t)qieo::kMaxSegRows * (narrow ? 8 : 16);
+        for (int rule = 0; rule < 2; ++rule)
+            for (int cip = 0; cip < 2; ++cip) {
+                ce = cudaFuncSetAttribute(reinterpret_cast<const void *>(batch_kernel_of(narrow, rule, cip)),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+                if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "kernel attribute: %s", cudaGetErrorString(ce)));
+            }
+        int bps = 0;
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &bps, reinterpret_cast<const void *>(batch_kernel_of(narrow, 0, true)), qieo::kThreads, smem_max);
+        if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "occupancy: %s", cudaGetErrorString(ce)));
+        S->bps[narrow] = std::max(1, bps);
+    }
+    S->worker = std::thread(server_loop, S);
+    *out = S;
+    return QIEO_OK;
+}
+
+qieo_status qieo_server_submit(qieo_server *S, const qieo_problem *pr, const qieo_params *pa,
+                               int32_t generations, int64_t *id_out)
+{
+    if (!S || !pr || !pa || !id_out) return fail(QIEO_ERR_INVALID, "NULL argument");
+    if (generations < 1) return fail(QIEO_ERR_INVALID, "generations must be >= 1");
+    if (pr->ng < 1 || !pr->weights || !pr->values || pa->np < 1 || pr->capacity < 0 ||
+        pa->dtheta_den < 4 || pa->dtheta_den > kMaxD || pa->dtheta_den % 4 != 0 ||
+        pa->penalty_lambda < 1 || (pa->rotate_rule != 0 && pa->rotate_rule != 1))
+        return fail(QIEO_ERR_INVALID, "invalid problem or params");
+    for (int32_t j = 0; j < pr->ng; ++j)
+        if (pr->weights[j] < 0) return fail(QIEO_ERR_INVALID, "weight %d is negative", j);
+    size_t off[kParts];
+    const size_t bytes = instance_layout(pr->ng, pa->np, pa->dtheta_den, generations, off);
+    if (bytes > S->alloc.total())
+        return fail(QIEO_ERR_OOM, "solve needs %zu bytes of device memory; the server arena holds %zu",
+                    bytes, S->alloc.total());
+    std::unique_ptr<SolveRequest> R(new (std::nothrow) SolveRequest());
+    if (!R) return fail(QIEO_ERR_OOM, "host allocation failed");
+    R->w.assign(pr->weights, pr->weights + pr->ng);
+    R->v.assign(pr->values, pr->values + pr->ng);
+    R->prob = *pr;
+    R->prob.weights = R->w.data();
+    R->prob.values = R->v.data();
+    R->params = *pa;
+    R->gens = generations;
+    R->bytes = bytes;
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->stop) return fail(QIEO_ERR_INVALID, "server is stopping");
+    R->id = S->next_id++;
+    R->t_submit = server_now(S);
+    *id_out = R->id;
+    S->queue.push_back(R.get());
+    S->all[R->id] = std::move(R);
+    S->cv_work.notify_one();
+    return QIEO_OK;
+}
+
+qieo_status qieo_server_poll(qieo_server *S, int64_t id, int32_t wait_ms, uint8_t *bits_out,
+                             qieo_solve_result *res)
+{
+    if (!S || !res) return fail(QIEO_ERR_INVALID, "NULL argument");
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(QIEO_ERR_INVALID, "unknown request %lld", (long long)id);
+    SolveRequest *R = it->second.get();
+    if (wait_ms > 0)
+        S->cv_done.wait_for(lock, std::chrono::milliseconds(wait_ms),
+                            [&] { return R->state >= QIEO_SOLVE_DONE; });
+    res->state = R->state;
+    res->status = R->status;
+    res->fitness = R->best[0];
+    res->generation = (int32_t)R->best[1];
+    res->chromosome = (int32_t)R->best[2];
+    res->submit_s = R->t_submit;
+    res->admit_s = R->t_admit;
+    res->done_s = R->t_done;
+    if (bits_out && R->state == QIEO_SOLVE_DONE) unpack_row(R->best_row.data(), R->prob.ng, bits_out);
+    return QIEO_OK;
+}
+
+qieo_status qieo_server_cancel(qieo_server *S, int64_t id)
+{
+    if (!S) return fail(QIEO_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(QIEO_ERR_INVALID, "unknown request %lld", (long long)id);
+    SolveRequest *R = it->second.get();
+    if (R->state != QIEO_SOLVE_QUEUED) return fail(QIEO_ERR_BUSY, "request %lld is no longer queued", (long long)id);
+    S->queue.erase(std::find(S->queue.begin(), S->queue.end(), R));
+    R->state = QIEO_SOLVE_CANCELLED;
+    R->t_done = server_now(S);
+    S->cv_done.notify_all();
+    return QIEO_OK;
+}
+
+qieo_status qieo_server_destroy(qieo_server *S)
+{
+    if (!S) return QIEO_OK;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+        for (SolveRequest *R : S->queue) {
+            R->state = QIEO_SOLVE_CANCELLED;
+            R->t_done = server_now(S);
+        }
+        S->queue.clear();
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->device);
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    for (cudaEvent_t ev : S->spare_events) cudaEventDestroy(ev);
+    for (int r = 0; r < 2; ++r) {
+        if (S->wl_dev[r]) cudaFree(S->wl_dev[r]);
+        if (S->wl_host[r]) cudaFreeHost(S->wl_host[r]);
+    }
+    if (S->arena) cudaFree(S->arena);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
+    delete S;
     return QIEO_OK;
 }
 

@@ -39,8 +39,15 @@ EXPORTS = (
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
-    "qieo_autotune", "qieo_last_error",
+    "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
+    "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
 )
+
+QIEO_SOLVE_QUEUED = 0
+QIEO_SOLVE_RUNNING = 1
+QIEO_SOLVE_DONE = 2
+QIEO_SOLVE_CANCELLED = 3
+QIEO_SOLVE_FAILED = 4
 
 QIEO_NOALLOC_MAX_NP = 65536
 
@@ -66,6 +73,16 @@ class qieo_launch_shape(C.Structure):
     _fields_ = [("lanes_per_row", C.c_int32), ("warps_per_row", C.c_int32),
                 ("grid_ctas", C.c_int32), ("narrow", C.c_int32), ("tiles", C.c_int32),
                 ("rows_per_cta", C.c_int32)]
+
+
+class qieo_server_config(C.Structure):
+    _fields_ = [("memory_bytes", C.c_int64), ("max_active", C.c_int32), ("gens_per_step", C.c_int32)]
+
+
+class qieo_solve_result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("fitness", C.c_int64),
+                ("generation", C.c_int32), ("chromosome", C.c_int32), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double)]
 
 
 _LIB: C.CDLL | None = None
@@ -109,6 +126,11 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_batch_run": ([P, i32], C.c_int),
         "qieo_destroy_batch": ([P], C.c_int),
         "qieo_autotune": ([P, i32, P], C.c_int),
+        "qieo_server_create": ([P, P], C.c_int),
+        "qieo_server_submit": ([P, P, P, i32, P], C.c_int),
+        "qieo_server_poll": ([P, i64, i32, P, P], C.c_int),
+        "qieo_server_cancel": ([P, i64], C.c_int),
+        "qieo_server_destroy": ([P], C.c_int),
         "qieo_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -258,6 +280,79 @@ def qieo_autotune(h, trial_generations: int) -> qieo_launch_shape:
     s = qieo_launch_shape()
     _check(load().qieo_autotune(h, int(trial_generations), C.byref(s)))
     return s
+
+
+def qieo_server_create(memory_bytes: int = 0, max_active: int = 0, gens_per_step: int = 0):
+    cfg = qieo_server_config(int(memory_bytes), int(max_active), int(gens_per_step))
+    h = C.c_void_p()
+    _check(load().qieo_server_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def qieo_server_submit(h, weights, values, capacity: int, params: qieo_params, generations: int) -> int:
+    w = np.ascontiguousarray(weights, dtype=np.int32)
+    v = np.ascontiguousarray(values, dtype=np.int32)
+    pr = qieo_problem(int(w.shape[0]), w.ctypes.data, v.ctypes.data, int(capacity))
+    rid = C.c_int64()
+    _check(load().qieo_server_submit(h, C.byref(pr), C.byref(params), int(generations), C.byref(rid)))
+    return int(rid.value)
+
+
+def qieo_server_poll(h, rid: int, wait_ms: int = 0, ng: int = 0):
+    res = qieo_solve_result()
+    bits = np.zeros(max(ng, 1), dtype=np.uint8)
+    _check(load().qieo_server_poll(h, int(rid), int(wait_ms), _ptr(bits) if ng else None,
+                                   C.byref(res)))
+    return res, (bits[:ng] if ng else None)
+
+
+def qieo_server_cancel(h, rid: int) -> None:
+    _check(load().qieo_server_cancel(h, int(rid)))
+
+
+def qieo_server_destroy(h) -> None:
+    _check(load().qieo_server_destroy(h))
+
+
+class Server:
+    """Owner of a solve server handle."""
+
+    def __init__(self, memory_bytes: int = 0, max_active: int = 0, gens_per_step: int = 0):
+        self.h = qieo_server_create(memory_bytes, max_active, gens_per_step)
+        self.ng = {}
+
+    def submit(self, problem, np_: int, generations: int, seed: int = 1, inst: int = 0,
+               D: int = 100, lam: int = 1, rule: int = QIEO_RULE_R1) -> int:
+        p = qieo_default_params()
+        p.np, p.seed, p.instance_id = int(np_), int(seed) & 0xFFFFFFFF, int(inst) & 0xFFFFFFFF
+        p.dtheta_den, p.penalty_lambda, p.rotate_rule = int(D), int(lam), int(rule)
+        rid = qieo_server_submit(self.h, problem.weights, problem.values, problem.capacity, p,
+                                 generations)
+        self.ng[rid] = int(problem.ng)
+        return rid
+
+    def poll(self, rid: int, wait_ms: int = 0):
+        return qieo_server_poll(self.h, rid, wait_ms, self.ng.get(rid, 0))
+
+    def cancel(self, rid: int) -> None:
+        qieo_server_cancel(self.h, rid)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            qieo_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Batch:
