@@ -101,11 +101,12 @@ __device__ __forceinline__ unsigned long long elite_key(int64_t f, int32_t c)
 
 // Error bits reported through GenParams::error.
 constexpr int32_t kErrBarrierTimeout = 1;
+constexpr int32_t kErrEliteRange = 2;   // a generation closed with no chromosome finished
 
 struct GenParams {
     uint4 *state;                 // [np][svec] scaled angle indices
     uint8_t *xbits;               // [2][np][xstride]
-    const uint4 *items_narrow;    // [2 svec] packed (v << 16 | w), 4 genes per uint4
+    const uint4 *items_narrow;    // [svec] byte vectors (w0 w2 w1 w3, w4 w6 w5 w7, same for v)
     const int4 *w4;               // wide: [2 svec] weights
     const int4 *v4;               // wide: [2 svec] values
     unsigned long long *acc;      // narrow [np]; wide [2 np]
@@ -218,6 +219,13 @@ __device__ void close_generation(const GenParams &p, int32_t t)
         }
     }
     if (tid == 0) {
+        // Every row finishes in every generation, so the elite lies in [0, np); anything
+        // else is recorded as an internal error and replaced by row 0 so that no later
+        // access leaves the population.
+        if (bc < 0 || bc >= p.np) {
+            atomicOr(p.error, kErrEliteRange);
+            bc = 0;
+        }
         p.hist_e[t] = bc;
         p.hist_f[t] = bf;
         *p.elite_idx = bc;
@@ -301,8 +309,12 @@ __device__ __forceinline__ void segment_sum(int lanes, uint32_t &accn, int64_t &
 
 // Per-segment constants of one thread: its vector of a tile, the 8 items of that vector
 // and the elite alleles of the previous generation for it.
+//
+// Narrow items are kept as four byte vectors, w4a = (w0, w2, w1, w3), w4b = (w4, w6, w5,
+// w7) and the same for v, so that the sums of a pass are four byte dot products (dp4a)
+// with the allele bytes built in the same order (see allele_bytes).
 struct SegCtx {
-    uint32_t wv[8];               // narrow items (v << 16 | w)
+    uint32_t w4a, w4b, v4a, v4b;  // narrow items as byte vectors
     int32_t wi[8], vi[8];         // wide items
     uint32_t e8;                  // elite alleles of the previous generation (8 genes)
     uint32_t ctr0;                // Philox counter word 0 of the first 4 genes
@@ -317,13 +329,9 @@ __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int til
     g.vec = tile * tile_vecs + v_in;
     g.active = g.vec < p.svec;
     if (kNarrow) {
-        uint4 a = make_uint4(0, 0, 0, 0), c = a;
-        if (g.active) {
-            a = __ldg(p.items_narrow + 2 * (size_t)g.vec);
-            c = __ldg(p.items_narrow + 2 * (size_t)g.vec + 1);
-        }
-        g.wv[0] = a.x; g.wv[1] = a.y; g.wv[2] = a.z; g.wv[3] = a.w;
-        g.wv[4] = c.x; g.wv[5] = c.y; g.wv[6] = c.z; g.wv[7] = c.w;
+        uint4 a = make_uint4(0, 0, 0, 0);
+        if (g.active) a = __ldg(p.items_narrow + g.vec);
+        g.w4a = a.x; g.w4b = a.y; g.v4a = a.z; g.v4b = a.w;
     } else {
         int4 a = make_int4(0, 0, 0, 0), c = a, d = a, e = a;
         if (g.active) {
@@ -360,73 +368,107 @@ struct InlineKeys {
     }
 };
 
-// One vector of one row: CIP(t-1), QIP(t), the row's partial sums, stores. Returns the
-// packed or wide sums through accn / acw, acv (before the segment reduction).
+// Allele nibble (bit i = allele of gene i) -> bytes (x0, x2, x1, x3), each 0 or 1. The
+// multiplier's four terms shift bit 0 by 0, bit 2 by 6, bit 1 by 15 and bit 3 by 21; all
+// sixteen partial products land on distinct bits, so nothing carries, and the mask keeps
+// bits 0, 8, 16 and 24.
+__device__ __forceinline__ uint32_t allele_bytes(uint32_t nibble)
+{
+    return (nibble * 0x00208041u) & 0x01010101u;
+}
+
+// Bytes (x0, x2, x1, x3), each 0 or 1 -> nibble (bit i = x_i). The terms shift byte 0 to
+// bit 24, byte 1 to bit 26, byte 2 to bit 25 and byte 3 to bit 27; the other partial
+// products fall below bit 20 or at bit 32 and above, again without carries.
+__device__ __forceinline__ uint32_t allele_nibble_hi(uint32_t bytes)
+{
+    return bytes * 0x01040208u;   // the nibble is bits 24..27
+}
+
+// Packed narrow sums (sum v << 16 | sum w) of the 8 genes of a pass.
+__device__ __forceinline__ uint32_t narrow_sums(const SegCtx &g, uint32_t xa, uint32_t xb)
+{
+    const uint32_t sw = __dp4a(xa, g.w4a, __dp4a(xb, g.w4b, 0u));
+    const uint32_t sv = __dp4a(xa, g.v4a, __dp4a(xb, g.v4b, 0u));
+    return sw | (sv << 16);
+}
+
+// One vector of one row: CIP(t-1), QIP(t), the row's partial sums. Returns the new state
+// and the packed or wide sums through accn / acw, acv (before the segment reduction).
+//
+// Fixed-allele pass: a qubit at theta = 0 or pi/2 (n = 0 or 2K, T = 0 or 2^32) yields the
+// same allele for every draw, and CIP leaves it where it is when it already sits at the
+// bound on the elite's side (or is not rotated). When that holds for every qubit of the
+// pass in the whole warp, the alleles are the bits of the state itself, no Philox call is
+// needed, and the state is unchanged (fixed = true: the caller skips its store). The test
+// is skipped for 15 passes after it fails, which keeps its cost low while the population
+// is still spread out.
 template <bool kNarrow, int kRule, bool kCip, class Keys>
 __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys, const SegCtx &g, uint4 s,
                                             uint32_t xo, int32_t c, int32_t t,
-                                            const unsigned char *thr_bytes, bool &check,
+                                            const unsigned char *thr_bytes, bool &fixed,
                                             int &countdown, uint32_t &xbits, uint32_t &accn,
                                             int64_t &acw, int64_t &acv)
 {
-    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
     const uint32_t off_top = (uint32_t)(8 * p.K);
-    if (kCip) s = rotate_vec(s, g.e8, kRule == 1 ? (g.e8 ^ xo) : 0xffu, k8);
-    const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
-    xbits = 0u;
+    const uint32_t k8 = off_top * 0x00010001u;
+    const uint32_t m8 = kRule == 1 ? (g.e8 ^ xo) : 0xffu;   // genes the rotation moves
     accn = 0u;
     acw = 0;
     acv = 0;
+    fixed = false;
 
-    // A qubit at theta = 0 or pi/2 (n = 0 or 2K) has a fixed allele (T = 0 or 2^32), so
-    // when every qubit of the pass in the whole warp is there, no draw can change anything
-    // and the Philox calls are not needed. The test is skipped for 15 passes after it
-    // fails, which keeps its cost low while the population is still spread out.
-    bool sat = false;
     if (countdown == 0) {
-        uint32_t z = 0u;   // per half h in [0, 8K]: min(h, 8K - h) == 0 iff h is 0 or 8K
+        // A half h in {0, 8K} is h == b * 8K with b its bit number bp (any set bit of 8K).
+        const int bp = __ffs((int)off_top) - 1;
+        const uint32_t b0 = (s.x >> bp) & 0x00010001u, b1 = (s.y >> bp) & 0x00010001u;
+        const uint32_t b2 = (s.z >> bp) & 0x00010001u, b3 = (s.w >> bp) & 0x00010001u;
+        const bool sat = s.x == b0 * off_top && s.y == b1 * off_top && s.z == b2 * off_top &&
+                         s.w == b3 * off_top;
+        // b0 holds gene 0 at bit 0 and gene 1 at bit 16, so xa = (x0, x2, x1, x3) as bytes
+        const uint32_t xa = b0 | (b1 << 8), xb = b2 | (b3 << 8);
+        const uint32_t xs = (allele_nibble_hi(xa) >> 24) | ((allele_nibble_hi(xb) >> 20) & 0xf0u);
+        const bool ok = sat && (!kCip || ((g.e8 ^ xs) & m8) == 0u);
+        if (__all_sync(0xffffffffu, ok)) {
+            fixed = true;
+            xbits = xs;
+            if (kNarrow) {
+                accn = narrow_sums(g, xa, xb);
+            } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) z |= __vminu2(sp[q], k8 - sp[q]);
-        sat = __all_sync(0xffffffffu, z == 0u);
-        if (!sat) countdown = 15;
+                for (int i = 0; i < 8; ++i) {
+                    if ((xs >> i) & 1u) {
+                        acw += g.wi[i];
+                        acv += g.vi[i];
+                    }
+                }
+            }
+            return s;
+        }
+        countdown = 15;
     } else {
         --countdown;
     }
-    (void)check;
-    if (sat) {
+
+    if (kCip) s = rotate_vec(s, g.e8, m8, k8);
+    const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
+    const Draw4 r0 = keys(g.ctr0, (uint32_t)c, (uint32_t)t);
+    const Draw4 r1 = keys(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t);
+    const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
+    xbits = 0u;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
-            if (off != 0u) {
-                xbits |= 1u << i;
-                if (kNarrow) {
-                    accn += g.wv[i];
-                } else {
-                    acw += g.wi[i];
-                    acv += g.vi[i];
-                }
-            }
-        }
-    } else {
-        const Draw4 r0 = keys(g.ctr0, (uint32_t)c, (uint32_t)t);
-        const Draw4 r1 = keys(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t);
-        const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
-            const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
-            const bool x = (u[i] < thr) || (off == off_top);
-            if (x) {
-                xbits |= 1u << i;
-                if (kNarrow) {
-                    accn += g.wv[i];
-                } else {
-                    acw += g.wi[i];
-                    acv += g.vi[i];
-                }
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
+        const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+        if ((u[i] < thr) || (off == off_top)) {
+            xbits |= 1u << i;
+            if (!kNarrow) {
+                acw += g.wi[i];
+                acv += g.vi[i];
             }
         }
     }
+    if (kNarrow) accn = narrow_sums(g, allele_bytes(xbits & 0xfu), allele_bytes(xbits >> 4));
     return s;
 }
 
@@ -490,7 +532,6 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
     const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
     const int rpp = b.rows_per_pass;
     int countdown = 0;
-    bool check = true;
 
     for (int i = threadIdx.x; i < 2 * p.seg_rows_max; i += kThreads) {
         if (kNarrow) s_acc32[i] = 0u;
@@ -530,10 +571,11 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
             const bool ok = rr < seg_rows;
             uint32_t xbits, accn;
             int64_t acw, acv;
+            bool fixed;
             sv = qubit_pass<kNarrow, kRule, kCip>(p, ParamKeys{p}, g, sv, xo, ra + rr, t, thr_bytes,
-                                                  check, countdown, xbits, accn, acw, acv);
+                                                  fixed, countdown, xbits, accn, acw, acv);
             if (g.active && ok) {
-                sptr[(size_t)pass * sstep] = sv;
+                if (!fixed) sptr[(size_t)pass * sstep] = sv;   // a fixed pass leaves it as it is
                 xptr[(size_t)pass * xstep] = (uint8_t)xbits;
             }
             add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
@@ -603,7 +645,6 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 {
     const int rpp = b.rows_per_pass;
     const int passes = (seg_rows + rpp - 1) / rpp;
-    bool check = true;
 
     SegCtx g;
     seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
@@ -655,10 +696,11 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         const bool ok = rr < seg_rows;
         uint32_t xbits, accn;
         int64_t acw, acv;
-        sv = qubit_pass<kNarrow, kRule, kCip>(p, keys, g, sv, xo, ra + rr, t, thr_bytes, check,
+        bool fixed;
+        sv = qubit_pass<kNarrow, kRule, kCip>(p, keys, g, sv, xo, ra + rr, t, thr_bytes, fixed,
                                               countdown, xbits, accn, acw, acv);
         if (g.active && ok) {
-            *st_ptr = sv;
+            if (!fixed) *st_ptr = sv;   // a fixed pass leaves the state as it is
             *xst_ptr = (uint8_t)xbits;
         }
         add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
