@@ -522,7 +522,7 @@ size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size
     const size_t ngp = svec * 8;
     const size_t sizes[kParts] = {(size_t)np * svec * sizeof(uint4),
                                   2 * (size_t)np * xstride,
-                                  ngp * 2,
+                                  ngp * 6,
                                   ngp * 8,
                                   xstride,
                                   (size_t)np * 2 * sizeof(unsigned long long),
@@ -675,16 +675,18 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     }
 
     // Items in both layouts, padded with zeros to whole vectors (padding adds nothing).
-    // Narrow: per vector of 8 genes the byte vectors (w0, w2, w1, w3), (w4, w6, w5, w7),
-    // (v0, v2, v1, v3), (v4, v6, v5, v7), in the byte order the kernels build alleles in.
-    std::vector<uint32_t> packed(ngp / 2, 0u), wide(2 * ngp, 0u);
+    // Narrow: (v << 16 | w) per gene, then per vector of 8 genes the byte vectors
+    // (w0, w2, w1, w3), (w4, w6, w5, w7), (v0, v2, v1, v3), (v4, v6, v5, v7), in the byte
+    // order the kernels build alleles in.
+    std::vector<uint32_t> packed(ngp + ngp / 2, 0u), wide(2 * ngp, 0u);
     static const int kByteOf[8] = {0, 2, 1, 3, 0, 2, 1, 3};
     for (int32_t j = 0; j < q->ng; ++j) {
         if (q->narrow_items) {
+            packed[(size_t)j] = ((uint32_t)pr->values[j] << 16) | (uint32_t)pr->weights[j];
             const size_t v = (size_t)j / 8;
             const int i = j % 8, hi = i / 4, sh = 8 * kByteOf[i];
-            packed[4 * v + hi] |= (uint32_t)pr->weights[j] << sh;
-            packed[4 * v + 2 + hi] |= (uint32_t)pr->values[j] << sh;
+            packed[ngp + 4 * v + hi] |= (uint32_t)pr->weights[j] << sh;
+            packed[ngp + 4 * v + 2 + hi] |= (uint32_t)pr->values[j] << sh;
         }
         wide[(size_t)j] = (uint32_t)pr->weights[j];
         wide[ngp + (size_t)j] = (uint32_t)pr->values[j];

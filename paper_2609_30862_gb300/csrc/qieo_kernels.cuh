@@ -40,7 +40,7 @@
 namespace qieo {
 
 constexpr int kThreads = 256;
-constexpr int kMaxSegRows = 2048;          // tile-rows summed in shared memory at once
+constexpr int kMaxSegRows = 1536;          // tile-rows summed in shared memory at once
 constexpr int kMaxK = 1000;                // D <= 4000
 constexpr int kMaxThr = 2 * kMaxK + 1;
 
@@ -106,7 +106,8 @@ constexpr int32_t kErrEliteRange = 2;   // a generation closed with no chromosom
 struct GenParams {
     uint4 *state;                 // [np][svec] scaled angle indices
     uint8_t *xbits;               // [2][np][xstride]
-    const uint4 *items_narrow;    // [svec] byte vectors (w0 w2 w1 w3, w4 w6 w5 w7, same for v)
+    const uint4 *items_narrow;    // [2 svec] packed (v << 16 | w), 4 genes per uint4, then
+                                  // [svec] byte vectors (w0 w2 w1 w3, w4 w6 w5 w7, same for v)
     const int4 *w4;               // wide: [2 svec] weights
     const int4 *v4;               // wide: [2 svec] values
     unsigned long long *acc;      // narrow [np]; wide [2 np]
@@ -310,17 +311,21 @@ __device__ __forceinline__ void segment_sum(int lanes, uint32_t &accn, int64_t &
 // Per-segment constants of one thread: its vector of a tile, the 8 items of that vector
 // and the elite alleles of the previous generation for it.
 //
-// Narrow items are kept as four byte vectors, w4a = (w0, w2, w1, w3), w4b = (w4, w6, w5,
-// w7) and the same for v, so that the sums of a pass are four byte dot products (dp4a)
-// with the allele bytes built in the same order (see allele_bytes).
+// Narrow items are kept twice: packed (v << 16 | w) per gene in registers, added under the
+// allele predicates of a drawn pass; and as four byte vectors w4a = (w0, w2, w1, w3),
+// w4b = (w4, w6, w5, w7) and the same for v in the thread's slot of s_item_bytes, where a
+// fixed-allele pass forms its sums as byte dot products (dp4a) with allele bytes built in
+// the same order (see allele_nibble_hi).
 struct SegCtx {
-    uint32_t w4a, w4b, v4a, v4b;  // narrow items as byte vectors
+    uint32_t wv[8];               // narrow items (v << 16 | w)
     int32_t wi[8], vi[8];         // wide items
     uint32_t e8;                  // elite alleles of the previous generation (8 genes)
     uint32_t ctr0;                // Philox counter word 0 of the first 4 genes
     int vec;
     bool active;                  // vec < svec
 };
+
+__shared__ uint4 s_item_bytes[kThreads];   // per thread: w4a, w4b, v4a, v4b
 
 template <bool kNarrow, bool kCip>
 __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int tile, int v_in,
@@ -329,9 +334,15 @@ __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int til
     g.vec = tile * tile_vecs + v_in;
     g.active = g.vec < p.svec;
     if (kNarrow) {
-        uint4 a = make_uint4(0, 0, 0, 0);
-        if (g.active) a = __ldg(p.items_narrow + g.vec);
-        g.w4a = a.x; g.w4b = a.y; g.v4a = a.z; g.v4b = a.w;
+        uint4 a = make_uint4(0, 0, 0, 0), c = a, d = a;
+        if (g.active) {
+            a = __ldg(p.items_narrow + 2 * (size_t)g.vec);
+            c = __ldg(p.items_narrow + 2 * (size_t)g.vec + 1);
+            d = __ldg(p.items_narrow + 2 * (size_t)p.svec + g.vec);
+        }
+        g.wv[0] = a.x; g.wv[1] = a.y; g.wv[2] = a.z; g.wv[3] = a.w;
+        g.wv[4] = c.x; g.wv[5] = c.y; g.wv[6] = c.z; g.wv[7] = c.w;
+        s_item_bytes[threadIdx.x] = d;   // read back by this thread only
     } else {
         int4 a = make_int4(0, 0, 0, 0), c = a, d = a, e = a;
         if (g.active) {
@@ -368,15 +379,6 @@ struct InlineKeys {
     }
 };
 
-// Allele nibble (bit i = allele of gene i) -> bytes (x0, x2, x1, x3), each 0 or 1. The
-// multiplier's four terms shift bit 0 by 0, bit 2 by 6, bit 1 by 15 and bit 3 by 21; all
-// sixteen partial products land on distinct bits, so nothing carries, and the mask keeps
-// bits 0, 8, 16 and 24.
-__device__ __forceinline__ uint32_t allele_bytes(uint32_t nibble)
-{
-    return (nibble * 0x00208041u) & 0x01010101u;
-}
-
 // Bytes (x0, x2, x1, x3), each 0 or 1 -> nibble (bit i = x_i). The terms shift byte 0 to
 // bit 24, byte 1 to bit 26, byte 2 to bit 25 and byte 3 to bit 27; the other partial
 // products fall below bit 20 or at bit 32 and above, again without carries.
@@ -385,11 +387,13 @@ __device__ __forceinline__ uint32_t allele_nibble_hi(uint32_t bytes)
     return bytes * 0x01040208u;   // the nibble is bits 24..27
 }
 
-// Packed narrow sums (sum v << 16 | sum w) of the 8 genes of a pass.
-__device__ __forceinline__ uint32_t narrow_sums(const SegCtx &g, uint32_t xa, uint32_t xb)
+// Packed narrow sums (sum v << 16 | sum w) of the 8 genes of a pass from allele bytes
+// (x0, x2, x1, x3) and (x4, x6, x5, x7).
+__device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
 {
-    const uint32_t sw = __dp4a(xa, g.w4a, __dp4a(xb, g.w4b, 0u));
-    const uint32_t sv = __dp4a(xa, g.v4a, __dp4a(xb, g.v4b, 0u));
+    const uint4 ib = s_item_bytes[threadIdx.x];
+    const uint32_t sw = __dp4a(xa, ib.x, __dp4a(xb, ib.y, 0u));
+    const uint32_t sv = __dp4a(xa, ib.z, __dp4a(xb, ib.w, 0u));
     return sw | (sv << 16);
 }
 
@@ -433,7 +437,7 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
             fixed = true;
             xbits = xs;
             if (kNarrow) {
-                accn = narrow_sums(g, xa, xb);
+                accn = narrow_sums(xa, xb);
             } else {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -462,13 +466,14 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
         const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
         if ((u[i] < thr) || (off == off_top)) {
             xbits |= 1u << i;
-            if (!kNarrow) {
+            if (kNarrow) {
+                accn += g.wv[i];
+            } else {
                 acw += g.wi[i];
                 acv += g.vi[i];
             }
         }
     }
-    if (kNarrow) accn = narrow_sums(g, allele_bytes(xbits & 0xfu), allele_bytes(xbits >> 4));
     return s;
 }
 

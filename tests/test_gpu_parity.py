@@ -137,10 +137,10 @@ def test_async_ring_and_register_streaming_agree(rule):
 
 def test_long_shares_split_into_segments():
     """Two blocks over 6000 rows x 2 tiles: each block's share crosses a tile boundary and
-    exceeds the 2048 tile-rows its shared memory sums at once."""
+    exceeds the 1536 tile-rows its shared memory sums at once."""
     prob = W.knapsack(2050, 18)
     shape = compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2))
-    assert shape.tiles == 2 and shape.rows_per_cta == 2048
+    assert shape.tiles == 2 and shape.rows_per_cta == 1536
     compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2), flags=Q.QIEO_FLAG_REGISTER_PREFETCH)
 
 
