@@ -8,7 +8,9 @@ all ranks (each rank solves its own independent instance: weak scaling, no colle
 the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
-  python bench.py --impl reference ...   # the CPU oracle timed on the host cores
+  python bench.py --workload c4           # 256 uneven instances, batched (solves/s)
+  python bench.py --workload c5           # served Poisson stream (solves/s, p50/p99)
+  python bench.py --impl reference ...    # the CPU oracle timed on the host cores
 
 Prints one JSON line (rank 0).
 """
@@ -33,7 +35,7 @@ METRIC = "gene-updates/s (Np*Ng*gens) & % roofline"
 UNIT = "gene-updates/s"
 SM_COUNT = 152
 LANES_PER_SM = 128
-# Integer operations per gene-update that the method itself needs (see DESIGN.md):
+# Integer operations per gene-update that the method itself needs:
 # Philox4x32-10 = 10 rounds x (2 wide multiplies + 2 three-input xors) per 4 genes = 10,
 # CIP (packed add/max/sub/min on 2 genes) = 2, observation (index extract + compare) = 2,
 # evaluation (packed item add) = 1, allele packing = 1.
@@ -193,6 +195,9 @@ def run_reference(a):
     bounded sample of the same workload. Rank 0 only."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
+    if a.workload in ("c4", "c5"):
+        run_reference_solves(a)
+        return
     from oracle import oracle as O
     c = WL.WORKLOADS[a.workload]
     prob = WL.knapsack(c["ng"], c["item_seed"])
@@ -224,6 +229,46 @@ def run_reference(a):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_solves(a):
+    """Reference arm of the batched (c4) and served (c5) workloads: the oracle solving the
+    manifest's instances (300 generations each) in order, a bounded number per step, on all
+    host cores. The metric is solves/s."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    O.build()
+    G = 300
+    specs = WL.batch_manifest(256 if a.workload == "c4" else a.requests, first_seed=1)
+    budget_s = 150.0 / max(1, a.steps + a.warmup)
+    pos, times, counts = 0, [], []
+    for k in range(a.warmup + a.steps):
+        t0, done = time.perf_counter(), 0
+        while time.perf_counter() - t0 < budget_s or done == 0:
+            sp = specs[pos % len(specs)]
+            pos += 1
+            O.run(WL.knapsack(sp.ng, sp.seed), sp.np_, G, seed=sp.seed, inst=sp.seed,
+                  kind="omp", threads=cores)
+            done += 1
+        if k >= a.warmup:
+            times.append(time.perf_counter() - t0)
+            counts.append(done)
+    total = sum(times)
+    value = sum(counts) / total
+    sample = "%d manifest instances x %d generations per step on average, OpenMP build, %d threads" % (
+        round(sum(counts) / len(counts)), G, cores)
+    line = {
+        "impl": "reference", "metric": "solves/s", "value": value, "unit": "solves/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "%s: manifest instances (Ng log-uniform [50, 20000], Np uniform "
+                               "{32,64,128,256,512}), 300 generations" % a.workload},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -384,77 +429,184 @@ def run_gpu(a):
     return np
 
 
+def batch_oracle_sample(specs, G: int, target_s: float = 10.0):
+    """The oracle (OpenMP build, all host cores) solving manifest instances in order until
+    about target_s of CPU work. Returns (solves/s, cores, sample text)."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    O.build()
+    O.set_threads(cores)
+    done, t0 = 0, time.perf_counter()
+    for sp in specs:
+        prob = WL.knapsack(sp.ng, sp.seed)
+        O.run(prob, sp.np_, G, seed=sp.seed, inst=sp.seed, kind="omp", threads=cores)
+        done += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, cores, "first %d manifest instances x %d generations, OpenMP build, %d threads" % (
+        done, G, cores)
+
+
 def run_batched(a):
     """c4: 256 independent instances (Ng log-uniform in [50, 20000], Np uniform in
     {32..512}, seeds 1..256), 300 generations each. One step = reset + 300 generations of
-    all 256; the batched launch is compared with one launch sequence per instance."""
+    all 256 in one batched launch per generation; compared with one launch sequence per
+    instance. Under torchrun every rank solves its own 256 (seeds offset by 256 x rank)."""
     import torch
     from paper_2609_30862_gb300 import qieo as Q
-    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
-        return
-    torch.cuda.set_device(0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     Q.load()
-    G = 300
-    specs = WL.batch_manifest(256)
+    G, n = 300, 256
+    specs = WL.batch_manifest(n, first_seed=1 + n * rank)
+    probs = [WL.knapsack(sp.ng, sp.seed) for sp in specs]
     stream = torch.cuda.Stream()
-    insts = []
-    tune_s = 0.0
-    for sp in specs:
-        prob = WL.knapsack(sp.ng, sp.seed)
-        inst = Q.Instance(prob, sp.np_, seed=sp.seed, inst=sp.seed, stream=stream.cuda_stream)
-        if not a.no_autotune:
-            t0 = time.perf_counter()
-            inst.autotune(4)
-            tune_s += time.perf_counter() - t0
-        insts.append(inst)
-    genes = sum(sp.np_ * sp.ng for sp in specs) * G
+
+    def make(tune: bool):
+        out, t = [], 0.0
+        for sp, prob in zip(specs, probs):
+            inst = Q.Instance(prob, sp.np_, seed=sp.seed, inst=sp.seed, stream=stream.cuda_stream)
+            if tune:
+                t0 = time.perf_counter()
+                inst.autotune(4)
+                t += time.perf_counter() - t0
+            out.append(inst)
+        return out, t
+
+    insts, tune_s = make(not a.no_autotune)
+    genes_per_gen = sum(sp.np_ * sp.ng for sp in specs)
+    genes = genes_per_gen * G
+    state_bytes = sum(sp.np_ * ((sp.ng + 7) // 8) * 16 for sp in specs)
+    flush = state_bytes < 2 * L2_BYTES
+    flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda") if flush else None
     batch = Q.Batch(insts)
 
-    def step_batched():
-        for i in insts:
-            i.reset()
-        batch.run(G)
-
-    def step_single():
-        for i in insts:
-            i.reset()
-            i.run(G)
-
-    def timed(fn, steps, warmup):
-        for _ in range(warmup):
-            fn()
+    def barrier():
         torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        for _ in range(steps):
-            fn()
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        return ev[0].elapsed_time(ev[1]) / 1e3
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t[0])
 
     with torch.cuda.stream(stream):
-        tb = timed(step_batched, a.steps, a.warmup)
-        ts = timed(step_single, max(1, a.steps // 5), 1)
-        # every member's result must be the same whichever way it was run
+        for _ in range(a.warmup):
+            for i in insts:
+                i.reset()
+            batch.run(G)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+        sampler = ClockSampler(gpu_id_for_smi(torch, local)) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        barrier()
+        for k in range(a.steps):
+            if flush:
+                flush_buf.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            for i in insts:
+                i.reset()
+            evs[k][1].record(stream)
+            batch.run(G)
+            evs[k][2].record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        tb = max_over_ranks(sum(e0.elapsed_time(e2) for e0, _, e2 in evs) / 1e3)
+        run_s = max_over_ranks(sum(e1.elapsed_time(e2) for _, e1, e2 in evs) / 1e3)
+
+        # one launch sequence per instance, same members and results
+        single_steps = max(1, a.steps // 5)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        barrier()
+        ev[0].record(stream)
+        for _ in range(single_steps):
+            for i in insts:
+                i.reset()
+                i.run(G)
+        ev[1].record(stream)
+        barrier()
+        ts = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3)
         ok = all(i.best()[1] >= 0 for i in insts)
-    value = 256 * a.steps / tb
-    line = {
-        "metric": "solves/s (256 instances x 300 generations)", "value": value, "unit": "solves/s",
-        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tb / a.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": "c4: 256 instances, Ng log-uniform [50, 20000], Np uniform {32,64,128,256,512}, "
-                               "300 generations, seeds 1..256", "parallelism": "one batched launch per generation"},
-        "gene_updates_per_s": genes * a.steps / tb,
-        "one_launch_per_instance": {"value": 256 * max(1, a.steps // 5) / ts, "unit": "solves/s",
-                                    "gene_updates_per_s": genes * max(1, a.steps // 5) / ts},
-        "speedup_vs_one_launch_per_instance": (256 * a.steps / tb) / (256 * max(1, a.steps // 5) / ts),
-        "autotune_s": tune_s, "records_ok": ok,
-    }
     batch.close()
     for i in insts:
         i.close()
-    print(json.dumps(line), flush=True)
+
+    # end to end through the C ABI with host buffers: create the 256 instances (items
+    # uploaded), run them as one batch, read every best record back, destroy -- every step
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for k in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
+            barrier()
+            t0 = time.perf_counter()
+            hs, _ = make(False)
+            hb = Q.Batch(hs)
+            hb.run(G)
+            for h in hs:
+                h.best()
+            hb.close()
+            for h in hs:
+                h.close()
+            torch.cuda.synchronize()
+            if k > 0:
+                e2e_times.append(time.perf_counter() - t0)
+    e2e_value = (world * n * len(e2e_times) / max_over_ranks(sum(e2e_times))
+                 if e2e_times else None)
+    h2d = sum(((sp.ng + 7) // 8) * 8 * 4 * 3 + 4 * 51 for sp in specs)
+    d2h = sum(((sp.ng + 7) // 8 + 15) // 16 * 16 + 24 for sp in specs)
+
+    # Roofline of batch_generation_kernel: a batched run is G launches plus one final CIP
+    # launch over all members; per launch the algorithmic bytes are 4 B x every member's
+    # genes (state read + write), timed as the run / G.
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    launch_s = run_s / (a.steps * G)
+    achieved = STATE_BYTES_PER_GENE * genes_per_gen / launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src,
+            "state_in_l2": state_bytes < L2_BYTES, "traffic": profile_traffic("batch_generation_kernel", "c4"),
+            "kernel": "batch_generation_kernel (one launch per generation for all members)",
+            "us_per_generation": launch_s * 1e6}
+    value = world * n * a.steps / tb
+    line = {
+        "metric": "solves/s (256 instances x 300 generations)", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tb / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "c4: 256 instances, Ng log-uniform [50, 20000], Np uniform {32,64,128,256,512}, "
+                               "300 generations, seeds 1..256", "parallelism": "one batched launch per generation"
+                               + ("; 256 instances per rank" if world > 1 else ""),
+                   "state_bytes": state_bytes,
+                   "l2": "flushed between steps (512 MB write)" if flush else "state larger than L2 (no flush)"},
+        "gene_updates_per_s": world * genes * a.steps / tb,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": "256 x qieo_create_instance from host arrays + qieo_create_batch + qieo_batch_run + "
+                        "256 x qieo_get_best + destroy, per step"},
+        "gpu_launches": a.steps * (n + G + 1),
+        "clocks": clocks,
+        "one_launch_per_instance": {"value": world * n * single_steps / ts, "unit": "solves/s",
+                                    "gene_updates_per_s": world * genes * single_steps / ts},
+        "speedup_vs_one_launch_per_instance": (n * a.steps / tb) / (n * single_steps / ts),
+        "autotune_s": tune_s, "records_ok": ok,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, cores, sample = batch_oracle_sample(specs, G)
+        line["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_served(a):
@@ -499,6 +651,8 @@ def run_served(a):
     # continuous batching
     srv = Q.Server(gens_per_step=25)
     ids = []
+    sampler = ClockSampler(gpu_id_for_smi(torch, 0))
+    sampler.start()
     t_start = time.perf_counter()
     for i, sp in enumerate(specs):
         delay = arrivals[i] - (time.perf_counter() - t_start)
@@ -506,10 +660,12 @@ def run_served(a):
             time.sleep(delay)
         ids.append(srv.submit(probs[i], sp.np_, G, seed=sp.seed, inst=sp.seed))
     results = [srv.poll(rid, wait_ms=600000)[0] for rid in ids]
+    clocks = sampler.stop()
     assert all(r.state == Q.QIEO_SOLVE_DONE for r in results)
     lat = [r.done_s - r.submit_s for r in results]
     span = max(r.done_s for r in results) - min(r.submit_s for r in results)
     served = latency_stats(lat, span)
+    stats = srv.stats()
     srv.close()
 
     # serial per-request launches: one instance at a time, in arrival order
@@ -525,17 +681,43 @@ def run_served(a):
             inst.best()
         lat_s.append(time.perf_counter() - t_start - arrivals[i])
     serial = latency_stats(lat_s, time.perf_counter() - t_start)
+
+    genes = sum(sp.np_ * sp.ng for sp in specs) * G
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    achieved = STATE_BYTES_PER_GENE * genes / span / 1e9
+    h2d = sum(((sp.ng + 7) // 8) * 8 * 4 * 3 + 4 * 51 + 8 * sp.ng for sp in specs) // n
+    d2h = sum(sp.ng + 64 for sp in specs) // n
     line = {
         "metric": "served solves/s and p50/p99 latency (Poisson arrivals, 300 generations)",
         "value": served["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
+        "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
         "config": {"workload": "c5: %d requests, sizes as c4, Poisson arrivals at %.1f/s" % (n, rate),
-                   "parallelism": "continuous batching, 25 generations per step"},
+                   "parallelism": "continuous batching, 25 generations per step",
+                   "l2": "arrival-driven: no flush (the resident set changes every step)"},
         "served": served,
         "serial_per_request": dict(serial, requests=m),
         "arrival_rate_per_s": rate,
+        # the whole stream goes through the public API (submit from host arrays, poll the
+        # result back), so value is itself end to end; the bytes are per request
+        "e2e": {"value": served["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": "qieo_server_submit (host arrays) ... qieo_server_poll (best record and "
+                        "alleles), wall clock over the stream; bytes are per request"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src,
+                     "traffic": None, "kernel": "batch_generation_kernel (server steps)",
+                     "note": "4 B per served gene-update over the stream's span, idle gaps between "
+                             "arrivals included"},
+        "gpu_launches": stats["kernel_launches"],
+        "server_stats": stats,
+        "clocks": clocks,
     }
+    if not a.no_cpu_baseline:
+        rate_cpu, cores, sample = batch_oracle_sample(specs, G)
+        line["cpu_baseline"] = {"value": rate_cpu, "unit": "solves/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
 
 

@@ -241,6 +241,18 @@ qieo_status qieo_server_submit(qieo_server *server, const qieo_problem *problem,
 qieo_status qieo_server_poll(qieo_server *server, int64_t id, int32_t wait_ms, uint8_t *bits_out,
                              qieo_solve_result *result);
 
+/* Counters of a server since its creation. kernel_launches counts every kernel the server
+ * put on the GPU (one initialisation per admitted solve; per step and group of members,
+ * one batched launch per generation plus the final rotation). */
+typedef struct {
+    int64_t submitted, admitted, completed, steps, kernel_launches;
+    int32_t queued, active;   /* now */
+    int32_t max_active;       /* most resident solves seen at once */
+    int32_t reserved;
+} qieo_server_stats;
+
+qieo_status qieo_server_get_stats(qieo_server *server, qieo_server_stats *out);
+
 /* Cancels a request that is still queued (QIEO_ERR_BUSY once it runs). */
 qieo_status qieo_server_cancel(qieo_server *server, int64_t id);
 

@@ -191,9 +191,10 @@ qieo_status configure(qieo_instance *q)
     const int rpp = qieo::kThreads / tile;
     const int ntile = (q->svec + tile - 1) / tile;
     // 16-bit packed sums inside a warp need items <= 255 (256 genes * 255 < 2^16); the
-    // packed row word needs row sums < 2^28 and at most 255 tiles per row.
+    // packed row word (count << 52 | SV << 26 | SW) needs row sums < 2^26 and at most 4095
+    // tiles per row.
     q->narrow = (!(q->flags & QIEO_FLAG_FORCE_WIDE) && q->narrow_items &&
-                 q->sum_w < (1ll << 28) && q->sum_v < (1ll << 28) && ntile <= 255) ? 1 : 0;
+                 q->sum_w < (1ll << 26) && q->sum_v < (1ll << 26) && ntile <= 4095) ? 1 : 0;
     const int64_t units = (int64_t)ntile * q->np;
     const size_t row_bytes = q->narrow ? 8 : 16;
 
@@ -1001,7 +1002,7 @@ struct qieo_batch {
         int32_t grid = 1;
         size_t smem = 0;
         int32_t seg_rows_max = 1;
-        void *dev = nullptr;                        // params | segs | block_begin | inst_segs
+        void *dev = nullptr;                        // params | segs | queue | inst_segs
         std::vector<qieo::GenParams> host_params;   // what is on the device
         qieo::BatchArgs args{};
     };
@@ -1038,77 +1039,61 @@ void (*batch_kernel_of(bool narrow, int rule, bool cip))(qieo::BatchArgs)
     return cip ? PickBatch<false, 0, true>::get() : PickBatch<false, 0, false>::get();
 }
 
-// Cuts the members' tile-rows into segments and deals them to `grid` blocks by cost
-// (active vectors per row plus a fixed per-row and per-segment overhead).
+// Cuts the members' tile-rows into segments of about a quarter of a block's average share
+// (by cost: active vectors per row plus a fixed per-row overhead) and orders them largest
+// first for the kernel's segment queue.
 void partition(const std::vector<qieo_instance *> &members, int grid,
-               std::vector<qieo::BatchSeg> &segs, std::vector<int32_t> &block_begin,
-               std::vector<int32_t> &inst_segs, int32_t &seg_rows_max)
+               std::vector<qieo::BatchSeg> &segs, std::vector<int32_t> &inst_segs,
+               int32_t &seg_rows_max)
 {
-    struct Piece {
-        int32_t inst, tile, rows, np_rows, rpp;
-        double row_cost;
+    struct Cut {
+        qieo::BatchSeg seg;
+        double cost;
     };
-    std::vector<Piece> pieces;
+    // one pass covers rpp rows of a tile; its cost is the block's 256 thread-slots, of
+    // which the ragged last tile of a row leaves some idle
+    auto row_cost = [](const qieo_instance *q, int tile) {
+        const int tv = q->lanes * q->warps;
+        const int active = std::min(tv, q->svec - tile * tv);
+        return (double)qieo::kThreads * (0.25 + 0.75 * (double)active / tv) / (qieo::kThreads / tv);
+    };
     double total = 0.0;
+    for (const qieo_instance *q : members) {
+        const int tv = q->lanes * q->warps;
+        const int ntile = (q->svec + tv - 1) / tv;
+        for (int tile = 0; tile < ntile; ++tile) total += row_cost(q, tile) * q->np;
+    }
+    // About four segments per block on average: enough for the queue to even out the
+    // blocks' loads, few enough that the per-segment flush stays small.
+    const double target = std::max(1.0, total / (4.0 * grid));
+    std::vector<Cut> cuts;
+    inst_segs.assign(members.size(), 0);
+    seg_rows_max = 1;
     for (size_t i = 0; i < members.size(); ++i) {
         const qieo_instance *q = members[i];
         const int tv = q->lanes * q->warps;
-        const int ntile = (q->svec + tv - 1) / tv;
         const int rpp = qieo::kThreads / tv;
+        const int ntile = (q->svec + tv - 1) / tv;
+        const int max_rows = std::max(rpp, qieo::kMaxSegRows / rpp * rpp);
         for (int tile = 0; tile < ntile; ++tile) {
-            const int active = std::min(tv, q->svec - tile * tv);
-            // one pass covers rpp rows; its cost is the block's 256 thread-slots
-            const double pass_cost = (double)qieo::kThreads * (0.25 + 0.75 * (double)active / tv);
-            const double row_cost = pass_cost / rpp;
-            pieces.push_back({(int32_t)i, tile, q->np, q->np, rpp, row_cost});
-            total += row_cost * q->np + 2048.0;
-        }
-    }
-    // Greedy packing of the pieces in order into blocks of at most `quota` cost (a segment
-    // costs its rows plus a fixed overhead); the smallest quota that fits the grid is found
-    // by bisection.
-    const double seg_overhead = 2048.0;
-    auto pack = [&](double quota, bool emit) -> int64_t {
-        int64_t blk = 0;
-        double used = 0.0;
-        if (emit) {
-            segs.clear();
-            block_begin.assign((size_t)grid + 1, 0);
-            inst_segs.assign(members.size(), 0);
-            seg_rows_max = 1;
-        }
-        for (const Piece &pc : pieces) {
-            int32_t ra = 0;
-            while (ra < pc.np_rows) {
-                int64_t fit = (int64_t)std::max(0.0, (quota - used - seg_overhead) / pc.row_cost);
-                fit = fit / pc.rpp * pc.rpp;
-                if (fit < pc.rpp && used > 0.0) {       // this block is full
-                    ++blk;
-                    if (emit && blk <= grid) block_begin[(size_t)blk] = (int32_t)segs.size();
-                    used = 0.0;
-                    continue;
-                }
-                int32_t rows = (int32_t)std::min<int64_t>(pc.np_rows - ra, std::max<int64_t>(fit, pc.rpp));
-                rows = std::min(rows, qieo::kMaxSegRows / pc.rpp * pc.rpp);
-                if (emit) {
-                    segs.push_back({pc.inst, pc.tile, ra, rows});
-                    inst_segs[(size_t)pc.inst] += 1;
-                    seg_rows_max = std::max(seg_rows_max, rows);
-                }
-                used += seg_overhead + rows * pc.row_cost;
-                ra += rows;
+            const double rc = row_cost(q, tile);
+            int want = (int)std::min<double>(max_rows, std::max<double>(rpp, target / rc));
+            want = std::max(rpp, want / rpp * rpp);
+            const int nseg = (q->np + want - 1) / want;
+            int rows = (q->np + nseg - 1) / nseg;
+            rows = std::min(max_rows, (rows + rpp - 1) / rpp * rpp);
+            for (int ra = 0; ra < q->np; ra += rows) {
+                const int r = std::min(rows, q->np - ra);
+                cuts.push_back({{(int32_t)i, tile, ra, r}, rc * r});
+                inst_segs[i] += 1;
+                seg_rows_max = std::max(seg_rows_max, r);
             }
         }
-        return blk + 1;
-    };
-    double lo = total / grid, hi = 2.0 * total + seg_overhead;
-    for (int it = 0; it < 60 && hi - lo > 1.0; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (pack(mid, false) <= grid) hi = mid;
-        else lo = mid;
     }
-    const int64_t used_blocks = pack(hi, true);
-    for (int64_t b = used_blocks; b <= grid; ++b) block_begin[(size_t)b] = (int32_t)segs.size();
+    std::stable_sort(cuts.begin(), cuts.end(), [](const Cut &x, const Cut &y) { return x.cost > y.cost; });
+    segs.clear();
+    segs.reserve(cuts.size());
+    for (const Cut &c : cuts) segs.push_back(c.seg);
 }
 
 qieo_status upload_group(qieo_batch *bt, qieo_batch::Group &g)
@@ -1141,13 +1126,13 @@ qieo_status build_group(qieo_batch *bt, qieo_batch::Group &g)
                                                            qieo::kThreads, smem_max));
     g.grid = std::max(1, bps) * std::max(1, q0->sm_count);
     std::vector<qieo::BatchSeg> segs;
-    std::vector<int32_t> block_begin, inst_segs;
-    partition(g.members, g.grid, segs, block_begin, inst_segs, g.seg_rows_max);
+    std::vector<int32_t> inst_segs;
+    partition(g.members, g.grid, segs, inst_segs, g.seg_rows_max);
     g.smem = qieo::kRingBytes + (size_t)g.seg_rows_max * row_bytes;
     const size_t n = g.members.size();
     size_t off[4], total = 0;
     const size_t sizes[4] = {n * sizeof(qieo::GenParams), segs.size() * sizeof(qieo::BatchSeg),
-                             block_begin.size() * sizeof(int32_t), n * sizeof(int32_t)};
+                             2 * sizeof(unsigned int), n * sizeof(int32_t)};
     for (int i = 0; i < 4; ++i) {
         off[i] = total;
         total = align_up(total + sizes[i], 256);
@@ -1156,11 +1141,12 @@ qieo_status build_group(qieo_batch *bt, qieo_batch::Group &g)
     char *d = (char *)g.dev;
     g.args.params = (const qieo::GenParams *)(d + off[0]);
     g.args.segs = (const qieo::BatchSeg *)(d + off[1]);
-    g.args.block_begin = (const int32_t *)(d + off[2]);
+    g.args.queue = (unsigned int *)(d + off[2]);
     g.args.inst_segs = (const int32_t *)(d + off[3]);
+    g.args.nsegs = (int32_t)segs.size();
     g.args.seg_rows_max = g.seg_rows_max;
     CUDA_TRY(cudaMemcpyAsync(d + off[1], segs.data(), sizes[1], cudaMemcpyHostToDevice, bt->stream));
-    CUDA_TRY(cudaMemcpyAsync(d + off[2], block_begin.data(), sizes[2], cudaMemcpyHostToDevice, bt->stream));
+    CUDA_TRY(cudaMemsetAsync(d + off[2], 0, sizes[2], bt->stream));
     CUDA_TRY(cudaMemcpyAsync(d + off[3], inst_segs.data(), sizes[3], cudaMemcpyHostToDevice, bt->stream));
     qieo_status st = upload_group(bt, g);
     if (st != QIEO_OK) return st;
@@ -1475,6 +1461,8 @@ struct qieo_server {
     std::chrono::steady_clock::time_point t0;
     std::thread worker;
     int bps[2] = {1, 1};                 // batch kernel blocks per SM: [wide, narrow]
+    int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_steps = 0, n_launches = 0;
+    int32_t max_active_seen = 0;
 };
 
 namespace {
@@ -1494,8 +1482,10 @@ void destroy_instance_nosync(qieo_instance *q)
 
 // Enqueues `G` generations (+ the final rotation) of every member on the server stream
 // with the batched kernel; the work list goes through the next double-buffered region.
-qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance *> &members, int32_t G)
+qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance *> &members, int32_t G,
+                                int64_t *launched)
 {
+    *launched = 0;
     const int r = S->wl_next;
     S->wl_next ^= 1;
     char *host = S->wl_host[r];
@@ -1517,11 +1507,11 @@ qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance 
             if (grp.empty()) continue;
             const int grid = S->bps[narrow] * S->sm_count;
             std::vector<qieo::BatchSeg> segs;
-            std::vector<int32_t> block_begin, inst_segs;
+            std::vector<int32_t> inst_segs;
             int32_t seg_rows_max = 1;
-            partition(grp, grid, segs, block_begin, inst_segs, seg_rows_max);
+            partition(grp, grid, segs, inst_segs, seg_rows_max);
             const size_t sizes[4] = {grp.size() * sizeof(qieo::GenParams), segs.size() * sizeof(qieo::BatchSeg),
-                                     block_begin.size() * sizeof(int32_t), inst_segs.size() * sizeof(int32_t)};
+                                     2 * sizeof(unsigned int), inst_segs.size() * sizeof(int32_t)};
             size_t off[4];
             for (int i = 0; i < 4; ++i) {
                 off[i] = used;
@@ -1532,7 +1522,7 @@ qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance 
             for (size_t i = 0; i < grp.size(); ++i)
                 std::memcpy(host + off[0] + i * sizeof(qieo::GenParams), &grp[i]->gp, sizeof(qieo::GenParams));
             std::memcpy(host + off[1], segs.data(), sizes[1]);
-            std::memcpy(host + off[2], block_begin.data(), sizes[2]);
+            std::memset(host + off[2], 0, sizes[2]);   // the segment queue starts empty
             std::memcpy(host + off[3], inst_segs.data(), sizes[3]);
             Launch L;
             L.narrow = narrow != 0;
@@ -1541,8 +1531,9 @@ qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance 
             L.smem = qieo::kRingBytes + (size_t)seg_rows_max * (narrow ? 8 : 16);
             L.args.params = (const qieo::GenParams *)(dev + off[0]);
             L.args.segs = (const qieo::BatchSeg *)(dev + off[1]);
-            L.args.block_begin = (const int32_t *)(dev + off[2]);
+            L.args.queue = (unsigned int *)(dev + off[2]);
             L.args.inst_segs = (const int32_t *)(dev + off[3]);
+            L.args.nsegs = (int32_t)segs.size();
             L.args.seg_rows_max = seg_rows_max;
             launches.push_back(L);
         }
@@ -1568,6 +1559,7 @@ qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance 
         else qieo::batch_cip_kernel<0><<<L.grid, qieo::kThreads, 0, S->stream>>>(L.args);
         CUDA_TRY(cudaGetLastError());
     }
+    *launched = (int64_t)launches.size() * (G + 1);
     return QIEO_OK;
 }
 
@@ -1602,6 +1594,7 @@ void retire_oldest_step(qieo_server *S)
         R->status = st;
         R->state = st == QIEO_OK ? QIEO_SOLVE_DONE : QIEO_SOLVE_FAILED;
         R->t_done = server_now(S);
+        if (st == QIEO_OK) S->n_completed += 1;
     }
     S->spare_events.push_back(rec.done);
     S->cv_done.notify_all();
@@ -1644,6 +1637,9 @@ void server_loop(qieo_server *S)
                 R->remaining = R->gens;
                 R->state = QIEO_SOLVE_RUNNING;
                 S->active.push_back(R);
+                S->n_admitted += 1;
+                S->n_launches += 1;   // the instance's generation-0 initialisation
+                S->max_active_seen = std::max(S->max_active_seen, (int32_t)S->active.size());
             } else {
                 S->alloc.release(R->off, R->bytes);
                 R->status = st;
@@ -1660,7 +1656,8 @@ void server_loop(qieo_server *S)
                 members.push_back(R->inst);
             }
             StepRecord rec;
-            qieo_status st = enqueue_server_step(S, members, G);
+            int64_t launched = 0;
+            qieo_status st = enqueue_server_step(S, members, G, &launched);
             if (st == QIEO_OK) {
                 if (S->spare_events.empty()) {
                     cudaEvent_t ev = nullptr;
@@ -1688,8 +1685,13 @@ void server_loop(qieo_server *S)
                 else still.push_back(R);
             }
             S->active.swap(still);
-            if (st == QIEO_OK) S->inflight.push_back(rec);
-            else S->cv_done.notify_all();
+            S->n_launches += launched;
+            if (st == QIEO_OK) {
+                S->n_steps += 1;
+                S->inflight.push_back(rec);
+            } else {
+                S->cv_done.notify_all();
+            }
         } else if (!S->inflight.empty()) {
             retire_oldest_step(S);
         }
@@ -1787,6 +1789,7 @@ qieo_status qieo_server_submit(qieo_server *S, const qieo_problem *pr, const qie
     if (S->stop) return fail(QIEO_ERR_INVALID, "server is stopping");
     R->id = S->next_id++;
     R->t_submit = server_now(S);
+    S->n_submitted += 1;
     *id_out = R->id;
     S->queue.push_back(R.get());
     S->all[R->id] = std::move(R);
@@ -1814,6 +1817,22 @@ qieo_status qieo_server_poll(qieo_server *S, int64_t id, int32_t wait_ms, uint8_
     res->admit_s = R->t_admit;
     res->done_s = R->t_done;
     if (bits_out && R->state == QIEO_SOLVE_DONE) unpack_row(R->best_row.data(), R->prob.ng, bits_out);
+    return QIEO_OK;
+}
+
+qieo_status qieo_server_get_stats(qieo_server *S, qieo_server_stats *out)
+{
+    if (!S || !out) return fail(QIEO_ERR_INVALID, "server and out must be non-NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    out->submitted = S->n_submitted;
+    out->admitted = S->n_admitted;
+    out->completed = S->n_completed;
+    out->steps = S->n_steps;
+    out->kernel_launches = S->n_launches;
+    out->queued = (int32_t)S->queue.size();
+    out->active = (int32_t)S->active.size();
+    out->max_active = S->max_active_seen;
+    out->reserved = 0;
     return QIEO_OK;
 }
 

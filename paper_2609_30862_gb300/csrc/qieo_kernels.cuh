@@ -24,7 +24,7 @@
 //   xbits  [2][np][xstride]: alleles of generation t in plane t & 1; bit i of byte v is
 //          gene 8v + i; rows padded to 16 bytes.
 //   items  narrow: uint32 (v << 16 | w) per gene; wide: int32 w[], int32 v[].
-//   acc    narrow: uint64 (count << 56 | SV << 28 | SW) per row; wide: int64 SW, SV per row
+//   acc    narrow: uint64 (count << 52 | SV << 26 | SW) per row; wide: int64 SW, SV per row
 //          plus a uint32 count per row.
 //
 // Work split: a generation is ntile * np tile-rows (tile = lanes*warps vectors of one row).
@@ -149,12 +149,12 @@ template <bool kNarrow>
 __device__ __forceinline__ void combine_row(const GenParams &p, int32_t c, uint64_t sw, uint64_t sv)
 {
     if (kNarrow) {
-        const unsigned long long add = (1ull << 56) | (sv << 28) | sw;
+        const unsigned long long add = (1ull << 52) | (sv << 26) | sw;
         const unsigned long long old = atomicAdd(p.acc + c, add);
-        if ((int32_t)(old >> 56) == p.ntile - 1) {
+        if ((int32_t)(old >> 52) == p.ntile - 1) {
             const unsigned long long full = old + add;
             p.acc[c] = 0ull;
-            finish_row(p, c, (int64_t)(full & 0xfffffffull), (int64_t)((full >> 28) & 0xfffffffull));
+            finish_row(p, c, (int64_t)(full & 0x3ffffffull), (int64_t)((full >> 26) & 0x3ffffffull));
         }
     } else {
         atomicAdd(p.acc + 2 * (size_t)c, (unsigned long long)sw);
@@ -985,11 +985,12 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
 // ---------------------------------------------------------------------------------------
 // Batched form: many independent instances in one persistent launch per generation. The
 // host cuts every instance's ntile * np tile-rows into segments (one tile, at most
-// kMaxSegRows rows each) and gives each block a contiguous run of segments of about
-// equal cost. A block switches instance between segments (parameters, threshold table,
-// tile geometry); each instance's ticket counts its finished segments, and the block that
-// finishes an instance's last segment closes that instance's generation. Instances of one
-// launch share the item-sum form and the rotation rule (the host groups them).
+// kMaxSegRows rows each) of a few per block on average, ordered largest first; blocks take
+// them from a queue. A block switches instance between segments (parameters, threshold
+// table, tile geometry); each instance's ticket counts its finished segments, and the
+// block that finishes an instance's last segment closes that instance's generation.
+// Instances of one launch share the item-sum form and the rotation rule (the host groups
+// them).
 // ---------------------------------------------------------------------------------------
 struct BatchSeg {
     int32_t inst, tile, ra, rows;
@@ -997,9 +998,11 @@ struct BatchSeg {
 
 struct BatchArgs {
     const GenParams *params;      // [n] per-instance parameters
-    const BatchSeg *segs;         // segments, block-major
-    const int32_t *block_begin;   // [grid + 1] first segment of each block
+    const BatchSeg *segs;         // [nsegs] segments, largest first
     const int32_t *inst_segs;     // [n] segments per instance
+    unsigned int *queue;          // [2] next segment to take, blocks finished (both 0
+                                  // between launches: the last block clears them)
+    int32_t nsegs;
     int32_t seg_rows_max;
 };
 
@@ -1012,12 +1015,21 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
     SmemParts m = carve_smem<true>(smem_raw);
     const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
     uint4 *slots = m.ring + threadIdx.x;
+    __shared__ int32_t s_si;
     grid_dependency_wait();
     clear_row_sums<kNarrow>(a.seg_rows_max, m.acc32, m.acc64);
     int countdown = 0;
     int32_t cur_inst = -1;
     int32_t table_K = -1;
-    for (int32_t si = a.block_begin[blockIdx.x]; si < a.block_begin[blockIdx.x + 1]; ++si) {
+    // Segments are taken from a shared queue in order (largest first), so blocks that draw
+    // cheap segments (saturated instances, small rows) take more of them. The index is
+    // read by every thread before the segment's first barrier, after which thread 0 may
+    // overwrite it.
+    for (;;) {
+        if (threadIdx.x == 0) s_si = (int32_t)atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const int32_t si = s_si;
+        if (si >= a.nsegs) break;
         const BatchSeg sg = a.segs[si];
         const GenParams &p = a.params[sg.inst];
         if (sg.inst != cur_inst) {
@@ -1057,6 +1069,15 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
         }
     }
     allow_dependent_launch();
+    // The last block to finish clears the queue for the next launch (which reads it only
+    // after this grid has completed).
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 1, 1u) == gridDim.x - 1u) {
+            a.queue[0] = 0u;
+            a.queue[1] = 0u;
+        }
+    }
 }
 
 // Final rotation of a batched run over the same segments.
@@ -1064,7 +1085,7 @@ template <int kRule>
 __global__ void __launch_bounds__(kThreads) batch_cip_kernel(const BatchArgs a)
 {
     grid_dependency_wait();
-    for (int32_t si = a.block_begin[blockIdx.x]; si < a.block_begin[blockIdx.x + 1]; ++si) {
+    for (int32_t si = blockIdx.x; si < a.nsegs; si += gridDim.x) {
         const BatchSeg sg = a.segs[si];
         const GenParams &p = a.params[sg.inst];
         const int32_t t_last = *p.gen - 1;

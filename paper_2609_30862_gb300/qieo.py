@@ -40,7 +40,7 @@ EXPORTS = (
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
     "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
-    "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
+    "qieo_server_get_stats", "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
 )
 
 QIEO_SOLVE_QUEUED = 0
@@ -77,6 +77,12 @@ class qieo_launch_shape(C.Structure):
 
 class qieo_server_config(C.Structure):
     _fields_ = [("memory_bytes", C.c_int64), ("max_active", C.c_int32), ("gens_per_step", C.c_int32)]
+
+
+class qieo_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("steps", C.c_int64), ("kernel_launches", C.c_int64), ("queued", C.c_int32),
+                ("active", C.c_int32), ("max_active", C.c_int32), ("reserved", C.c_int32)]
 
 
 class qieo_solve_result(C.Structure):
@@ -129,6 +135,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_server_create": ([P, P], C.c_int),
         "qieo_server_submit": ([P, P, P, i32, P], C.c_int),
         "qieo_server_poll": ([P, i64, i32, P, P], C.c_int),
+        "qieo_server_get_stats": ([P, P], C.c_int),
         "qieo_server_cancel": ([P, i64], C.c_int),
         "qieo_server_destroy": ([P], C.c_int),
         "qieo_last_error": ([], C.c_char_p),
@@ -306,6 +313,12 @@ def qieo_server_poll(h, rid: int, wait_ms: int = 0, ng: int = 0):
     return res, (bits[:ng] if ng else None)
 
 
+def qieo_server_get_stats(h) -> qieo_server_stats:
+    st = qieo_server_stats()
+    _check(load().qieo_server_get_stats(h, C.byref(st)))
+    return st
+
+
 def qieo_server_cancel(h, rid: int) -> None:
     _check(load().qieo_server_cancel(h, int(rid)))
 
@@ -336,6 +349,10 @@ class Server:
 
     def cancel(self, rid: int) -> None:
         qieo_server_cancel(self.h, rid)
+
+    def stats(self) -> dict:
+        st = qieo_server_get_stats(self.h)
+        return {name: getattr(st, name) for name, _ in st._fields_ if name != "reserved"}
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None:

@@ -82,6 +82,9 @@ _LAYOUT_PROG = r"""
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(qieo_problem), sizeof(qieo_params),
          sizeof(qieo_launch_shape), offsetof(qieo_params, stream), offsetof(qieo_problem, capacity));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qieo_server_config), sizeof(qieo_solve_result),
+         offsetof(qieo_solve_result, submit_s), sizeof(qieo_server_stats),
+         offsetof(qieo_server_stats, queued), offsetof(qieo_server_stats, max_active));
   return 0;
 }
 """
@@ -98,5 +101,8 @@ def test_struct_layout_matches_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [C.sizeof(Q.qieo_problem), C.sizeof(Q.qieo_params), C.sizeof(Q.qieo_launch_shape),
-            Q.qieo_params.stream.offset, Q.qieo_problem.capacity.offset]
+            Q.qieo_params.stream.offset, Q.qieo_problem.capacity.offset,
+            C.sizeof(Q.qieo_server_config), C.sizeof(Q.qieo_solve_result),
+            Q.qieo_solve_result.submit_s.offset, C.sizeof(Q.qieo_server_stats),
+            Q.qieo_server_stats.queued.offset, Q.qieo_server_stats.max_active.offset]
     assert got == want

@@ -163,12 +163,25 @@ def test_scan_mode_elite():
     compare(prob, 45, [25], seed=13, lam=2**30)
 
 
-def test_many_tiles_force_wide_sums():
-    """One lane per row tile and 263 tiles per row: more tiles than the packed row word
-    counts, so the 64-bit row sums are used."""
+def test_many_tiles_packed_and_wide_sums():
+    """One lane per row tile. 263 tiles per row fit the 12-bit tile count of the packed row
+    word; 4,100 tiles do not, so the 64-bit row sums are used."""
     prob = W.knapsack(2100, 14)
     shape = compare(prob, 12, [8], seed=14, shape=(1, 1, 0))
-    assert shape.tiles == 263 and shape.narrow == 0
+    assert shape.tiles == 263 and shape.narrow == 1
+    prob = W.knapsack(32800, 15)
+    shape = compare(prob, 12, [3], seed=15, shape=(1, 1, 0))
+    assert shape.tiles == 4100 and shape.narrow == 0
+
+
+@pytest.mark.parametrize("ng,narrow", [(263000, 1), (263200, 0)])
+def test_packed_row_sum_limit(ng, narrow):
+    """Items of 255 everywhere: total weight just below 2^26 keeps the packed row word,
+    just above it switches to the 64-bit row sums. Both match the oracle."""
+    w = np.full(ng, 255, dtype=np.int32)
+    prob = W.custom_problem(w, w.copy(), int(w.sum()) // 2)
+    shape = compare(prob, 4, [3], seed=16)
+    assert shape.narrow == narrow
 
 
 def test_narrow_boundary_items():

@@ -84,3 +84,21 @@ def test_server_cancel_queued_only():
             assert e.value.status == Q.QIEO_ERR_BUSY
         for rid in [first] + queued[:-1]:
             assert srv.poll(rid, wait_ms=60000)[0].state == Q.QIEO_SOLVE_DONE
+
+
+def test_server_counts_steps_and_launches():
+    """The server's counters agree with what it was asked to do: every request admitted and
+    completed, at least one step per gens_per_step generations, and per step one batched
+    launch per generation plus the final rotation (one group here: narrow items, R1)."""
+    srv = Q.Server(gens_per_step=10)
+    probs = [W.knapsack(200 + 37 * i, 300 + i) for i in range(6)]
+    ids = [srv.submit(p, 40, 30, seed=3, inst=i) for i, p in enumerate(probs)]
+    for rid in ids:
+        res, _ = srv.poll(rid, wait_ms=60000)
+        assert res.state == Q.QIEO_SOLVE_DONE
+    st = srv.stats()
+    srv.close()
+    assert st["submitted"] == st["admitted"] == st["completed"] == 6
+    assert st["queued"] == 0 and st["active"] == 0 and 1 <= st["max_active"] <= 6
+    assert st["steps"] >= 3
+    assert st["kernel_launches"] >= 6 + st["steps"] * 2
