@@ -57,7 +57,19 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0,
+                    help="--impl reference: seconds of oracle work over warm-up + timed steps")
     return ap.parse_args()
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest of one float over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
 
 
 def workload_config(name: str) -> dict:
@@ -203,7 +215,7 @@ def run_reference(a):
     prob = WL.knapsack(c["ng"], c["item_seed"])
     cores = os.cpu_count() or 1
     O.build()
-    budget_s = 150.0
+    budget_s = a.ref_budget_s
     t0 = time.perf_counter()
     O.run(prob, c["np"], 1, seed=c["seed"], inst=c["inst"], kind="omp", threads=cores)
     t1 = time.perf_counter() - t0
@@ -242,7 +254,7 @@ def run_reference_solves(a):
     O.build()
     G = 300
     specs = WL.batch_manifest(256 if a.workload == "c4" else a.requests, first_seed=1)
-    budget_s = 150.0 / max(1, a.steps + a.warmup)
+    budget_s = a.ref_budget_s / max(1, a.steps + a.warmup)
     pos, times, counts = 0, [], []
     for k in range(a.warmup + a.steps):
         t0, done = time.perf_counter(), 0
@@ -336,10 +348,8 @@ def run_gpu(a):
     step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
     run_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
     total_ms = float(sum(step_ms))
-    tot = torch.tensor([total_ms, float(sum(run_ms))], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    total_ms, run_total_ms = float(tot[0]), float(tot[1])
+    total_ms = max_over_ranks(total_ms, dist)
+    run_total_ms = max_over_ranks(float(sum(run_ms)), dist)
     value = world * genes_per_step * a.steps / (total_ms / 1e3)
 
     # Roofline of the fused generation kernel. A run is G launches of generation_kernel +
@@ -386,10 +396,7 @@ def run_gpu(a):
             torch.cuda.synchronize()
             if i > 0:
                 e2e_times.append(time.perf_counter() - t0)
-    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = (world * genes_per_step * len(e2e_times) / float(e2e_t[0])
+    e2e_value = (world * genes_per_step * len(e2e_times) / max_over_ranks(sum(e2e_times), dist)
                  if e2e_times else None)
     svec = (ng + 7) // 8
     h2d = svec * 8 * 4 * (1 if shape.narrow else 2) + 4 * (2 * 25 + 1)
@@ -493,12 +500,6 @@ def run_batched(a):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t[0])
-
     with torch.cuda.stream(stream):
         for _ in range(a.warmup):
             for i in insts:
@@ -520,8 +521,8 @@ def run_batched(a):
             evs[k][2].record(stream)
         barrier()
         clocks = sampler.stop() if sampler else None
-        tb = max_over_ranks(sum(e0.elapsed_time(e2) for e0, _, e2 in evs) / 1e3)
-        run_s = max_over_ranks(sum(e1.elapsed_time(e2) for _, e1, e2 in evs) / 1e3)
+        tb = max_over_ranks(sum(e0.elapsed_time(e2) for e0, _, e2 in evs) / 1e3, dist)
+        run_s = max_over_ranks(sum(e1.elapsed_time(e2) for _, e1, e2 in evs) / 1e3, dist)
 
         # one launch sequence per instance, same members and results
         single_steps = max(1, a.steps // 5)
@@ -534,7 +535,7 @@ def run_batched(a):
                 i.run(G)
         ev[1].record(stream)
         barrier()
-        ts = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3)
+        ts = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, dist)
         ok = all(i.best()[1] >= 0 for i in insts)
     batch.close()
     for i in insts:
@@ -558,7 +559,7 @@ def run_batched(a):
             torch.cuda.synchronize()
             if k > 0:
                 e2e_times.append(time.perf_counter() - t0)
-    e2e_value = (world * n * len(e2e_times) / max_over_ranks(sum(e2e_times))
+    e2e_value = (world * n * len(e2e_times) / max_over_ranks(sum(e2e_times), dist)
                  if e2e_times else None)
     h2d = sum(((sp.ng + 7) // 8) * 8 * 4 * 3 + 4 * 51 for sp in specs)
     d2h = sum(((sp.ng + 7) // 8 + 15) // 16 * 16 + 24 for sp in specs)

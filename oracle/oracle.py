@@ -68,6 +68,11 @@ def _lib(kind: str = "serial") -> C.CDLL:
             L.qo_run_fp64.argtypes = [i32, P, P, i64, i32, i32, i64, u32, u32, i32, i32,
                                       P, P, P, P, P, P, P, P, P, P, P]
             L.qo_run_fp64.restype = C.c_int
+            L.qo_rows_observe.argtypes = [i32, P, P, i64, i32, i64, u32, u32, i32, i32, i32,
+                                          P, P, P]
+            L.qo_rows_observe.restype = C.c_int
+            L.qo_rows_rotate.argtypes = [i32, i32, i32, i32, P, P, P]
+            L.qo_rows_rotate.restype = C.c_int
             L.qo_set_threads.argtypes = [i32]
             L.qo_set_threads.restype = C.c_int
             L.qo_is_openmp.argtypes = []
@@ -118,6 +123,33 @@ def bruteforce(w, v, W: int, lam: int = 1):
     x = np.zeros(w.shape[0], dtype=np.uint8)
     best = int(_lib().qo_bruteforce(int(w.shape[0]), _p(w), _p(v), int(W), int(lam), _p(x)))
     return best, x
+
+
+def rows_observe(problem, k_rows, gen: int, c0: int, seed: int = 1, inst: int = 0,
+                 D: int = 100, lam: int = 1):
+    """QIP + Evaluation of rows c0 .. c0 + nr of a population (k_rows[nr, ng]); returns
+    (x[nr, ng], f[nr]). Draws use the global chromosome index."""
+    k = np.ascontiguousarray(k_rows, dtype=np.int16)
+    nr, ng = k.shape
+    w = np.ascontiguousarray(problem.weights, dtype=np.int32)
+    v = np.ascontiguousarray(problem.values, dtype=np.int32)
+    x = np.zeros((nr, ng), dtype=np.uint8)
+    f = np.zeros(nr, dtype=np.int64)
+    if _lib().qo_rows_observe(ng, _p(w), _p(v), int(problem.capacity), int(D), int(lam),
+                              int(seed) & 0xFFFFFFFF, int(inst) & 0xFFFFFFFF, int(gen), int(c0),
+                              int(nr), _p(k), _p(x), _p(f)) != 0:
+        raise ValueError("invalid arguments")
+    return x, f
+
+
+def rows_rotate(k_rows: np.ndarray, x_rows, x_elite, D: int = 100, rule: int = 0) -> None:
+    """CIP of a row block toward the elite's alleles, in place on k_rows[nr, ng] (int16)."""
+    assert k_rows.dtype == np.int16 and k_rows.flags.c_contiguous
+    nr, ng = k_rows.shape
+    x = np.ascontiguousarray(x_rows, dtype=np.uint8)
+    xe = np.ascontiguousarray(x_elite, dtype=np.uint8)
+    if _lib().qo_rows_rotate(ng, int(D), int(rule), nr, _p(k_rows), _p(x), _p(xe)) != 0:
+        raise ValueError("invalid arguments")
 
 
 class State:

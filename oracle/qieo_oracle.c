@@ -14,7 +14,7 @@
  *     table step toward the elite's allele), then terminate or loop.
  *   - Eq. (1): f = sum(v x) if sum(w x) <= W, else -lambda (sum(w x) - W).
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent (labelled S1 .. S14 in this file):
  *   S1  dtheta = pi / D (D = 100 for all named workloads); start angle pi/4.
  *   S2  theta stays in [0, pi/2]; a step that would leave it is not taken.
  *   S3  rule R1: every qubit moves one step toward the elite's allele (+ if it is 1,
@@ -231,6 +231,53 @@ int qo_run(int32_t ng, const int32_t *w, const int32_t *v, int64_t W,
         *t = gen + 1;
     }
     free(T);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * The same generation split by rows, for an instance whose population is divided into
+ * row blocks (one per process): the QIP and Evaluation bullets of Sec. III-B on rows
+ * [c0, c0 + nr) only, and the CIP bullet on a block toward an elite row that the caller
+ * found over all blocks. Draws stay keyed by the global chromosome index (reading S7), so
+ * the blocks together compute exactly what qo_run computes for the whole population.
+ *
+ * qo_rows_observe: in k[nr*ng] (the block's angle indices); out x[nr*ng], f[nr].
+ * qo_rows_rotate:  in/out k[nr*ng]; in x[nr*ng] (the block's alleles of the same
+ *                  generation) and xe[ng] (the elite's alleles).
+ * ---------------------------------------------------------------------------------- */
+int qo_rows_observe(int32_t ng, const int32_t *w, const int32_t *v, int64_t W, int32_t D,
+                    int64_t lambda, uint32_t seed, uint32_t inst, int32_t gen, int32_t c0,
+                    int32_t nr, const int16_t *k, uint8_t *x, int64_t *f)
+{
+    if (check_args(ng, w, 1, D, lambda, 0) || c0 < 0 || nr < 0) return 1;
+    const int32_t K = D / 4;
+    uint64_t *T = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(2 * K + 1));
+    qo_threshold_table(D, T);
+    for (int32_t i = 0; i < nr; ++i) {
+        const int16_t *ki = k + (size_t)i * ng;
+        uint8_t *xi = x + (size_t)i * ng;
+        for (int32_t j = 0; j < ng; ++j)
+            xi[j] = (uint8_t)qo_observe(ki[j] + K, draw(seed, inst, gen, c0 + i, j), T);
+        f[i] = qo_fitness(ng, w, v, W, lambda, xi);
+    }
+    free(T);
+    return 0;
+}
+
+int qo_rows_rotate(int32_t ng, int32_t D, int32_t rule, int32_t nr, int16_t *k,
+                   const uint8_t *x, const uint8_t *xe)
+{
+    if (ng < 1 || D < 4 || D % 4 != 0 || (rule != 0 && rule != 1) || nr < 0) return 1;
+    const int32_t K = D / 4;
+    for (int32_t i = 0; i < nr; ++i) {
+        int16_t *ki = k + (size_t)i * ng;
+        const uint8_t *xi = x + (size_t)i * ng;
+        for (int32_t j = 0; j < ng; ++j) {
+            if (rule == 1 && xi[j] == xe[j]) continue;
+            const int32_t kn = ki[j] + (xe[j] ? 1 : -1);
+            if (kn >= -K && kn <= K) ki[j] = (int16_t)kn;
+        }
+    }
     return 0;
 }
 
