@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--phases", action="store_true",
+                    help="per-step breakdown (CIP, QIP, Evaluation, DetermineElite) of the "
+                         "unfused form, and device vs host DetermineElite, on --workload")
     ap.add_argument("--ref-budget-s", type=float, default=150.0,
                     help="--impl reference: seconds of oracle work over warm-up + timed steps")
     return ap.parse_args()
@@ -722,8 +725,86 @@ def run_served(a):
     print(json.dumps(line), flush=True)
 
 
+def run_phases(a):
+    """Per-step time breakdown of a generation (the paper's Table VI analysis on this GPU):
+    the unfused form runs CIP, QIP, Evaluation and DetermineElite as four timed launches;
+    the fused kernel and the host-DetermineElite variant run the same solve for comparison.
+    All three produce identical results."""
+    import torch
+    from paper_2609_30862_gb300 import qieo as Q
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(0)
+    Q.load()
+    c = WL.WORKLOADS[a.workload]
+    prob = WL.knapsack(c["ng"], c["item_seed"])
+    np_, G = c["np"], c["gens"]
+    stream = torch.cuda.Stream()
+
+    def timed_run(inst, reps):
+        best = None
+        with torch.cuda.stream(stream):
+            for r in range(reps + 1):
+                inst.reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                inst.run(G)
+                e1.record(stream)
+                e1.synchronize()
+                if r:
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+        return 1e3 * best / G, inst.best()
+
+    mk = lambda **kw: Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"], stream=stream.cuda_stream, **kw)
+    with mk() as I:
+        fused_us, fused_best = timed_run(I, max(1, a.steps))
+    with mk(flags=Q.QIEO_FLAG_UNFUSED) as I:
+        unfused_us, unfused_best = timed_run(I, max(1, a.steps))
+    with mk(flags=Q.QIEO_FLAG_UNFUSED | Q.QIEO_FLAG_TIME_KERNELS) as I:
+        with torch.cuda.stream(stream):
+            I.run(G)
+            I.synchronize()
+        ms, gens = I.phase_times()
+    with mk(elite_on_host=1) as I:
+        host_us, host_best = timed_run(I, 1)
+    with mk(elite_on_host=1, flags=Q.QIEO_FLAG_TIME_KERNELS) as I:
+        with torch.cuda.stream(stream):
+            I.run(G)
+            I.synchronize()
+        hms, hgens = I.phase_times()
+    per = {k: 1e3 * v / gens for k, v in ms.items()}
+    tot = sum(per.values())
+    assert fused_best[1:] == unfused_best[1:] == host_best[1:]
+    line = {
+        "metric": "time per generation by step (CIP, QIP, Evaluation, DetermineElite)",
+        "value": fused_us, "unit": "us/generation", "n_gpus": 1, "steps": max(1, a.steps),
+        "warmup": 1, "higher_is_better": False, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(a.workload),
+        "fused_us_per_generation": fused_us,
+        "unfused_us_per_generation": unfused_us,
+        "fusion_speedup": unfused_us / fused_us,
+        "unfused_step_us_per_generation": per,
+        "unfused_step_fraction": {k: v / tot for k, v in per.items()},
+        "determine_elite": {
+            "device_us_per_generation": per["determine_elite"],
+            "host_us_per_generation": 1e3 * hms["determine_elite"] / hgens,
+            "host_over_device": (hms["determine_elite"] / hgens) / (ms["determine_elite"] / gens),
+            "host_variant_run_us_per_generation": host_us,
+            "what_host": "copy of fitness[np] to the host + host argmax + the launch recording the "
+                         "elite, after the generation kernel finished",
+        },
+        "gpu_launches": max(1, a.steps) * (G + 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.impl != "reference" and a.phases:
+        run_phases(a)
+        return
     if a.impl != "reference" and a.workload == "c5":
         run_served(a)
         return

@@ -72,6 +72,11 @@ typedef struct {
                                          per generation */
 #define QIEO_FLAG_REGISTER_PREFETCH 0x20 /* stream the state with register prefetch instead
                                             of asynchronous copies into shared memory */
+#define QIEO_FLAG_UNFUSED       0x40  /* run each generation as four launches, one per step
+                                         of Sec. III-B (CIP, QIP, Evaluation,
+                                         DetermineElite), the way the paper offloads them;
+                                         same results, for the per-step time breakdown.
+                                         Not with elite_on_host or QIEO_FLAG_COOPERATIVE */
 
 typedef struct {
     int32_t np;              /* chromosomes, >= 1 */
@@ -164,6 +169,15 @@ qieo_status qieo_set_launch_shape(qieo_instance *inst, const qieo_launch_shape *
 /* Accumulated device time of the generation kernels (QIEO_FLAG_TIME_KERNELS) and the
  * number of generation-kernel launches it covers; qieo_reset clears neither. */
 qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launches);
+
+/* Accumulated time per step of a generation, ms[4] = {CIP, QIP, Evaluation,
+ * DetermineElite}, and the number of generations it covers. Filled by runs with
+ * QIEO_FLAG_TIME_KERNELS and QIEO_FLAG_UNFUSED (device time of each step's launch, CUDA
+ * events), and, for the DetermineElite entry only, by runs with QIEO_FLAG_TIME_KERNELS and
+ * elite_on_host = 1 (host wall time of the fitness copy to the host, the host argmax and
+ * the launch that records the elite, measured after the generation kernel finished).
+ * qieo_reset clears neither. */
+qieo_status qieo_get_phase_times(qieo_instance *inst, double ms[4], int64_t *generations);
 
 /* A batch: many instances advanced together, one persistent kernel launch per generation
  * for all of them (survey-level "batching" of independent QIEO solves; the paper runs one

@@ -139,6 +139,11 @@ struct qieo_instance {
 
     // host DetermineElite
     int64_t *h_fit = nullptr;
+
+    // per-step timing (QIEO_FLAG_UNFUSED / elite_on_host with QIEO_FLAG_TIME_KERNELS)
+    std::vector<cudaEvent_t> phase_ev;
+    double phase_ms[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t phase_gens = 0;
 };
 
 namespace {
@@ -438,8 +443,15 @@ qieo_status run_device(qieo_instance *q, int32_t G)
 
 qieo_status run_host_de(qieo_instance *q, int32_t G)
 {
+    const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     for (int32_t g = 0; g < G; ++g) {
         CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 0));
+        std::chrono::steady_clock::time_point t0;
+        if (timing) {   // DetermineElite's share starts once the generation kernel is done
+            qieo_status st = wait_stream(q->stream);
+            if (st != QIEO_OK) return st;
+            t0 = std::chrono::steady_clock::now();
+        }
         CUDA_TRY(cudaMemcpyAsync(q->h_fit, q->gp.fitness, (size_t)q->np * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, q->stream));
         qieo_status st = wait_stream(q->stream);
@@ -449,9 +461,69 @@ qieo_status run_host_de(qieo_instance *q, int32_t G)
             if (q->h_fit[c] > q->h_fit[e]) e = c;
         qieo::record_elite_kernel<<<1, qieo::kThreads, 0, q->stream>>>(q->gp, e);
         CUDA_TRY(cudaGetLastError());
+        if (timing) {
+            q->phase_ms[3] += 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            q->phase_gens += 1;
+        }
     }
     CUDA_TRY(launch_final_cip(q));
     return wait_stream(q->stream);
+}
+
+// The four steps of each generation as four launches (QIEO_FLAG_UNFUSED): CIP toward the
+// previous elite (not in a run's first generation: the previous run ended with it), QIP,
+// Evaluation, DetermineElite; then the final CIP of the run. With QIEO_FLAG_TIME_KERNELS an
+// event is recorded around every launch and the run waits to add up the steps' times.
+qieo_status run_unfused(qieo_instance *q, int32_t G)
+{
+    const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
+    const size_t total = (size_t)q->np * q->svec;
+    const int blocks = (int)std::max<size_t>(
+        1, std::min<size_t>((total + qieo::kThreads - 1) / qieo::kThreads, (size_t)std::max(q->sm_count, 1) * 8));
+    const int eval_blocks = std::max(1, std::min(q->np, std::max(q->sm_count, 1) * 8));
+    size_t need = timing ? (size_t)4 * G + 1 : 0;
+    while (q->phase_ev.size() < need) {
+        cudaEvent_t e = nullptr;
+        CUDA_TRY(cudaEventCreate(&e));
+        q->phase_ev.push_back(e);
+    }
+    std::vector<int> phase_of;   // phase of the launch that ends at event i + 1
+    size_t ev = 0;
+    auto mark = [&](int phase) -> cudaError_t {
+        if (!timing) return cudaSuccess;
+        if (phase >= 0) phase_of.push_back(phase);
+        return cudaEventRecord(q->phase_ev[ev++], q->stream);
+    };
+    CUDA_TRY(mark(-1));
+    for (int32_t g = 0; g < G; ++g) {
+        if (g > 0) {
+            if (q->rule) qieo::cip_kernel<1><<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp);
+            else qieo::cip_kernel<0><<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp);
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(mark(0));
+        }
+        qieo::qip_kernel<<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(mark(1));
+        qieo::eval_kernel<<<eval_blocks, qieo::kThreads, 0, q->stream>>>(q->gp);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(mark(2));
+        qieo::de_kernel<<<1, qieo::kThreads, 0, q->stream>>>(q->gp);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(mark(3));
+    }
+    CUDA_TRY(launch_final_cip(q));
+    if (timing) {
+        qieo_status st = wait_stream(q->stream);
+        if (st != QIEO_OK) return st;
+        for (size_t i = 0; i < phase_of.size(); ++i) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, q->phase_ev[i], q->phase_ev[i + 1]));
+            q->phase_ms[phase_of[i]] += ms;
+        }
+        q->phase_gens += G;
+    }
+    return QIEO_OK;
 }
 
 // Waits for the instance's stream and reports a device-side wait that ran out.
@@ -571,6 +643,8 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     if (pa->elite_on_host != 0 && pa->elite_on_host != 1)
         return fail(QIEO_ERR_INVALID, "elite_on_host must be 0 or 1");
     if (pr->capacity < 0) return fail(QIEO_ERR_INVALID, "capacity must be >= 0");
+    if ((pa->flags & QIEO_FLAG_UNFUSED) && (pa->elite_on_host || (pa->flags & QIEO_FLAG_COOPERATIVE)))
+        return fail(QIEO_ERR_INVALID, "QIEO_FLAG_UNFUSED excludes elite_on_host and QIEO_FLAG_COOPERATIVE");
 
     int64_t sum_w = 0, sum_v = 0, sum_absv = 0;
     int32_t max_w = 0, max_v = 0, min_v = 0;
@@ -762,6 +836,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
+    for (cudaEvent_t e : q->phase_ev) cudaEventDestroy(e);
     if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
     delete q;
     return QIEO_OK;
@@ -795,7 +870,8 @@ qieo_status qieo_run(qieo_instance *q, int32_t G)
     if (st != QIEO_OK) return st;
     st = ensure_history(q, q->t + G);
     if (st != QIEO_OK) return st;
-    st = q->host_de ? run_host_de(q, G) : run_device(q, G);
+    st = q->host_de ? run_host_de(q, G)
+                    : (q->flags & QIEO_FLAG_UNFUSED) ? run_unfused(q, G) : run_device(q, G);
     if (st != QIEO_OK) return st;
     q->t += G;
     if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_checked(q);
@@ -986,6 +1062,16 @@ qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches
     if (st != QIEO_OK) return st;
     if (ms) *ms = q->kernel_ms;
     if (launches) *launches = q->kernel_launches;
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_phase_times(qieo_instance *q, double ms[4], int64_t *generations)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (ms)
+        for (int i = 0; i < 4; ++i) ms[i] = q->phase_ms[i];
+    if (generations) *generations = q->phase_gens;
     return QIEO_OK;
 }
 
@@ -1477,6 +1563,7 @@ void destroy_instance_nosync(qieo_instance *q)
     drop_graphs(q);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
+    for (cudaEvent_t e : q->phase_ev) cudaEventDestroy(e);
     delete q;
 }
 

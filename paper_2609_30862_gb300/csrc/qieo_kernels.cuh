@@ -983,6 +983,104 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
 }
 
 // ---------------------------------------------------------------------------------------
+// Unfused form: the four steps of a generation as four launches, the way the paper offloads
+// them as separate target regions (Sec. III-B): cip_kernel (CIP toward the previous elite),
+// qip_kernel (observation of every qubit into the allele plane), eval_kernel (eq. (1) per
+// chromosome from the alleles) and de_kernel (DetermineElite and the records). Each step
+// passes its result to the next through device memory, so the state is read twice and
+// written once per generation and the alleles are written once and read once; the results
+// equal the fused kernel's.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) qip_kernel(const GenParams p)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    load_thresholds(p, s_thr);
+    __syncthreads();
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    const int32_t t = *p.gen;
+    uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint32_t off_top = (uint32_t)(8 * p.K);
+    const size_t total = (size_t)p.np * p.svec;
+    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * kThreads) {
+        const size_t c = i / (size_t)p.svec;
+        const size_t v = i - c * (size_t)p.svec;
+        const uint4 s = p.state[i];
+        const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
+        const Draw4 r0 = philox4x32_10_rk(2u * (uint32_t)v, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r1 = philox4x32_10_rk(2u * (uint32_t)v + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
+        uint32_t xbits = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t off = (k & 1) ? (sp[k >> 1] >> 16) : (sp[k >> 1] & 0xffffu);
+            const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+            if ((u[k] < thr) || (off == off_top)) xbits |= 1u << k;
+        }
+        x_cur[c * p.xstride + v] = (uint8_t)xbits;
+    }
+}
+
+// Row sums of one chromosome per block iteration from its alleles and the 32-bit items
+// (zero on the padding genes), then eq. (1) into fitness[c].
+__global__ void __launch_bounds__(kThreads) eval_kernel(const GenParams p)
+{
+    __shared__ long long s_w[kThreads / 32], s_v[kThreads / 32];
+    const int32_t t = *p.gen;
+    const uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+    for (int32_t c = blockIdx.x; c < p.np; c += gridDim.x) {
+        const uint8_t *xr = x_cur + (size_t)c * p.xstride;
+        long long w = 0, v = 0;
+        for (int32_t vec = threadIdx.x; vec < p.svec; vec += kThreads) {
+            const uint32_t xb = xr[vec];
+            if (!xb) continue;
+            const int4 a = __ldg(p.w4 + 2 * (size_t)vec), b = __ldg(p.w4 + 2 * (size_t)vec + 1);
+            const int4 d = __ldg(p.v4 + 2 * (size_t)vec), e = __ldg(p.v4 + 2 * (size_t)vec + 1);
+            const int32_t wi[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const int32_t vi[8] = {d.x, d.y, d.z, d.w, e.x, e.y, e.z, e.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if ((xb >> k) & 1u) {
+                    w += wi[k];
+                    v += vi[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_w[threadIdx.x >> 5] = w;
+            s_v[threadIdx.x >> 5] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long sw = 0, sv = 0;
+            for (int i = 0; i < kThreads / 32; ++i) {
+                sw += s_w[i];
+                sv += s_v[i];
+            }
+            p.fitness[c] = sw <= p.capacity ? (int64_t)sv : -p.lambda * ((int64_t)sw - p.capacity);
+        }
+        __syncthreads();
+    }
+}
+
+// DetermineElite over fitness[] (lowest index of the maximum) and the records; one block.
+__global__ void __launch_bounds__(kThreads) de_kernel(GenParams p)
+{
+    p.key_mode = 0;
+    const int32_t t = *p.gen;
+    close_generation(p, t);
+    if (threadIdx.x == 0) {
+        *p.gen = t + 1;
+        *p.bar_gen = t + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Batched form: many independent instances in one persistent launch per generation. The
 // host cuts every instance's ntile * np tile-rows into segments (one tile, at most
 // kMaxSegRows rows each) of a few per block on average, ordered largest first; blocks take

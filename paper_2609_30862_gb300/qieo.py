@@ -30,6 +30,7 @@ QIEO_FLAG_FORCE_WIDE = 0x4
 QIEO_FLAG_TIME_KERNELS = 0x8
 QIEO_FLAG_COOPERATIVE = 0x10
 QIEO_FLAG_REGISTER_PREFETCH = 0x20
+QIEO_FLAG_UNFUSED = 0x40
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
@@ -37,7 +38,8 @@ EXPORTS = (
     "qieo_run", "qieo_set_wait_timeout", "qieo_synchronize", "qieo_get_best",
     "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
-    "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time", "qieo_philox",
+    "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
+    "qieo_get_phase_times", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
     "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
     "qieo_server_get_stats", "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
@@ -126,6 +128,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_get_launch_shape": ([P, P], C.c_int),
         "qieo_set_launch_shape": ([P, P], C.c_int),
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
+        "qieo_get_phase_times": ([P, P, P], C.c_int),
         "qieo_philox": ([P, P, i32], C.c_int),
         "qieo_generation_noalloc": ([P, P, i32, P, P, P, P], C.c_int),
         "qieo_create_batch": ([P, i32, P], C.c_int),
@@ -243,6 +246,14 @@ def qieo_get_launch_shape(h) -> qieo_launch_shape:
 def qieo_set_launch_shape(h, lanes_per_row: int, warps_per_row: int, grid_ctas: int = 0) -> None:
     s = qieo_launch_shape(int(lanes_per_row), int(warps_per_row), int(grid_ctas), 0, 0, 0)
     _check(load().qieo_set_launch_shape(h, C.byref(s)))
+
+
+def qieo_get_phase_times(h):
+    """({CIP, QIP, Evaluation, DetermineElite} ms, generations covered)."""
+    ms = (C.c_double * 4)()
+    n = C.c_int64()
+    _check(load().qieo_get_phase_times(h, ms, C.byref(n)))
+    return {"cip": ms[0], "qip": ms[1], "evaluation": ms[2], "determine_elite": ms[3]}, int(n.value)
 
 
 def qieo_get_kernel_time(h):
@@ -474,6 +485,9 @@ class Instance:
 
     def kernel_time(self):
         return qieo_get_kernel_time(self.h)
+
+    def phase_times(self):
+        return qieo_get_phase_times(self.h)
 
     def autotune(self, trial_generations: int = 8) -> qieo_launch_shape:
         return qieo_autotune(self.h, trial_generations)

@@ -62,6 +62,13 @@ def test_defaults_and_errors_without_gpu(lib):
     with pytest.raises(Q.QieoError):
         Q.qieo_create_instance([2**31 - 1] * 4, [1] * 4, 1, _params(p, penalty_lambda=2**32))
     with pytest.raises(Q.QieoError) as e:
+        Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, flags=Q.QIEO_FLAG_UNFUSED, elite_on_host=1))
+    assert e.value.status == Q.QIEO_ERR_INVALID and "UNFUSED" in str(e.value)
+    with pytest.raises(Q.QieoError) as e:
+        Q.qieo_create_instance([1, 2], [3, 4], 2,
+                               _params(p, flags=Q.QIEO_FLAG_UNFUSED | Q.QIEO_FLAG_COOPERATIVE))
+    assert e.value.status == Q.QIEO_ERR_INVALID
+    with pytest.raises(Q.QieoError) as e:
         Q.qieo_run(None, 1)
     assert e.value.status == Q.QIEO_ERR_INVALID
 

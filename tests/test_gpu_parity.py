@@ -256,3 +256,28 @@ def test_barrier_wait_timeout_is_reported():
         k, t = I.state()
         ref = O.run(prob, 300, 5, seed=16)
         assert t == 5 and np.array_equal(k, ref.k)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_unfused_four_launch_form(rule):
+    """QIEO_FLAG_UNFUSED runs CIP, QIP, Evaluation and DetermineElite as four launches per
+    generation; results equal the oracle (ragged ng, split runs), and with kernel timing
+    every step's time is accounted for every generation."""
+    prob = W.knapsack(1003, 31)
+    compare(prob, 37, [6, 5], seed=31, rule=rule, flags=Q.QIEO_FLAG_UNFUSED)
+    with Q.Instance(prob, 37, seed=31, rule=rule,
+                    flags=Q.QIEO_FLAG_UNFUSED | Q.QIEO_FLAG_TIME_KERNELS) as I:
+        I.run(8)
+        I.run(4)
+        ms, gens = I.phase_times()
+        assert gens == 12
+        assert all(v > 0 for v in ms.values()), ms
+
+
+def test_host_elite_phase_time():
+    prob = W.knapsack(500, 32)
+    compare(prob, 20, [5], seed=32, host=1, flags=Q.QIEO_FLAG_TIME_KERNELS)
+    with Q.Instance(prob, 20, seed=32, elite_on_host=1, flags=Q.QIEO_FLAG_TIME_KERNELS) as I:
+        I.run(6)
+        ms, gens = I.phase_times()
+        assert gens == 6 and ms["determine_elite"] > 0 and ms["qip"] == 0
