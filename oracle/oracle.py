@@ -65,6 +65,9 @@ def _lib(kind: str = "serial") -> C.CDLL:
             L.qo_run.argtypes = [i32, P, P, i64, i32, i32, i64, u32, u32, i32, i32,
                                  P, P, P, P, P, P, P, P]
             L.qo_run.restype = C.c_int
+            L.qo_run_converge.argtypes = [i32, P, P, i64, i32, i32, i64, u32, u32, i32, i32,
+                                          P, P, P, P, P, P, P, P, i32, P, P]
+            L.qo_run_converge.restype = C.c_int
             L.qo_run_fp64.argtypes = [i32, P, P, i64, i32, i32, i64, u32, u32, i32, i32,
                                       P, P, P, P, P, P, P, P, P, P, P]
             L.qo_run_fp64.restype = C.c_int
@@ -166,6 +169,12 @@ class State:
         self.f = np.zeros(np_, dtype=np.int64)
         self.hist_e = np.zeros(0, dtype=np.int32)
         self.hist_f = np.zeros(0, dtype=np.int64)
+        # convergence test: run length of equal elite fitness, stopped flag, that fitness
+        self.conv = np.zeros(3, dtype=np.int64)
+
+    @property
+    def stopped(self) -> bool:
+        return bool(self.conv[1])
 
     def copy(self) -> "State":
         s = State.__new__(State)
@@ -176,9 +185,11 @@ class State:
 
 def run(problem, np_: int, gens: int, seed: int = 1, inst: int = 0, D: int = 100,
         lam: int = 1, rule: int = 0, state: State | None = None, kind: str = "serial",
-        threads: int = 0) -> State:
+        threads: int = 0, window: int = 0) -> State:
     """Run `gens` generations of the angle-index form from `state` (a fresh instance if
-    None) and return the updated state. `problem` has .weights, .values, .capacity."""
+    None) and return the updated state. `problem` has .weights, .values, .capacity.
+    window > 0: stop once the elite fitness has been equal for `window` consecutive
+    generations (then `gens` is the cap and the history holds the generations run)."""
     w = np.ascontiguousarray(problem.weights, dtype=np.int32)
     v = np.ascontiguousarray(problem.values, dtype=np.int32)
     ng = int(w.shape[0])
@@ -188,13 +199,22 @@ def run(problem, np_: int, gens: int, seed: int = 1, inst: int = 0, D: int = 100
     L = _lib(kind)
     if kind == "omp":
         L.qo_set_threads(int(threads) if threads else (os.cpu_count() or 1))
-    rc = L.qo_run(ng, _p(w), _p(v), int(problem.capacity), np_, D, lam, seed & 0xFFFFFFFF,
-                  inst & 0xFFFFFFFF, rule, gens, _p(st.k), _p(st.t), _p(st.best),
-                  _p(st.best_x), _p(st.x), _p(st.f), _p(he), _p(hf))
+    if window > 0:
+        done = np.zeros(1, dtype=np.int32)
+        rc = L.qo_run_converge(ng, _p(w), _p(v), int(problem.capacity), np_, D, lam,
+                               seed & 0xFFFFFFFF, inst & 0xFFFFFFFF, rule, gens, _p(st.k),
+                               _p(st.t), _p(st.best), _p(st.best_x), _p(st.x), _p(st.f), _p(he),
+                               _p(hf), int(window), _p(st.conv), _p(done))
+        n = int(done[0])
+    else:
+        rc = L.qo_run(ng, _p(w), _p(v), int(problem.capacity), np_, D, lam, seed & 0xFFFFFFFF,
+                      inst & 0xFFFFFFFF, rule, gens, _p(st.k), _p(st.t), _p(st.best),
+                      _p(st.best_x), _p(st.x), _p(st.f), _p(he), _p(hf))
+        n = gens
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
-    st.hist_e = np.concatenate([st.hist_e, he])
-    st.hist_f = np.concatenate([st.hist_f, hf])
+    st.hist_e = np.concatenate([st.hist_e, he[:n]])
+    st.hist_f = np.concatenate([st.hist_f, hf[:n]])
     return st
 
 

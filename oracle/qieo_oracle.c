@@ -14,7 +14,7 @@
  *     table step toward the elite's allele), then terminate or loop.
  *   - Eq. (1): f = sum(v x) if sum(w x) <= W, else -lambda (sum(w x) - W).
  *
- * Readings where the paper is silent (labelled S1 .. S14 in this file):
+ * Readings where the paper is silent (labelled S1 .. S15 in this file):
  *   S1  dtheta = pi / D (D = 100 for all named workloads); start angle pi/4.
  *   S2  theta stays in [0, pi/2]; a step that would leave it is not taken.
  *   S3  rule R1: every qubit moves one step toward the elite's allele (+ if it is 1,
@@ -28,6 +28,9 @@
  *   S8/S9 the elite is the lowest-index maximum of f; the best-so-far record is replaced
  *       only by a strictly larger fitness.
  *   S14 CIP also follows the last generation of a run.
+ *   S15 convergence (Sec. IV, off unless asked for): stop once the elite fitness has been
+ *       the same for 20 consecutive generations; the fitness values are integers, so the
+ *       "within 1e-6 of their mean" clause means equal. The generation count is the cap.
  *
  * Pins (tests): Philox against PyTorch's independent header implementation; the
  * threshold table against a 60-digit evaluation; eq. (1) against a dynamic-programming
@@ -178,18 +181,28 @@ static int check_args(int32_t ng, const int32_t *w, int32_t np, int32_t D, int64
  * best_x[ng]. Out: x[np*ng] and f[np] of the last generation run, hist_e[G] and
  * hist_f[G] the elite index and fitness of each generation run.
  * Runs G generations; each is QIP, Evaluation, DetermineElite, CIP (Fig. 1).
+ *
+ * Convergence (Sec. IV, Workload): the run stops once the elite fitness has been the same
+ * for `window` consecutive generations (reading S15: the fitness values are integers, so
+ * "within 1e-6 of their mean" means equal); the generation cap is G. window = 0 turns the
+ * test off. conv[3] carries the test across calls: {length of the run of equal elite
+ * fitness values ending at the last generation, 1 once stopped, that fitness}. A stopped
+ * instance runs no further generation. Returns the number of generations run in *done.
  * ---------------------------------------------------------------------------------- */
-int qo_run(int32_t ng, const int32_t *w, const int32_t *v, int64_t W,
-           int32_t np, int32_t D, int64_t lambda, uint32_t seed, uint32_t inst, int32_t rule,
-           int32_t G, int16_t *k, int32_t *t, int64_t *best, uint8_t *best_x,
-           uint8_t *x, int64_t *f, int32_t *hist_e, int64_t *hist_f)
+static int run_loop(int32_t ng, const int32_t *w, const int32_t *v, int64_t W,
+                    int32_t np, int32_t D, int64_t lambda, uint32_t seed, uint32_t inst,
+                    int32_t rule, int32_t G, int16_t *k, int32_t *t, int64_t *best,
+                    uint8_t *best_x, uint8_t *x, int64_t *f, int32_t *hist_e, int64_t *hist_f,
+                    int32_t window, int64_t *conv, int32_t *done)
 {
-    if (check_args(ng, w, np, D, lambda, rule) || G < 0) return 1;
+    if (check_args(ng, w, np, D, lambda, rule) || G < 0 || window < 0) return 1;
     const int32_t K = D / 4;
     uint64_t *T = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(2 * K + 1));
     qo_threshold_table(D, T);
+    *done = 0;
 
     for (int32_t g = 0; g < G; ++g) {
+        if (window > 0 && conv[1]) break;
         const int32_t gen = *t;
 
         /* QIP: observe every qubit; Evaluation: eq. (1) per chromosome. */
@@ -229,9 +242,37 @@ int qo_run(int32_t ng, const int32_t *w, const int32_t *v, int64_t W,
             }
         }
         *t = gen + 1;
+        *done = g + 1;
+
+        /* Convergence test on the elite fitness of the generations so far. */
+        if (window > 0) {
+            conv[0] = (gen > 0 && conv[0] > 0 && f[e] == conv[2]) ? conv[0] + 1 : 1;
+            conv[2] = f[e];
+            if (conv[0] >= window) conv[1] = 1;
+        }
     }
     free(T);
     return 0;
+}
+
+int qo_run(int32_t ng, const int32_t *w, const int32_t *v, int64_t W,
+           int32_t np, int32_t D, int64_t lambda, uint32_t seed, uint32_t inst, int32_t rule,
+           int32_t G, int16_t *k, int32_t *t, int64_t *best, uint8_t *best_x,
+           uint8_t *x, int64_t *f, int32_t *hist_e, int64_t *hist_f)
+{
+    int32_t done = 0;
+    return run_loop(ng, w, v, W, np, D, lambda, seed, inst, rule, G, k, t, best, best_x, x, f,
+                    hist_e, hist_f, 0, NULL, &done);
+}
+
+int qo_run_converge(int32_t ng, const int32_t *w, const int32_t *v, int64_t W,
+                    int32_t np, int32_t D, int64_t lambda, uint32_t seed, uint32_t inst,
+                    int32_t rule, int32_t G, int16_t *k, int32_t *t, int64_t *best,
+                    uint8_t *best_x, uint8_t *x, int64_t *f, int32_t *hist_e, int64_t *hist_f,
+                    int32_t window, int64_t *conv, int32_t *done)
+{
+    return run_loop(ng, w, v, W, np, D, lambda, seed, inst, rule, G, k, t, best, best_x, x, f,
+                    hist_e, hist_f, window, conv, done);
 }
 
 /* ------------------------------------------------------------------------------------

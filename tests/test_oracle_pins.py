@@ -276,3 +276,54 @@ def test_rejects_invalid(oracle_mod):
         oracle_mod.run(prob, 4, 1, lam=0)
     with pytest.raises(ValueError):
         oracle_mod.run(prob, 0, 1)
+
+
+def _first_converged(hist_f, window):
+    """First generation t whose last `window` elite fitness values (t-window+1 .. t) are all
+    equal, found from the history of a run without the stop (the definition itself)."""
+    for t in range(window - 1, len(hist_f)):
+        if np.all(hist_f[t - window + 1:t + 1] == hist_f[t]):
+            return t
+    return None
+
+
+@pytest.mark.parametrize("ng,np_,seed,rule", [(200, 30, 3, 0), (120, 17, 8, 0), (60, 5, 2, 0)])
+def test_convergence_stop_matches_its_definition(oracle_mod, ng, np_, seed, rule):
+    """Sec. IV: stop once the elite fitness has been stable for 20 generations. The
+    stopping generation equals the first one that the definition picks out of an
+    unstopped run's history, the stopped state equals that run cut after it (its CIP
+    included), split runs stop at the same place, and a stopped instance stays put."""
+    O = oracle_mod
+    prob = W.knapsack(ng, seed)
+    full = O.run(prob, np_, 400, seed=seed, rule=rule)
+    tc = _first_converged(full.hist_f, 20)
+    assert tc is not None
+    stopped = O.run(prob, np_, 400, seed=seed, rule=rule, window=20)
+    assert int(stopped.t[0]) == tc + 1 and stopped.stopped
+    cut = O.run(prob, np_, tc + 1, seed=seed, rule=rule)
+    assert np.array_equal(stopped.k, cut.k)
+    assert np.array_equal(stopped.hist_e, cut.hist_e) and np.array_equal(stopped.hist_f, cut.hist_f)
+    assert np.array_equal(stopped.best, cut.best)
+    split = O.State(np_, ng)
+    for g in (7, 13, 50, 400):
+        split = O.run(prob, np_, g, seed=seed, rule=rule, state=split, window=20)
+    assert int(split.t[0]) == tc + 1 and np.array_equal(split.k, stopped.k)
+    again = O.run(prob, np_, 10, seed=seed, rule=rule, state=stopped.copy(), window=20)
+    assert int(again.t[0]) == tc + 1 and np.array_equal(again.k, stopped.k)
+
+
+def test_convergence_window_one_and_cap(oracle_mod):
+    """Window 1 stops after the first generation; a cap below the stopping generation runs
+    exactly the cap; rule R2 keeps the population diverse, and where the definition finds
+    no stable window the run goes to its cap."""
+    O = oracle_mod
+    prob = W.knapsack(100, 4)
+    one = O.run(prob, 12, 50, seed=4, window=1)
+    assert int(one.t[0]) == 1
+    capped = O.run(prob, 12, 5, seed=4, window=20)
+    assert int(capped.t[0]) == 5 and not capped.stopped
+    prob = W.knapsack(120, 8)
+    full = O.run(prob, 17, 150, seed=8, rule=1)
+    assert _first_converged(full.hist_f, 20) is None
+    r2 = O.run(prob, 17, 150, seed=8, rule=1, window=20)
+    assert int(r2.t[0]) == 150 and not r2.stopped and np.array_equal(r2.k, full.k)
