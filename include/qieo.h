@@ -77,6 +77,14 @@ typedef struct {
                                          DetermineElite), the way the paper offloads them;
                                          same results, for the per-step time breakdown.
                                          Not with elite_on_host or QIEO_FLAG_COOPERATIVE */
+#define QIEO_FLAG_CONVERGE      0x80  /* stop once the elite fitness has been the same for
+                                         QIEO_CONVERGE_WINDOW consecutive generations
+                                         (Sec. IV, Workload); the generations asked of a run
+                                         are then a cap. The generation that meets the test
+                                         still gets its CIP. Default path, batches and the
+                                         server only: not with elite_on_host,
+                                         QIEO_FLAG_COOPERATIVE or QIEO_FLAG_UNFUSED */
+#define QIEO_CONVERGE_WINDOW    20
 
 typedef struct {
     int32_t np;              /* chromosomes, >= 1 */
@@ -179,6 +187,12 @@ qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launc
  * qieo_reset clears neither. */
 qieo_status qieo_get_phase_times(qieo_instance *inst, double ms[4], int64_t *generations);
 
+/* Convergence test of an instance created with QIEO_FLAG_CONVERGE: *stopped = 1 once it
+ * stopped (no later generation runs; qieo_get_state's t is one past the generation that
+ * met the test), *stable = the number of consecutive generations, ending at the last one
+ * run, whose elite fitness is the same. Either pointer may be NULL. */
+qieo_status qieo_get_convergence(qieo_instance *inst, int32_t *stopped, int32_t *stable);
+
 /* A batch: many instances advanced together, one persistent kernel launch per generation
  * for all of them (survey-level "batching" of independent QIEO solves; the paper runs one
  * problem at a time). The instances keep their own state, records and generation
@@ -237,14 +251,17 @@ typedef struct {
     int64_t fitness;          /* best-so-far record of the solve (see qieo_get_best) */
     int32_t generation, chromosome;
     double submit_s, admit_s, done_s;   /* seconds on the server's clock */
+    int32_t generations_run;  /* generations the solve ran (fewer than asked if it converged) */
+    int32_t converged;        /* 1: stopped by the convergence test (QIEO_FLAG_CONVERGE) */
 } qieo_solve_result;
 
 /* Creates a server on the current device. QIEO_ERR_OOM if the arena cannot be reserved. */
 qieo_status qieo_server_create(const qieo_server_config *config, qieo_server **out);
 
 /* Queues one solve: `generations` generations of problem (host arrays, copied) with params
- * (np, D, lambda, seed, instance_id, rotate_rule; stream, flags and elite_on_host are
- * ignored). *id_out receives the request id. QIEO_ERR_OOM when the solve needs more device
+ * (np, D, lambda, seed, instance_id, rotate_rule, and of the flags QIEO_FLAG_CONVERGE, with
+ * which `generations` is a cap and the solve leaves as soon as it converged; stream, the
+ * other flags and elite_on_host are ignored). *id_out receives the request id. QIEO_ERR_OOM when the solve needs more device
  * memory than the whole arena (it could never be admitted); QIEO_ERR_INVALID for bad
  * arguments. Thread-safe. */
 qieo_status qieo_server_submit(qieo_server *server, const qieo_problem *problem,

@@ -608,7 +608,7 @@ size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size
                                   sizeof(int32_t),
                                   (size_t)(D / 2 + 1) * sizeof(uint32_t),
                                   sizeof(int32_t),
-                                  sizeof(int32_t),
+                                  3 * sizeof(int32_t),   // error word, convergence words
                                   (size_t)hist_cap * sizeof(int32_t),
                                   (size_t)hist_cap * sizeof(int64_t)};
     size_t total = 0;
@@ -645,6 +645,10 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     if (pr->capacity < 0) return fail(QIEO_ERR_INVALID, "capacity must be >= 0");
     if ((pa->flags & QIEO_FLAG_UNFUSED) && (pa->elite_on_host || (pa->flags & QIEO_FLAG_COOPERATIVE)))
         return fail(QIEO_ERR_INVALID, "QIEO_FLAG_UNFUSED excludes elite_on_host and QIEO_FLAG_COOPERATIVE");
+    if ((pa->flags & QIEO_FLAG_CONVERGE) &&
+        (pa->elite_on_host || (pa->flags & (QIEO_FLAG_COOPERATIVE | QIEO_FLAG_UNFUSED))))
+        return fail(QIEO_ERR_INVALID, "QIEO_FLAG_CONVERGE excludes elite_on_host, QIEO_FLAG_COOPERATIVE "
+                    "and QIEO_FLAG_UNFUSED");
 
     int64_t sum_w = 0, sum_v = 0, sum_absv = 0;
     int32_t max_w = 0, max_v = 0, min_v = 0;
@@ -736,6 +740,8 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     g.thr = (const uint32_t *)(b + off[13]);
     g.bar_gen = (int32_t *)(b + off[14]);
     g.error = (int32_t *)(b + off[15]);
+    g.conv = g.error + 1;
+    g.converge = (q->flags & QIEO_FLAG_CONVERGE) ? 1 : 0;
     g.wait_ns = kDefaultBarrierWaitNs;
     g.np = q->np;
     g.svec = q->svec;
@@ -1062,6 +1068,20 @@ qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches
     if (st != QIEO_OK) return st;
     if (ms) *ms = q->kernel_ms;
     if (launches) *launches = q->kernel_launches;
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_convergence(qieo_instance *q, int32_t *stopped, int32_t *stable)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    int32_t w[2] = {0, 0};
+    st = fetch(q, w, q->gp.conv, sizeof w);
+    if (st != QIEO_OK) return st;
+    if (stopped) *stopped = w[1] != qieo::kRunning ? 1 : 0;
+    if (stable) *stable = w[0];
     return QIEO_OK;
 }
 
@@ -1515,11 +1535,14 @@ struct SolveRequest {
     int32_t remaining = 0;
     int64_t best[3] = {0, -1, -1};
     std::vector<uint8_t> best_row;
+    int32_t gens_run = 0, converged = 0;
 };
 
 struct StepRecord {
     cudaEvent_t done = nullptr;
     std::vector<SolveRequest *> finishing;
+    std::vector<SolveRequest *> watched;       // solves with the convergence test ...
+    const int32_t *stop_host = nullptr;        // ... and their stop states after the step
 };
 
 constexpr size_t kWorkListBytes = 16u << 20;   // per region: params, segments, block starts
@@ -1570,9 +1593,11 @@ void destroy_instance_nosync(qieo_instance *q)
 // Enqueues `G` generations (+ the final rotation) of every member on the server stream
 // with the batched kernel; the work list goes through the next double-buffered region.
 qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance *> &members, int32_t G,
-                                int64_t *launched)
+                                int64_t *launched, const std::vector<qieo_instance *> &watch,
+                                const int32_t **stop_host)
 {
     *launched = 0;
+    *stop_host = nullptr;
     const int r = S->wl_next;
     S->wl_next ^= 1;
     char *host = S->wl_host[r];
@@ -1647,6 +1672,21 @@ qieo_status enqueue_server_step(qieo_server *S, const std::vector<qieo_instance 
         CUDA_TRY(cudaGetLastError());
     }
     *launched = (int64_t)launches.size() * (G + 1);
+    if (!watch.empty()) {   // stop states of the solves with the convergence test, to the host
+        const size_t nw = watch.size();
+        const size_t p_off = used, o_off = align_up(p_off + nw * sizeof(int32_t *), 256);
+        const size_t end = align_up(o_off + nw * sizeof(int32_t), 256);
+        if (end > kWorkListBytes) return fail(QIEO_ERR_INVALID, "too many resident solves for one work list");
+        for (size_t i = 0; i < nw; ++i) std::memcpy(host + p_off + i * sizeof(int32_t *), &watch[i]->gp.conv, sizeof(int32_t *));
+        CUDA_TRY(cudaMemcpyAsync(dev + p_off, host + p_off, nw * sizeof(int32_t *), cudaMemcpyHostToDevice, S->stream));
+        const int blocks = (int)std::min<size_t>(64, (nw + qieo::kThreads - 1) / qieo::kThreads);
+        qieo::gather_stop_kernel<<<blocks, qieo::kThreads, 0, S->stream>>>(
+            (int32_t *const *)(dev + p_off), (int32_t)nw, (int32_t *)(dev + o_off));
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(host + o_off, dev + o_off, nw * sizeof(int32_t), cudaMemcpyDeviceToHost, S->stream));
+        *stop_host = (const int32_t *)(host + o_off);
+        *launched += 1;
+    }
     return QIEO_OK;
 }
 
@@ -1663,12 +1703,31 @@ void retire_oldest_step(qieo_server *S)
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     const qieo_status step_st = ce == cudaSuccess ? QIEO_OK : (ce == cudaErrorNotReady ? QIEO_ERR_TIMEOUT : QIEO_ERR_CUDA);
+    // Solves that converged in this step leave the resident set now; their memory is
+    // released once the step already queued after this one (which includes them but does
+    // nothing for a stopped solve) has finished too.
+    if (step_st == QIEO_OK && rec.stop_host) {
+        std::lock_guard<std::mutex> lock(S->mu);
+        for (size_t i = 0; i < rec.watched.size(); ++i) {
+            SolveRequest *R = rec.watched[i];
+            if (rec.stop_host[i] != qieo::kStopped) continue;
+            auto it = std::find(S->active.begin(), S->active.end(), R);
+            if (it == S->active.end()) continue;   // already finishing by its generation count
+            S->active.erase(it);
+            R->converged = 1;
+            R->remaining = 0;
+            if (!S->inflight.empty()) S->inflight.back().finishing.push_back(R);
+            else rec.finishing.push_back(R);
+        }
+    }
     for (SolveRequest *R : rec.finishing) {
         qieo_instance *q = R->inst;
         int32_t st = step_st;
         if (st == QIEO_OK) {
             R->best_row.resize((size_t)q->xstride);
             if (cudaMemcpyAsync(R->best, q->gp.best, sizeof R->best, cudaMemcpyDeviceToHost, S->copy_stream) != cudaSuccess ||
+                cudaMemcpyAsync(&R->gens_run, q->gp.gen, sizeof R->gens_run, cudaMemcpyDeviceToHost,
+                                S->copy_stream) != cudaSuccess ||
                 cudaMemcpyAsync(R->best_row.data(), q->gp.best_row, R->best_row.size(), cudaMemcpyDeviceToHost,
                                 S->copy_stream) != cudaSuccess ||
                 cudaStreamSynchronize(S->copy_stream) != cudaSuccess)
@@ -1712,7 +1771,7 @@ void server_loop(qieo_server *S)
         for (SolveRequest *R : admit) {
             qieo_params pa = R->params;
             pa.stream = S->stream;
-            pa.flags = 0;
+            pa.flags &= QIEO_FLAG_CONVERGE;
             pa.elite_on_host = 0;
             Placement pl{S->arena + R->off, R->bytes, R->gens};
             qieo_instance *q = nullptr;
@@ -1743,8 +1802,14 @@ void server_loop(qieo_server *S)
                 members.push_back(R->inst);
             }
             StepRecord rec;
+            std::vector<qieo_instance *> watch;
+            for (SolveRequest *R : S->active)
+                if (R->params.flags & QIEO_FLAG_CONVERGE) {
+                    rec.watched.push_back(R);
+                    watch.push_back(R->inst);
+                }
             int64_t launched = 0;
-            qieo_status st = enqueue_server_step(S, members, G, &launched);
+            qieo_status st = enqueue_server_step(S, members, G, &launched, watch, &rec.stop_host);
             if (st == QIEO_OK) {
                 if (S->spare_events.empty()) {
                     cudaEvent_t ev = nullptr;
@@ -1903,6 +1968,8 @@ qieo_status qieo_server_poll(qieo_server *S, int64_t id, int32_t wait_ms, uint8_
     res->submit_s = R->t_submit;
     res->admit_s = R->t_admit;
     res->done_s = R->t_done;
+    res->generations_run = R->gens_run;
+    res->converged = R->converged;
     if (bits_out && R->state == QIEO_SOLVE_DONE) unpack_row(R->best_row.data(), R->prob.ng, bits_out);
     return QIEO_OK;
 }

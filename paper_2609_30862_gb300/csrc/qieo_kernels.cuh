@@ -123,6 +123,10 @@ struct GenParams {
     unsigned int *ticket;         // blocks finished in this generation
     int32_t *bar_gen;             // grid barrier: generations released so far
     int32_t *error;               // kErr* bits
+    int32_t *conv;                // [2] convergence test: run length of equal elite
+                                  // fitness ending at the last generation, stop state
+                                  // (kRunning, kStopPending: the final CIP is still due,
+                                  // kStopped)
     const uint32_t *thr;          // [2K+1] low 32 bits of T[n] (T[2K] = 2^32 -> 0)
     int64_t capacity, lambda;
     int64_t units;                // ntile * np tile-rows
@@ -132,8 +136,21 @@ struct GenParams {
     int32_t lanes, warps, seg_rows_max, key_mode;
     int32_t apply_cip, do_de;
     int32_t ring;                 // 1: state streamed through the per-thread cp.async ring
+    int32_t converge;             // 1: stop once the elite fitness is stable (kConvergeWindow)
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
+
+// Convergence stop (Sec. IV, Workload): the run stops once the elite fitness has been the
+// same for kConvergeWindow consecutive generations (integer fitness: "within 1e-6 of the
+// mean" is equality). The generation that meets it still gets its CIP (Fig. 1 order): the
+// next launch of the instance applies it alone and marks the instance stopped.
+constexpr int32_t kConvergeWindow = 20;
+constexpr int32_t kRunning = 0, kStopPending = 1, kStopped = 2;
+
+__device__ __forceinline__ int32_t stop_state(const GenParams &p)
+{
+    return p.converge ? *(volatile const int32_t *)(p.conv + 1) : kRunning;
+}
 
 // Eq. (1) of a finished row; records the fitness and offers the row to the elite key.
 __device__ __forceinline__ void finish_row(const GenParams &p, int32_t c, int64_t sw, int64_t sv)
@@ -226,6 +243,11 @@ __device__ void close_generation(const GenParams &p, int32_t t)
         if (bc < 0 || bc >= p.np) {
             atomicOr(p.error, kErrEliteRange);
             bc = 0;
+        }
+        if (p.converge) {
+            const int32_t run = (t > 0 && p.conv[0] > 0 && bf == p.hist_f[t - 1]) ? p.conv[0] + 1 : 1;
+            p.conv[0] = run;
+            if (run >= kConvergeWindow) p.conv[1] = kStopPending;
         }
         p.hist_e[t] = bc;
         p.hist_f[t] = bf;
@@ -895,21 +917,30 @@ template <bool kNarrow, int kRule, bool kRing>
 __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) generation_kernel(const GenParams p)
 {
     __shared__ uint32_t s_thr[kMaxThr];
-    __shared__ int s_last;
+    __shared__ int s_last, s_stop;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemParts m = carve_smem<kRing>(smem_raw);
     load_thresholds(p, s_thr);
     grid_dependency_wait();
+    if (threadIdx.x == 0) s_stop = stop_state(p);
     __syncthreads();
+    const int32_t stop = s_stop;
+    if (stop == kStopped) return;            // converged in an earlier launch
     const BlockShare b = block_share(p);
     const int32_t t = *p.gen;
     const int32_t e_prev = *p.elite_idx;
-    if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing>(p, b, t, e_prev, m, s_thr);
-    else one_generation<kNarrow, kRule, false, kRing>(p, b, t, e_prev, m, s_thr);
+    if (stop == kStopPending) {
+        // the generation before met the convergence test: its CIP alone, then stopped
+        final_cip_body<kRule>(p, b, t - 1, e_prev);
+    } else if (p.apply_cip) {
+        one_generation<kNarrow, kRule, true, kRing>(p, b, t, e_prev, m, s_thr);
+    } else {
+        one_generation<kNarrow, kRule, false, kRing>(p, b, t, e_prev, m, s_thr);
+    }
 
     // The next generation's blocks may start their prologue now.
     allow_dependent_launch();
-    if (!p.do_de) return;
+    if (!p.do_de && stop == kRunning) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -919,6 +950,13 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    if (stop == kStopPending) {
+        if (threadIdx.x == 0) {
+            *p.ticket = 0u;
+            p.conv[1] = kStopped;
+        }
+        return;
+    }
     close_generation(p, t);
     if (threadIdx.x == 0) {
         *p.gen = t + 1;
@@ -965,7 +1003,12 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
 template <int kRule>
 __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
 {
+    __shared__ int s_stop, s_last;
     grid_dependency_wait();
+    if (threadIdx.x == 0) s_stop = stop_state(p);
+    __syncthreads();
+    const int32_t stop = s_stop;
+    if (stop == kStopped) return;
     const int32_t t_last = *p.gen - 1;
     const int32_t e = *p.elite_idx;
     const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
@@ -979,6 +1022,16 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
         const uint32_t e8 = elite[v];
         const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
         p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+    }
+    if (stop == kStopPending) {   // the run's last generation met the convergence test
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(p.ticket, 1u) == gridDim.x - 1u ? 1 : 0;
+        __syncthreads();
+        if (s_last && threadIdx.x == 0) {
+            *p.ticket = 0u;
+            p.conv[1] = kStopped;
+        }
     }
 }
 
@@ -1080,6 +1133,24 @@ __global__ void __launch_bounds__(kThreads) de_kernel(GenParams p)
     }
 }
 
+// CIP with elite e of generation t_prev on one segment (one tile, rows ra .. ra + rows).
+template <int kRule>
+__device__ __forceinline__ void rotate_segment(const GenParams &p, const BlockShare &b, int tile, int ra,
+                                               int rows, int32_t t_prev, int32_t e)
+{
+    const uint8_t *xl = p.xbits + (size_t)(t_prev & 1) * p.xplane;
+    const int vec = tile * b.tile_vecs + b.v_in;
+    if (vec >= p.svec) return;
+    const uint32_t e8 = __ldcg(xl + (size_t)e * p.xstride + vec);
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    for (int rr = b.r_sub; rr < rows; rr += b.rows_per_pass) {
+        const size_t c = (size_t)ra + rr;
+        const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
+        uint4 *sp = p.state + c * p.svec + vec;
+        *sp = rotate_vec(*sp, e8, m8, k8);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Batched form: many independent instances in one persistent launch per generation. The
 // host cuts every instance's ntile * np tile-rows into segments (one tile, at most
@@ -1113,7 +1184,7 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
     SmemParts m = carve_smem<true>(smem_raw);
     const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
     uint4 *slots = m.ring + threadIdx.x;
-    __shared__ int32_t s_si;
+    __shared__ int32_t s_si, s_stop;
     grid_dependency_wait();
     clear_row_sums<kNarrow>(a.seg_rows_max, m.acc32, m.acc64);
     int countdown = 0;
@@ -1138,15 +1209,22 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
                 __syncthreads();
             }
         }
+        if (threadIdx.x == 0) s_stop = stop_state(p);
+        __syncthreads();
+        const int32_t stop = s_stop;
+        if (stop == kStopped) continue;      // converged earlier: no work, no ticket
         const int32_t t = *p.gen;
         const int32_t e_prev = *p.elite_idx;
         const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
         uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
         const BlockShare b = tile_geometry(p.lanes, p.warps);
-        ring_segment<kNarrow, kRule, kCip>(p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra,
-                                           sg.rows, t, x_prev, x_cur,
-                                           x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots,
-                                           m.acc32, m.acc64, countdown);
+        if (stop == kStopPending)            // the CIP of the generation that converged
+            rotate_segment<kRule>(p, b, sg.tile, sg.ra, sg.rows, t - 1, e_prev);
+        else
+            ring_segment<kNarrow, kRule, kCip>(p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra,
+                                               sg.rows, t, x_prev, x_cur,
+                                               x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots,
+                                               m.acc32, m.acc64, countdown);
         // the block that finishes an instance's last segment closes its generation
         __threadfence();
         __syncthreads();
@@ -1157,11 +1235,18 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
         __syncthreads();
         if (s_last) {
             __threadfence();
-            close_generation(p, t);
-            if (threadIdx.x == 0) {
-                *p.gen = t + 1;
-                *p.ticket = 0u;
-                *p.bar_gen = t + 1;
+            if (stop == kStopPending) {
+                if (threadIdx.x == 0) {
+                    *p.ticket = 0u;
+                    p.conv[1] = kStopped;
+                }
+            } else {
+                close_generation(p, t);
+                if (threadIdx.x == 0) {
+                    *p.gen = t + 1;
+                    *p.ticket = 0u;
+                    *p.bar_gen = t + 1;
+                }
             }
             __syncthreads();
         }
@@ -1178,29 +1263,44 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
     }
 }
 
-// Final rotation of a batched run over the same segments.
+// Final rotation of a batched run over the same segments (an instance that met the
+// convergence test in the run's last generation is marked stopped by the block that
+// rotates its last segment).
 template <int kRule>
 __global__ void __launch_bounds__(kThreads) batch_cip_kernel(const BatchArgs a)
 {
+    __shared__ int s_stop, s_last;
     grid_dependency_wait();
     for (int32_t si = blockIdx.x; si < a.nsegs; si += gridDim.x) {
         const BatchSeg sg = a.segs[si];
         const GenParams &p = a.params[sg.inst];
-        const int32_t t_last = *p.gen - 1;
-        const int32_t e = *p.elite_idx;
-        const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
+        __syncthreads();
+        if (threadIdx.x == 0) s_stop = stop_state(p);
+        __syncthreads();
+        const int32_t stop = s_stop;
+        if (stop == kStopped) continue;
         const BlockShare b = tile_geometry(p.lanes, p.warps);
-        const int vec = sg.tile * b.tile_vecs + b.v_in;
-        if (vec >= p.svec) continue;
-        const uint32_t e8 = __ldcg(xl + (size_t)e * p.xstride + vec);
-        const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
-        for (int rr = b.r_sub; rr < sg.rows; rr += b.rows_per_pass) {
-            const size_t c = (size_t)sg.ra + rr;
-            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
-            uint4 *sp = p.state + c * p.svec + vec;
-            *sp = rotate_vec(*sp, e8, m8, k8);
+        rotate_segment<kRule>(p, b, sg.tile, sg.ra, sg.rows, *p.gen - 1, *p.elite_idx);
+        if (stop == kStopPending) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0)
+                s_last = atomicAdd(p.ticket, 1u) == (unsigned int)a.inst_segs[sg.inst] - 1u ? 1 : 0;
+            __syncthreads();
+            if (s_last && threadIdx.x == 0) {
+                *p.ticket = 0u;
+                p.conv[1] = kStopped;
+            }
         }
     }
+}
+
+// Stop states of a list of instances (the solve server reads them after each step).
+__global__ void __launch_bounds__(kThreads) gather_stop_kernel(int32_t *const *conv, int32_t n,
+                                                               int32_t *out)
+{
+    for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
+        out[i] = conv[i][1];
 }
 
 // Generation 0 state: every qubit at theta = pi/4 (n = K), no elite, no best record.
@@ -1227,6 +1327,8 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
         *p.elite_idx = 0;
         *p.bar_gen = 0;
         *p.error = 0;
+        p.conv[0] = 0;
+        p.conv[1] = kRunning;
         p.best[0] = 0;
         p.best[1] = -1;
         p.best[2] = -1;

@@ -31,6 +31,8 @@ QIEO_FLAG_TIME_KERNELS = 0x8
 QIEO_FLAG_COOPERATIVE = 0x10
 QIEO_FLAG_REGISTER_PREFETCH = 0x20
 QIEO_FLAG_UNFUSED = 0x40
+QIEO_FLAG_CONVERGE = 0x80
+QIEO_CONVERGE_WINDOW = 20
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
@@ -39,7 +41,7 @@ EXPORTS = (
     "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
-    "qieo_get_phase_times", "qieo_philox",
+    "qieo_get_phase_times", "qieo_get_convergence", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
     "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
     "qieo_server_get_stats", "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
@@ -90,7 +92,8 @@ class qieo_server_stats(C.Structure):
 class qieo_solve_result(C.Structure):
     _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("fitness", C.c_int64),
                 ("generation", C.c_int32), ("chromosome", C.c_int32), ("submit_s", C.c_double),
-                ("admit_s", C.c_double), ("done_s", C.c_double)]
+                ("admit_s", C.c_double), ("done_s", C.c_double), ("generations_run", C.c_int32),
+                ("converged", C.c_int32)]
 
 
 _LIB: C.CDLL | None = None
@@ -129,6 +132,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_set_launch_shape": ([P, P], C.c_int),
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
         "qieo_get_phase_times": ([P, P, P], C.c_int),
+        "qieo_get_convergence": ([P, P, P], C.c_int),
         "qieo_philox": ([P, P, i32], C.c_int),
         "qieo_generation_noalloc": ([P, P, i32, P, P, P, P], C.c_int),
         "qieo_create_batch": ([P, i32, P], C.c_int),
@@ -256,6 +260,13 @@ def qieo_get_phase_times(h):
     return {"cip": ms[0], "qip": ms[1], "evaluation": ms[2], "determine_elite": ms[3]}, int(n.value)
 
 
+def qieo_get_convergence(h):
+    """(stopped, stable generations) of an instance created with QIEO_FLAG_CONVERGE."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(load().qieo_get_convergence(h, C.byref(a), C.byref(b)))
+    return bool(a.value), int(b.value)
+
+
 def qieo_get_kernel_time(h):
     ms, n = C.c_double(), C.c_int64()
     _check(load().qieo_get_kernel_time(h, C.byref(ms), C.byref(n)))
@@ -346,10 +357,11 @@ class Server:
         self.ng = {}
 
     def submit(self, problem, np_: int, generations: int, seed: int = 1, inst: int = 0,
-               D: int = 100, lam: int = 1, rule: int = QIEO_RULE_R1) -> int:
+               D: int = 100, lam: int = 1, rule: int = QIEO_RULE_R1, flags: int = 0) -> int:
         p = qieo_default_params()
         p.np, p.seed, p.instance_id = int(np_), int(seed) & 0xFFFFFFFF, int(inst) & 0xFFFFFFFF
         p.dtheta_den, p.penalty_lambda, p.rotate_rule = int(D), int(lam), int(rule)
+        p.flags = int(flags)
         rid = qieo_server_submit(self.h, problem.weights, problem.values, problem.capacity, p,
                                  generations)
         self.ng[rid] = int(problem.ng)
@@ -488,6 +500,9 @@ class Instance:
 
     def phase_times(self):
         return qieo_get_phase_times(self.h)
+
+    def convergence(self):
+        return qieo_get_convergence(self.h)
 
     def autotune(self, trial_generations: int = 8) -> qieo_launch_shape:
         return qieo_autotune(self.h, trial_generations)

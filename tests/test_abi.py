@@ -68,6 +68,12 @@ def test_defaults_and_errors_without_gpu(lib):
         Q.qieo_create_instance([1, 2], [3, 4], 2,
                                _params(p, flags=Q.QIEO_FLAG_UNFUSED | Q.QIEO_FLAG_COOPERATIVE))
     assert e.value.status == Q.QIEO_ERR_INVALID
+    for bad in (dict(flags=Q.QIEO_FLAG_CONVERGE, elite_on_host=1),
+                dict(flags=Q.QIEO_FLAG_CONVERGE | Q.QIEO_FLAG_UNFUSED),
+                dict(flags=Q.QIEO_FLAG_CONVERGE | Q.QIEO_FLAG_COOPERATIVE)):
+        with pytest.raises(Q.QieoError) as e:
+            Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, **bad))
+        assert e.value.status == Q.QIEO_ERR_INVALID and "CONVERGE" in str(e.value)
     with pytest.raises(Q.QieoError) as e:
         Q.qieo_run(None, 1)
     assert e.value.status == Q.QIEO_ERR_INVALID
@@ -89,8 +95,8 @@ _LAYOUT_PROG = r"""
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(qieo_problem), sizeof(qieo_params),
          sizeof(qieo_launch_shape), offsetof(qieo_params, stream), offsetof(qieo_problem, capacity));
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qieo_server_config), sizeof(qieo_solve_result),
-         offsetof(qieo_solve_result, submit_s), sizeof(qieo_server_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(qieo_server_config), sizeof(qieo_solve_result),
+         offsetof(qieo_solve_result, submit_s), offsetof(qieo_solve_result, converged), sizeof(qieo_server_stats),
          offsetof(qieo_server_stats, queued), offsetof(qieo_server_stats, max_active));
   return 0;
 }
@@ -110,6 +116,7 @@ def test_struct_layout_matches_header():
     want = [C.sizeof(Q.qieo_problem), C.sizeof(Q.qieo_params), C.sizeof(Q.qieo_launch_shape),
             Q.qieo_params.stream.offset, Q.qieo_problem.capacity.offset,
             C.sizeof(Q.qieo_server_config), C.sizeof(Q.qieo_solve_result),
-            Q.qieo_solve_result.submit_s.offset, C.sizeof(Q.qieo_server_stats),
+            Q.qieo_solve_result.submit_s.offset, Q.qieo_solve_result.converged.offset,
+            C.sizeof(Q.qieo_server_stats),
             Q.qieo_server_stats.queued.offset, Q.qieo_server_stats.max_active.offset]
     assert got == want

@@ -113,3 +113,36 @@ def test_batch_rejects_bad_members():
             Q.qieo_create_batch([a.h, a.h])
         with pytest.raises(Q.QieoError):
             Q.qieo_create_batch([a.h, h.h])
+
+
+def test_batch_with_converging_members():
+    """Members with QIEO_FLAG_CONVERGE stop at the oracle's stopping generation inside the
+    batched runs (some inside a run, one on a run's last generation) while the others keep
+    going; every member equals its own oracle run."""
+    from oracle import oracle as O
+    cases = [(200, 30, 3), (120, 17, 8), (60, 5, 2), (60, 8, 2), (300, 40, 11)]
+    made = []
+    for ng, np_, seed in cases:
+        prob = W.knapsack(ng, seed)
+        ref = O.run(prob, np_, 300, seed=seed, window=20)
+        made.append((prob, np_, seed, ref, Q.Instance(prob, np_, seed=seed, flags=Q.QIEO_FLAG_CONVERGE)))
+    plain_prob = W.knapsack(500, 77)
+    plain = Q.Instance(plain_prob, 24, seed=77)
+    first = int(made[2][3].t[0])           # one member stops exactly at the end of run 1
+    with Q.Batch([m[4] for m in made] + [plain]) as b:
+        b.run(first)
+        for g in (25, 25, 25, 25, 25, 25, 25, 25, 25, 25):
+            b.run(g)
+    total = first + 250
+    for prob, np_, seed, ref, inst in made:
+        k, t = inst.state()
+        assert ref.stopped and t == int(ref.t[0]) <= total
+        assert np.array_equal(k, ref.k)
+        e, f = inst.history(0, t)
+        assert np.array_equal(e, ref.hist_e) and np.array_equal(f, ref.hist_f)
+        bits, bf, bg, bc = inst.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in ref.best)
+        assert inst.convergence()[0]
+        inst.close()
+    check_against_oracle(plain, plain_prob, 24, total, 77, 0)
+    plain.close()

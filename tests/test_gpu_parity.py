@@ -281,3 +281,48 @@ def test_host_elite_phase_time():
         I.run(6)
         ms, gens = I.phase_times()
         assert gens == 6 and ms["determine_elite"] > 0 and ms["qip"] == 0
+
+
+def _first_stable(hist_f, window=20):
+    for t in range(window - 1, len(hist_f)):
+        if np.all(hist_f[t - window + 1:t + 1] == hist_f[t]):
+            return t
+    return None
+
+
+@pytest.mark.parametrize("where", ["inside", "boundary", "first", "no_graph"])
+def test_convergence_stop_matches_oracle(where):
+    """QIEO_FLAG_CONVERGE: the run stops at the generation the oracle's convergence test
+    picks, whether that falls inside a run, on a run's last generation, or in the first
+    run; runs after the stop change nothing."""
+    from oracle import oracle as O
+    prob, np_, seed = W.knapsack(200, 3), 30, 3
+    ref = O.run(prob, np_, 400, seed=seed, window=20)
+    tc = int(ref.t[0]) - 1
+    assert ref.stopped and tc == _first_stable(O.run(prob, np_, 400, seed=seed).hist_f)
+    chunks = {"inside": [tc - 5, 50, 50], "boundary": [tc + 1, 30], "first": [400, 10],
+              "no_graph": [7] * 40}[where]
+    flags = Q.QIEO_FLAG_CONVERGE | (Q.QIEO_FLAG_NO_GRAPH if where == "no_graph" else 0)
+    with Q.Instance(prob, np_, seed=seed, flags=flags) as I:
+        for g in chunks:
+            I.run(g)
+        k, t = I.state()
+        assert t == tc + 1
+        assert np.array_equal(k, ref.k)
+        e, f = I.history(0, t)
+        assert np.array_equal(e, ref.hist_e) and np.array_equal(f, ref.hist_f)
+        bits, bf, bg, bc = I.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in ref.best)
+        assert np.array_equal(bits, ref.best_x)
+        assert I.convergence() == (True, 20)
+
+
+def test_convergence_flag_off_runs_every_generation():
+    from oracle import oracle as O
+    prob = W.knapsack(200, 3)
+    compare(prob, 30, [150], seed=3)
+    with Q.Instance(prob, 30, seed=3, flags=Q.QIEO_FLAG_CONVERGE) as I:
+        I.run(10)
+        stopped, stable = I.convergence()
+        ref = O.run(prob, 30, 10, seed=3, window=20)
+        assert not stopped and stable == int(ref.conv[0])

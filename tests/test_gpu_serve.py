@@ -102,3 +102,24 @@ def test_server_counts_steps_and_launches():
     assert st["queued"] == 0 and st["active"] == 0 and 1 <= st["max_active"] <= 6
     assert st["steps"] >= 3
     assert st["kernel_launches"] >= 6 + st["steps"] * 2
+
+
+def test_server_convergence_stop():
+    """Requests with QIEO_FLAG_CONVERGE leave as soon as they converged; each result equals
+    the oracle's run with the same stop, and a request without the flag runs its cap."""
+    from oracle import oracle as O
+    srv = Q.Server(gens_per_step=10)
+    cases = [(200, 30, 3), (120, 17, 8), (60, 5, 2), (300, 40, 11)]
+    ids = [srv.submit(W.knapsack(ng, s), np_, 400, seed=s, flags=Q.QIEO_FLAG_CONVERGE)
+           for ng, np_, s in cases]
+    plain = srv.submit(W.knapsack(90, 5), 16, 60, seed=5)
+    for rid, (ng, np_, s) in zip(ids, cases):
+        res, bits = srv.poll(rid, wait_ms=60000)
+        ref = O.run(W.knapsack(ng, s), np_, 400, seed=s, window=20)
+        assert res.state == Q.QIEO_SOLVE_DONE and res.converged == 1
+        assert res.generations_run == int(ref.t[0]) < 400
+        assert (res.fitness, res.generation, res.chromosome) == tuple(int(v) for v in ref.best)
+        assert np.array_equal(bits, ref.best_x)
+    res, _ = srv.poll(plain, wait_ms=60000)
+    assert res.state == Q.QIEO_SOLVE_DONE and res.converged == 0 and res.generations_run == 60
+    srv.close()
