@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--phases", action="store_true",
                     help="per-step breakdown (CIP, QIP, Evaluation, DetermineElite) of the "
                          "unfused form, and device vs host DetermineElite, on --workload")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time per generation over the paper's (Np, Ng) grid")
+    ap.add_argument("--sweep-max-gb", type=float, default=120.0,
+                    help="--sweep: skip pairs whose instance needs more device memory")
     ap.add_argument("--ref-budget-s", type=float, default=150.0,
                     help="--impl reference: seconds of oracle work over warm-up + timed steps")
     return ap.parse_args()
@@ -800,8 +804,73 @@ def run_phases(a):
     print(json.dumps(line), flush=True)
 
 
+SWEEP_NP = [32 << i for i in range(14)]                     # 32 .. 262,144
+SWEEP_NG = [500, 1000, 2500, 5000, 10000, 25000, 50000, 100000, 200000]
+
+
+def run_sweep(a):
+    """Time per generation over the paper's (Np, Ng) grid (Np = 32 .. 262,144 in powers of
+    two, Ng = 500 .. 200,000 in 1-2.5-5 steps), rules R1 and R2, for every pair whose
+    instance fits --sweep-max-gb of device memory. Each pair is timed over its first
+    generations from the start state (the population still spread: the costly phase), at
+    least 3 generations and about 2e9 gene-updates."""
+    import torch
+    from paper_2609_30862_gb300 import qieo as Q
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(0)
+    Q.load()
+    stream = torch.cuda.Stream()
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    rows = []
+    t_start = time.perf_counter()
+    for rule in (0, 1):
+        for np_ in SWEEP_NP:
+            for ng in SWEEP_NG:
+                svec = (ng + 7) // 8
+                need = np_ * svec * 16 + 2 * np_ * ((svec + 15) // 16 * 16) + 64 * svec + 64 * np_
+                if need > a.sweep_max_gb * 1e9:
+                    continue
+                if rule == 1 and (np_ * ng > 1 << 30):
+                    continue        # R2 on the smaller half of the grid only
+                G = int(max(3, min(200, round(2e9 / (np_ * ng)))))
+                prob = WL.knapsack(ng, 1)
+                with Q.Instance(prob, np_, seed=1, rule=rule, stream=stream.cuda_stream) as inst:
+                    with torch.cuda.stream(stream):
+                        inst.run(G)
+                        inst.reset()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        inst.run(G)
+                        e1.record(stream)
+                        e1.synchronize()
+                    us = 1e3 * e0.elapsed_time(e1) / G
+                    rows.append({"np": np_, "ng": ng, "rule": "R2" if rule else "R1", "gens": G,
+                                 "us_per_gen": round(us, 3),
+                                 "gene_updates_per_s": np_ * ng / (us * 1e-6),
+                                 "hbm_frac": STATE_BYTES_PER_GENE * np_ * ng / (us * 1e-6) / 1e9 / hbm,
+                                 "state_gb": round(np_ * svec * 16 / 1e9, 3)})
+                torch.cuda.empty_cache()
+    best = max(rows, key=lambda r: r["gene_updates_per_s"])
+    line = {
+        "metric": "time per generation over the (Np, Ng) grid", "value": best["gene_updates_per_s"],
+        "unit": "gene-updates/s (best pair)", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "Np in 32..262144 (x2), Ng in %s, item seed 1, first generations "
+                               "from the start state" % SWEEP_NG, "max_gb": a.sweep_max_gb},
+        "peak_hbm_gbs": hbm, "peak_source": peak_src, "pairs": rows,
+        "wall_s": time.perf_counter() - t_start,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.impl != "reference" and a.sweep:
+        run_sweep(a)
+        return
     if a.impl != "reference" and a.phases:
         run_phases(a)
         return
