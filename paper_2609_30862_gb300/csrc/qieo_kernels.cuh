@@ -198,6 +198,8 @@ __device__ void close_generation(const GenParams &p, int32_t t)
     const int tid = threadIdx.x;
     int64_t bf = INT64_MIN;
     int32_t bc = 0x7fffffff;
+    // the previous best record, loaded together with the elite key (one round trip)
+    const int64_t best_f = tid == 0 ? __ldcg(p.best) : 0, best_g = tid == 0 ? __ldcg(p.best + 1) : 0;
     if (p.key_mode) {
         if (tid == 0) {
             const unsigned long long k = __ldcg(p.key);
@@ -252,7 +254,6 @@ __device__ void close_generation(const GenParams &p, int32_t t)
         p.hist_e[t] = bc;
         p.hist_f[t] = bf;
         *p.elite_idx = bc;
-        const int64_t best_f = __ldcg(p.best), best_g = __ldcg(p.best + 1);
         const int improved = (best_g < 0 || bf > best_f) ? 1 : 0;
         if (improved) {
             p.best[0] = bf;
@@ -941,15 +942,16 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
     // The next generation's blocks may start their prologue now.
     allow_dependent_launch();
     if (!p.do_de && stop == kRunning) return;
-    __threadfence();
+    // Ticket: the barrier orders every thread's writes of this block before thread 0's
+    // release; the last block's acquire (then its barrier) makes all blocks' writes visible
+    // to the close.
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int prev = atomicAdd(p.ticket, 1u);
+        const unsigned int prev = atom_add_acq_rel(p.ticket, 1u);
         s_last = (prev == gridDim.x - 1u) ? 1 : 0;
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     if (stop == kStopPending) {
         if (threadIdx.x == 0) {
             *p.ticket = 0u;
@@ -1225,16 +1227,15 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
                                                sg.rows, t, x_prev, x_cur,
                                                x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots,
                                                m.acc32, m.acc64, countdown);
-        // the block that finishes an instance's last segment closes its generation
-        __threadfence();
+        // the block that finishes an instance's last segment closes its generation (barrier
+        // + release by thread 0, acquire by the last block's thread 0 + barrier)
         __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned int prev = atomicAdd(p.ticket, 1u);
+            const unsigned int prev = atom_add_acq_rel(p.ticket, 1u);
             s_last = (prev == (unsigned int)a.inst_segs[sg.inst] - 1u) ? 1 : 0;
         }
         __syncthreads();
         if (s_last) {
-            __threadfence();
             if (stop == kStopPending) {
                 if (threadIdx.x == 0) {
                     *p.ticket = 0u;
