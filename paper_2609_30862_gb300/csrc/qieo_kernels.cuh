@@ -281,25 +281,36 @@ struct BlockShare {
 };
 
 // Thread geometry of a tile of lanes x warps vectors in a block of kThreads threads.
+// (lanes and warps are powers of two, so the split is shifts and masks)
 __device__ __forceinline__ BlockShare tile_geometry(int lanes, int warps)
 {
     BlockShare b;
     b.lanes = lanes;
     b.tile_vecs = lanes * warps;
-    b.rows_per_pass = kThreads / b.tile_vecs;
-    b.r_sub = threadIdx.x / b.tile_vecs;
-    b.v_in = threadIdx.x - b.r_sub * b.tile_vecs;
+    const int sh = __ffs(b.tile_vecs) - 1;
+    b.rows_per_pass = kThreads >> sh;
+    b.r_sub = threadIdx.x >> sh;
+    b.v_in = threadIdx.x & (b.tile_vecs - 1);
     b.leader = (threadIdx.x & (lanes - 1)) == 0;
     b.u_begin = 0;
     b.u_end = 0;
     return b;
 }
 
+// Tile-rows [u_begin, u_end) of this block: an equal split of the ntile * np tile-rows, in
+// 32-bit arithmetic whenever the products fit (a 64-bit division is a long software routine).
 __device__ __forceinline__ BlockShare block_share(const GenParams &p)
 {
     BlockShare b = tile_geometry(p.lanes, p.warps);
-    b.u_begin = (int64_t)blockIdx.x * p.units / gridDim.x;
-    b.u_end = (int64_t)(blockIdx.x + 1) * p.units / gridDim.x;
+    const uint64_t units = (uint64_t)p.units;
+    if (units * gridDim.x <= 0xffffffffull) {
+        const uint32_t u = (uint32_t)units;
+        b.u_begin = (int64_t)((blockIdx.x * u) / gridDim.x);
+        b.u_end = (int64_t)(((blockIdx.x + 1u) * u) / gridDim.x);
+    } else {
+        b.u_begin = (int64_t)blockIdx.x * p.units / gridDim.x;
+        b.u_end = (int64_t)(blockIdx.x + 1) * p.units / gridDim.x;
+    }
     return b;
 }
 
