@@ -269,11 +269,16 @@ cudaLaunchConfig_t launch_config(const qieo_instance *q, dim3 grid, size_t smem,
     return cfg;
 }
 
-cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de)
+// One generation launch. deferred_g >= 0 selects the deferred close (generation *gen +
+// deferred_g of the run); -1 the close by the last block (the generation counter advances
+// per launch).
+cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de, int32_t deferred_g = -1)
 {
     qieo::GenParams p = q->gp;
     p.apply_cip = apply_cip;
     p.do_de = do_de;
+    p.deferred = deferred_g >= 0 ? 1 : 0;
+    p.g = deferred_g >= 0 ? deferred_g : 0;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(q, dim3(q->grid), q->smem, attr);
     return cudaLaunchKernelEx(&cfg, kernel_of<PickGen>(q, q->gp.ring != 0), p);
@@ -294,16 +299,23 @@ cudaError_t launch_run(const qieo_instance *q, int32_t G)
     return cudaLaunchKernelEx(&cfg, kernel_of<PickRun>(q, q->gp.ring != 0), q->gp, G);
 }
 
-cudaError_t launch_final_cip(const qieo_instance *q)
+cudaError_t launch_final_cip(const qieo_instance *q, int32_t deferred_G = 0)
 {
     const size_t total = (size_t)q->np * q->svec;
     const int blocks = (int)std::max<size_t>(
         1, std::min<size_t>((total + qieo::kThreads - 1) / qieo::kThreads,
                             (size_t)std::max(q->sm_count, 1) * 8));
+    qieo::GenParams p = q->gp;
+    p.deferred = deferred_G > 0 ? 1 : 0;
+    p.g = deferred_G;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(q, dim3(blocks), 0, attr);
-    if (q->rule) return cudaLaunchKernelEx(&cfg, qieo::cip_kernel<1>, q->gp);
-    return cudaLaunchKernelEx(&cfg, qieo::cip_kernel<0>, q->gp);
+    cudaError_t ce = q->rule ? cudaLaunchKernelEx(&cfg, qieo::cip_kernel<1>, p)
+                             : cudaLaunchKernelEx(&cfg, qieo::cip_kernel<0>, p);
+    if (ce != cudaSuccess || deferred_G <= 0) return ce;
+    cudaLaunchConfig_t one = launch_config(q, dim3(1), 0, attr);
+    one.blockDim = dim3(32);
+    return cudaLaunchKernelEx(&one, qieo::end_run_kernel, p, deferred_G);
 }
 
 qieo_status wait_stream(cudaStream_t s)
@@ -376,9 +388,12 @@ qieo_status ensure_history(qieo_instance *q, int32_t need)
 qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
 {
     if (q->flags & QIEO_FLAG_TIME_KERNELS) CUDA_TRY(cudaEventRecord(q->ev0, q->stream));
-    for (int32_t g = 0; g < G; ++g) CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 1));
+    // Deferred close whenever the elite key holds the fitness (the generation counter then
+    // advances once per run); otherwise the last block of each generation closes it.
+    const bool deferred = q->key_ok;
+    for (int32_t g = 0; g < G; ++g) CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 1, deferred ? g : -1));
     if (q->flags & QIEO_FLAG_TIME_KERNELS) CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
-    CUDA_TRY(launch_final_cip(q));
+    CUDA_TRY(launch_final_cip(q, deferred ? G : 0));
     return QIEO_OK;
 }
 
@@ -604,11 +619,11 @@ size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size
                                   3 * sizeof(int64_t),
                                   sizeof(int32_t),
                                   sizeof(unsigned int),
-                                  sizeof(unsigned long long),
+                                  3 * sizeof(unsigned long long),   // elite key slots
                                   sizeof(int32_t),
                                   (size_t)(D / 2 + 1) * sizeof(uint32_t),
                                   sizeof(int32_t),
-                                  3 * sizeof(int32_t),   // error word, convergence words
+                                  5 * sizeof(int32_t),   // error word, convergence words
                                   (size_t)hist_cap * sizeof(int32_t),
                                   (size_t)hist_cap * sizeof(int64_t)};
     size_t total = 0;
@@ -735,7 +750,7 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     g.best = (int64_t *)(b + off[8]);
     g.gen = (int32_t *)(b + off[9]);
     g.ticket = (unsigned int *)(b + off[10]);
-    g.key = (unsigned long long *)(b + off[11]);
+    g.keys = (unsigned long long *)(b + off[11]);
     g.elite_idx = (int32_t *)(b + off[12]);
     g.thr = (const uint32_t *)(b + off[13]);
     g.bar_gen = (int32_t *)(b + off[14]);
@@ -1077,11 +1092,12 @@ qieo_status qieo_get_convergence(qieo_instance *q, int32_t *stopped, int32_t *st
     if (st != QIEO_OK) return st;
     st = set_device(q);
     if (st != QIEO_OK) return st;
-    int32_t w[2] = {0, 0};
+    int32_t w[4] = {0, 0, 0, 0}, t = 0;
     st = fetch(q, w, q->gp.conv, sizeof w);
+    if (st == QIEO_OK) st = fetch(q, &t, q->gp.gen, sizeof t);
     if (st != QIEO_OK) return st;
-    if (stopped) *stopped = w[1] != qieo::kRunning ? 1 : 0;
-    if (stable) *stable = w[0];
+    if (stopped) *stopped = w[2] != qieo::kRunning ? 1 : 0;
+    if (stable) *stable = t > 0 ? w[(t - 1) & 1] : 0;
     return QIEO_OK;
 }
 

@@ -113,7 +113,7 @@ struct GenParams {
     unsigned long long *acc;      // narrow [np]; wide [2 np]
     unsigned int *cnt;            // wide: [np]
     int64_t *fitness;             // [np] of the last generation
-    unsigned long long *key;      // [1] elite key of the running generation
+    unsigned long long *keys;     // [3] elite key of generation t in slot t % 3
     int32_t *elite_idx;           // [1] elite of the last completed generation
     int32_t *hist_e;              // [capacity] elite index per generation
     int64_t *hist_f;              // [capacity] elite fitness per generation
@@ -123,10 +123,11 @@ struct GenParams {
     unsigned int *ticket;         // blocks finished in this generation
     int32_t *bar_gen;             // grid barrier: generations released so far
     int32_t *error;               // kErr* bits
-    int32_t *conv;                // [2] convergence test: run length of equal elite
-                                  // fitness ending at the last generation, stop state
-                                  // (kRunning, kStopPending: the final CIP is still due,
-                                  // kStopped)
+    int32_t *conv;                // [4] convergence test: run length of equal elite
+                                  // fitness ending at generation t in conv[t & 1], the
+                                  // stop state (kRunning, kStopPending: the final CIP is
+                                  // still due, kStopped) in conv[2], and in conv[3] the
+                                  // generation that met the test
     const uint32_t *thr;          // [2K+1] low 32 bits of T[n] (T[2K] = 2^32 -> 0)
     int64_t capacity, lambda;
     int64_t units;                // ntile * np tile-rows
@@ -137,6 +138,9 @@ struct GenParams {
     int32_t apply_cip, do_de;
     int32_t ring;                 // 1: state streamed through the per-thread cp.async ring
     int32_t converge;             // 1: stop once the elite fitness is stable (kConvergeWindow)
+    int32_t g;                    // generation of this launch within its run (deferred
+                                  // close: t = *gen + g; otherwise 0 and t = *gen)
+    int32_t deferred;             // 1: deferred close (see generation_kernel)
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -149,21 +153,28 @@ constexpr int32_t kRunning = 0, kStopPending = 1, kStopped = 2;
 
 __device__ __forceinline__ int32_t stop_state(const GenParams &p)
 {
-    return p.converge ? *(volatile const int32_t *)(p.conv + 1) : kRunning;
+    return p.converge ? *(volatile const int32_t *)(p.conv + 2) : kRunning;
+}
+
+__device__ __forceinline__ unsigned long long *key_slot(const GenParams &p, int32_t t)
+{
+    return p.keys + (t % 3);
 }
 
 // Eq. (1) of a finished row; records the fitness and offers the row to the elite key.
-__device__ __forceinline__ void finish_row(const GenParams &p, int32_t c, int64_t sw, int64_t sv)
+__device__ __forceinline__ void finish_row(const GenParams &p, int32_t c, int64_t sw, int64_t sv,
+                                           int32_t t)
 {
     const int64_t f = sw <= p.capacity ? sv : -p.lambda * (sw - p.capacity);
     p.fitness[c] = f;
-    if (p.key_mode) atomicMax(p.key, elite_key(f, c));
+    if (p.key_mode) atomicMax(key_slot(p, t), elite_key(f, c));
 }
 
 // Adds one block's sums of a tile-row to the row; the block that adds the last of the
 // ntile contributions evaluates the row.
 template <bool kNarrow>
-__device__ __forceinline__ void combine_row(const GenParams &p, int32_t c, uint64_t sw, uint64_t sv)
+__device__ __forceinline__ void combine_row(const GenParams &p, int32_t c, uint64_t sw, uint64_t sv,
+                                            int32_t t)
 {
     if (kNarrow) {
         const unsigned long long add = (1ull << 52) | (sv << 26) | sw;
@@ -171,7 +182,7 @@ __device__ __forceinline__ void combine_row(const GenParams &p, int32_t c, uint6
         if ((int32_t)(old >> 52) == p.ntile - 1) {
             const unsigned long long full = old + add;
             p.acc[c] = 0ull;
-            finish_row(p, c, (int64_t)(full & 0x3ffffffull), (int64_t)((full >> 26) & 0x3ffffffull));
+            finish_row(p, c, (int64_t)(full & 0x3ffffffull), (int64_t)((full >> 26) & 0x3ffffffull), t);
         }
     } else {
         atomicAdd(p.acc + 2 * (size_t)c, (unsigned long long)sw);
@@ -182,7 +193,7 @@ __device__ __forceinline__ void combine_row(const GenParams &p, int32_t c, uint6
             p.acc[2 * (size_t)c] = 0ull;
             p.acc[2 * (size_t)c + 1] = 0ull;
             p.cnt[c] = 0u;
-            finish_row(p, c, w, v);
+            finish_row(p, c, w, v, t);
         }
     }
 }
@@ -202,10 +213,10 @@ __device__ void close_generation(const GenParams &p, int32_t t)
     const int64_t best_f = tid == 0 ? __ldcg(p.best) : 0, best_g = tid == 0 ? __ldcg(p.best + 1) : 0;
     if (p.key_mode) {
         if (tid == 0) {
-            const unsigned long long k = __ldcg(p.key);
+            const unsigned long long k = __ldcg(key_slot(p, t));
             bc = (int32_t)(0xffffffu - (uint32_t)(k & 0xffffffull));
             bf = (int64_t)(k >> 24) - kKeyBias;
-            *p.key = 0ull;
+            *key_slot(p, t) = 0ull;
         }
     } else {
         for (int c = tid; c < p.np; c += kThreads) {
@@ -247,9 +258,13 @@ __device__ void close_generation(const GenParams &p, int32_t t)
             bc = 0;
         }
         if (p.converge) {
-            const int32_t run = (t > 0 && p.conv[0] > 0 && bf == p.hist_f[t - 1]) ? p.conv[0] + 1 : 1;
-            p.conv[0] = run;
-            if (run >= kConvergeWindow) p.conv[1] = kStopPending;
+            const int32_t prev = t > 0 ? p.conv[(t - 1) & 1] : 0;
+            const int32_t run = (prev > 0 && bf == p.hist_f[t - 1]) ? prev + 1 : 1;
+            p.conv[t & 1] = run;
+            if (run >= kConvergeWindow) {
+                p.conv[3] = t;
+                p.conv[2] = kStopPending;
+            }
         }
         p.hist_e[t] = bc;
         p.hist_f[t] = bf;
@@ -533,17 +548,17 @@ __device__ __forceinline__ void add_row_sums(int lanes, bool leader, bool ok, in
 // Adds the block's tile-row sums of a segment to the rows (one atomic per tile-row) and
 // clears the shared accumulators. Called by the whole block.
 template <bool kNarrow>
-__device__ __forceinline__ void flush_segment(const GenParams &p, int ra, int seg_rows,
+__device__ __forceinline__ void flush_segment(const GenParams &p, int32_t t, int ra, int seg_rows,
                                               uint32_t *s_acc32, unsigned long long *s_acc64)
 {
     __syncthreads();
     for (int i = threadIdx.x; i < seg_rows; i += kThreads) {
         if (kNarrow) {
-            combine_row<true>(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1]);
+            combine_row<true>(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1], t);
             s_acc32[2 * i] = 0u;
             s_acc32[2 * i + 1] = 0u;
         } else {
-            combine_row<false>(p, ra + i, s_acc64[2 * i], s_acc64[2 * i + 1]);
+            combine_row<false>(p, ra + i, s_acc64[2 * i], s_acc64[2 * i + 1], t);
             s_acc64[2 * i] = 0ull;
             s_acc64[2 * i + 1] = 0ull;
         }
@@ -636,7 +651,7 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
             xb1 = load_xold(pass + 4);
             process(sc, xc, pass + 2);
         }
-        flush_segment<kNarrow>(p, ra, seg_rows, s_acc32, s_acc64);
+        flush_segment<kNarrow>(p, t, ra, seg_rows, s_acc32, s_acc64);
     }
 }
 
@@ -748,7 +763,7 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         rr += rpp;
     }
     cp_async_wait<0>();
-    flush_segment<kNarrow>(p, ra, seg_rows, s_acc32, s_acc64);
+    flush_segment<kNarrow>(p, t, ra, seg_rows, s_acc32, s_acc64);
 }
 
 template <bool kNarrow>
@@ -921,19 +936,139 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_k
     final_cip_body<kRule>(p, b, t0 + G - 1, e);
 }
 
+// Records of generation t with elite e of fitness f: the history, the elite index, the
+// best-so-far record (its row copied on a strict improvement) and, with the convergence
+// test, the run length of equal elite fitness ending at t. Called by all threads of one
+// block; returns that run length (0 when the test is off).
+__device__ int32_t record_generation(const GenParams &p, int32_t t, int32_t e, int64_t f)
+{
+    __shared__ int32_t s_improved, s_run;
+    if (threadIdx.x == 0) {
+        const int64_t best_f = __ldcg(p.best), best_g = __ldcg(p.best + 1);
+        p.hist_e[t] = e;
+        p.hist_f[t] = f;
+        *p.elite_idx = e;
+        const int improved = (best_g < 0 || f > best_f) ? 1 : 0;
+        if (improved) {
+            p.best[0] = f;
+            p.best[1] = t;
+            p.best[2] = e;
+        }
+        int32_t run = 0;
+        if (p.converge) {
+            const int32_t prev = t > 0 ? p.conv[(t - 1) & 1] : 0;
+            run = (prev > 0 && f == p.hist_f[t - 1]) ? prev + 1 : 1;
+            p.conv[t & 1] = run;
+        }
+        s_improved = improved;
+        s_run = run;
+    }
+    __syncthreads();
+    if (s_improved) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(
+            p.xbits + (size_t)(t & 1) * p.xplane + (size_t)e * p.xstride);
+        uint4 *dst = reinterpret_cast<uint4 *>(p.best_row);
+        for (int i = threadIdx.x; i < p.xstride / 16; i += kThreads) dst[i] = __ldcg(src + i);
+    }
+    const int32_t run = s_run;
+    __syncthreads();
+    return run;
+}
+
+// Elite of generation t from its key slot (every row of t has been folded into it).
+__device__ __forceinline__ void elite_from_key(const GenParams &p, int32_t t, int32_t &e, int64_t &f)
+{
+    const unsigned long long k = __ldcg(key_slot(p, t));
+    e = (int32_t)(0xffffffu - (uint32_t)(k & 0xffffffull));
+    f = (int64_t)(k >> 24) - kKeyBias;
+    if (e < 0 || e >= p.np) {   // every row finishes in every generation; see close_generation
+        if (blockIdx.x == 0) atomicOr(p.error, kErrEliteRange);
+        e = 0;
+    }
+}
+
+// Stop state of a deferred-close launch at generation t: 1 when the instance stopped
+// before this launch's work (at a run's first generation: stopped at all; later: stopped
+// at a generation <= t - 2, whose CIP an earlier launch applied).
+__device__ __forceinline__ int deferred_skip(const GenParams &p, int32_t t)
+{
+    if (!p.converge) return 0;
+    const int32_t state = ld_acquire(p.conv + 2);
+    if (state != kStopped) return 0;
+    return (p.g == 0 || *(volatile const int32_t *)(p.conv + 3) <= t - 2) ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------------------
-// generation_kernel: one generation per launch. The last block to finish closes the
-// generation (no block waits for another).
+// generation_kernel: one generation per launch.
+//
+// Deferred close (device DetermineElite with the packed elite key, the default): no block
+// waits for another. Every block reads the elite of generation t - 1 from its key slot at
+// its start (the previous launch has completed, so every row of t - 1 is in the key) and
+// rotates toward it; block 0 also writes the records of t - 1 and clears the key slot of
+// t + 1. The records of a run's last generation are written by the final CIP launch, and a
+// last one-thread launch advances the generation counter by the run. The convergence test
+// of generation t - 1 is evaluated by every block from the same data (the key of t - 1,
+// the run length and elite fitness recorded for t - 2), so all blocks agree; when it holds,
+// the launch applies the CIP of t - 1 alone and block 0 marks the instance stopped.
+//
+// Otherwise (elite by a scan of fitness[] when the fitness does not fit the key, or the
+// host DetermineElite variant): the last block to finish closes the generation.
 // ---------------------------------------------------------------------------------------
 template <bool kNarrow, int kRule, bool kRing>
 __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) generation_kernel(const GenParams p)
 {
     __shared__ uint32_t s_thr[kMaxThr];
-    __shared__ int s_last, s_stop;
+    __shared__ int s_last, s_stop, s_t, s_e;
+    __shared__ long long s_f;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemParts m = carve_smem<kRing>(smem_raw);
     load_thresholds(p, s_thr);
     grid_dependency_wait();
+    if (p.deferred) {
+        if (threadIdx.x == 0) {
+            const int32_t t = *p.gen + p.g;
+            int stop = deferred_skip(p, t) ? kStopped : kRunning;
+            int32_t e = 0;
+            int64_t f = 0;
+            if (stop == kRunning && p.apply_cip) {
+                elite_from_key(p, t - 1, e, f);
+                if (p.converge) {   // did generation t - 1 meet the convergence test?
+                    const int32_t prev = t - 1 > 0 ? p.conv[(t - 2) & 1] : 0;
+                    const int32_t run = (prev > 0 && f == p.hist_f[t - 2]) ? prev + 1 : 1;
+                    if (run >= kConvergeWindow) stop = kStopPending;
+                }
+            }
+            s_t = t;
+            s_stop = stop;
+            s_e = e;
+            s_f = f;
+        }
+        __syncthreads();
+        const int32_t stop = s_stop, t = s_t, e_prev = s_e;
+        const int64_t f_prev = s_f;
+        if (stop == kStopped) return;
+        const BlockShare b = block_share(p);
+        if (blockIdx.x == 0) {
+            if (p.apply_cip) {
+                record_generation(p, t - 1, e_prev, f_prev);
+                if (stop == kStopPending && threadIdx.x == 0) {
+                    p.conv[3] = t - 1;
+                    __threadfence();
+                    st_release(p.conv + 2, kStopped);
+                }
+            }
+            if (threadIdx.x == 0) *key_slot(p, t + 1) = 0ull;
+        }
+        if (stop == kStopPending) {
+            final_cip_body<kRule>(p, b, t - 1, e_prev);   // the CIP of the converged generation
+            return;
+        }
+        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing>(p, b, t, e_prev, m, s_thr);
+        else one_generation<kNarrow, kRule, false, kRing>(p, b, t, e_prev, m, s_thr);
+        allow_dependent_launch();
+        return;
+    }
+
     if (threadIdx.x == 0) s_stop = stop_state(p);
     __syncthreads();
     const int32_t stop = s_stop;
@@ -966,7 +1101,7 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
     if (stop == kStopPending) {
         if (threadIdx.x == 0) {
             *p.ticket = 0u;
-            p.conv[1] = kStopped;
+            p.conv[2] = kStopped;
         }
         return;
     }
@@ -976,6 +1111,21 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
         *p.ticket = 0u;
         *p.bar_gen = t + 1;
     }
+}
+
+// End of a deferred-close run of G generations: advances the generation counter (to one past
+// the generation that met the convergence test, if the instance stopped) and clears the
+// three key slots. One thread.
+__global__ void end_run_kernel(const GenParams p, int32_t G)
+{
+    grid_dependency_wait();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int32_t gen = *p.gen;
+    int32_t next = gen + G;
+    if (p.converge && p.conv[2] == kStopped) next = min(next, p.conv[3] + 1);
+    *p.gen = next;
+    *p.bar_gen = next;
+    p.keys[0] = p.keys[1] = p.keys[2] = 0ull;
 }
 
 // Records of a generation whose elite e was picked on the host (host DetermineElite).
@@ -990,7 +1140,7 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
         p.hist_e[t] = e;
         p.hist_f[t] = fe;
         *p.elite_idx = e;
-        *p.key = 0ull;
+        *key_slot(p, t) = 0ull;
         const int improved = (p.best[1] < 0 || fe > p.best[0]) ? 1 : 0;
         if (improved) {
             p.best[0] = fe;
@@ -1016,8 +1166,48 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
 template <int kRule>
 __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
 {
-    __shared__ int s_stop, s_last;
+    __shared__ int s_stop, s_last, s_t, s_e;
+    __shared__ long long s_f;
     grid_dependency_wait();
+    if (p.deferred) {
+        // the final CIP of a deferred-close run of p.g generations: elite of the last
+        // generation from its key; block 0 writes that generation's records
+        if (threadIdx.x == 0) {
+            const int32_t t_last = *p.gen + p.g - 1;
+            const int skip = deferred_skip(p, t_last + 1);
+            int32_t e = 0;
+            int64_t f = 0;
+            if (!skip) elite_from_key(p, t_last, e, f);
+            s_stop = skip;
+            s_t = t_last;
+            s_e = e;
+            s_f = f;
+        }
+        __syncthreads();
+        if (s_stop) return;
+        const int32_t t_last = s_t, e = s_e;
+        if (blockIdx.x == 0) {
+            const int32_t run = record_generation(p, t_last, e, s_f);
+            if (run >= kConvergeWindow && threadIdx.x == 0) {
+                p.conv[3] = t_last;
+                __threadfence();
+                st_release(p.conv + 2, kStopped);
+            }
+        }
+        const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
+        const uint8_t *elite = xl + (size_t)e * p.xstride;
+        const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+        const size_t total = (size_t)p.np * p.svec;
+        for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
+             i += (size_t)gridDim.x * kThreads) {
+            const size_t c = i / (size_t)p.svec;
+            const size_t v = i - c * (size_t)p.svec;
+            const uint32_t e8 = elite[v];
+            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
+            p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+        }
+        return;
+    }
     if (threadIdx.x == 0) s_stop = stop_state(p);
     __syncthreads();
     const int32_t stop = s_stop;
@@ -1043,7 +1233,7 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
         __syncthreads();
         if (s_last && threadIdx.x == 0) {
             *p.ticket = 0u;
-            p.conv[1] = kStopped;
+            p.conv[2] = kStopped;
         }
     }
 }
@@ -1250,7 +1440,7 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
             if (stop == kStopPending) {
                 if (threadIdx.x == 0) {
                     *p.ticket = 0u;
-                    p.conv[1] = kStopped;
+                    p.conv[2] = kStopped;
                 }
             } else {
                 close_generation(p, t);
@@ -1301,7 +1491,7 @@ __global__ void __launch_bounds__(kThreads) batch_cip_kernel(const BatchArgs a)
             __syncthreads();
             if (s_last && threadIdx.x == 0) {
                 *p.ticket = 0u;
-                p.conv[1] = kStopped;
+                p.conv[2] = kStopped;
             }
         }
     }
@@ -1312,7 +1502,7 @@ __global__ void __launch_bounds__(kThreads) gather_stop_kernel(int32_t *const *c
                                                                int32_t *out)
 {
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
-        out[i] = conv[i][1];
+        out[i] = conv[i][2];
 }
 
 // Generation 0 state: every qubit at theta = pi/4 (n = K), no elite, no best record.
@@ -1335,12 +1525,13 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
     if (i0 == 0) {
         *p.gen = 0;
         *p.ticket = 0u;
-        *p.key = 0ull;
+        p.keys[0] = p.keys[1] = p.keys[2] = 0ull;
         *p.elite_idx = 0;
         *p.bar_gen = 0;
         *p.error = 0;
-        p.conv[0] = 0;
-        p.conv[1] = kRunning;
+        p.conv[0] = p.conv[1] = 0;
+        p.conv[2] = kRunning;
+        p.conv[3] = -1;
         p.best[0] = 0;
         p.best[1] = -1;
         p.best[2] = -1;
