@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="c5 arrivals per second (0: 0.8 x the measured batched capacity)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--state-i8", action="store_true",
+                    help="c1-c3: store the angle indices as bytes (QIEO_FLAG_STATE_I8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--phases", action="store_true",
@@ -79,12 +81,13 @@ def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
     return float(t[0])
 
 
-def workload_config(name: str) -> dict:
+def workload_config(name: str, state_i8: bool = False) -> dict:
     c = WL.WORKLOADS[name]
     return {
         "workload": "%s: 0/1 knapsack Ng=%d items (w uniform [1,10], v=w+5, W=floor(sum w/2)), "
-                    "Np=%d chromosomes, %d generations, dtheta=0.01pi, start pi/4, int16 angle "
-                    "state, Philox seed %d" % (name, c["ng"], c["np"], c["gens"], c["seed"]),
+                    "Np=%d chromosomes, %d generations, dtheta=0.01pi, start pi/4, %s angle "
+                    "state, Philox seed %d" % (name, c["ng"], c["np"], c["gens"],
+                                               "int8" if state_i8 else "int16", c["seed"]),
         "ng": c["ng"], "np": c["np"], "generations": c["gens"], "rotation_rule": "R1",
     }
 
@@ -316,10 +319,11 @@ def run_gpu(a):
     np_, ng, G = c["np"], c["ng"], c["gens"]
     genes_per_step = np_ * ng * G
     stream = torch.cuda.Stream()
+    flags = Q.QIEO_FLAG_STATE_I8 if a.state_i8 else 0
     inst = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
-                      stream=stream.cuda_stream)
+                      stream=stream.cuda_stream, flags=flags)
     shape = inst.shape()
-    state_bytes = np_ * ((ng + 7) // 8) * 16
+    state_bytes = np_ * ((ng + 7) // 8) * (8 if a.state_i8 else 16)
     flush = state_bytes < 2 * L2_BYTES
     flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda") if flush else None
 
@@ -370,11 +374,12 @@ def run_gpu(a):
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * LANES_PER_SM * max_mhz * 1e6 / 1e12
     hbm_peak = float(peaks["hbm_gbs"])
-    t_hbm = STATE_BYTES_PER_GENE * genes_per_launch / (hbm_peak * 1e9)
+    state_bpg = 2 if a.state_i8 else STATE_BYTES_PER_GENE   # byte state: 1 B read + 1 B written
+    t_hbm = state_bpg * genes_per_launch / (hbm_peak * 1e9)
     t_alu = ALU_OPS_PER_GENE * genes_per_launch / (alu_peak * 1e12)
     l2_resident = state_bytes < L2_BYTES
     if t_hbm >= t_alu:
-        achieved = STATE_BYTES_PER_GENE * genes_per_launch / launch_s / 1e9
+        achieved = state_bpg * genes_per_launch / launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src}
     else:
@@ -384,7 +389,7 @@ def run_gpu(a):
                 "peak_source": "derived: %d SMs x %d int32 lanes x %.0f MHz" % (
                     SM_COUNT, LANES_PER_SM, max_mhz)}
     roof["state_in_l2"] = l2_resident
-    roof["traffic"] = profile_traffic("generation_kernel", a.workload)
+    roof["traffic"] = None if a.state_i8 else profile_traffic("generation_kernel", a.workload)
     roof["kernel"] = "generation_kernel (one launch per generation)"
     roof["us_per_generation"] = launch_s * 1e6
 
@@ -396,7 +401,7 @@ def run_gpu(a):
             barrier()
             t0 = time.perf_counter()
             h = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
-                           stream=stream.cuda_stream)
+                           stream=stream.cuda_stream, flags=flags)
             h.run(G)
             bits, bf, bg, bc = h.best()
             h.close()
@@ -413,7 +418,7 @@ def run_gpu(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": dict(workload_config(a.workload),
+        "config": dict(workload_config(a.workload, a.state_i8),
                        l2="flushed between steps (512 MB write)" if flush
                        else "state larger than L2 (no flush)",
                        parallelism="one independent instance per GPU",

@@ -85,6 +85,13 @@ typedef struct {
                                          server only: not with elite_on_host,
                                          QIEO_FLAG_COOPERATIVE or QIEO_FLAG_UNFUSED */
 #define QIEO_CONVERGE_WINDOW    20
+#define QIEO_FLAG_STATE_I8      0x100 /* store each angle index in one byte instead of two
+                                         (k in [-K, K] fits when dtheta_den <= 120), halving
+                                         the state's memory traffic; identical results.
+                                         Needs items in [0, 255]; not with
+                                         QIEO_FLAG_REGISTER_PREFETCH, QIEO_FLAG_COOPERATIVE,
+                                         QIEO_FLAG_UNFUSED or QIEO_FLAG_FORCE_WIDE, and not in
+                                         batches */
 
 typedef struct {
     int32_t np;              /* chromosomes, >= 1 */

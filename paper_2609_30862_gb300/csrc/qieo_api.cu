@@ -106,6 +106,7 @@ struct qieo_instance {
 
     // problem bounds that decide the sum and elite-key modes
     bool narrow_items = false;     // 0 <= w, v <= 255
+    bool state8 = false;           // angle indices stored as bytes (QIEO_FLAG_STATE_I8)
     int64_t sum_w = 0, sum_v = 0, sum_absv = 0;
     bool key_ok = false;
 
@@ -178,9 +179,17 @@ struct PickRun {
     static type get() { return &qieo::run_kernel<N, R, T>; }
 };
 
+// The generation kernel of an instance (byte-state instances: narrow sums, ring form).
+PickGen<true, 0, true>::type gen_fn(const qieo_instance *q, bool ring)
+{
+    if (q->state8)
+        return q->rule ? &qieo::generation_kernel<true, 1, true, true> : &qieo::generation_kernel<true, 0, true, true>;
+    return kernel_of<PickGen>(q, ring);
+}
+
 const void *gen_kernel_of(const qieo_instance *q, bool ring)
 {
-    return reinterpret_cast<const void *>(kernel_of<PickGen>(q, ring));
+    return reinterpret_cast<const void *>(gen_fn(q, ring));
 }
 
 const void *run_kernel_of(const qieo_instance *q, bool ring)
@@ -202,6 +211,9 @@ qieo_status configure(qieo_instance *q)
                  q->sum_w < (1ll << 26) && q->sum_v < (1ll << 26) && ntile <= 4095) ? 1 : 0;
     const int64_t units = (int64_t)ntile * q->np;
     const size_t row_bytes = q->narrow ? 8 : 16;
+    if (q->state8 && !q->narrow)
+        return fail(QIEO_ERR_INVALID, "QIEO_FLAG_STATE_I8 needs the packed item sums: items in [0, 255], "
+                    "item sums below 2^26 and at most 4095 tiles per row");
 
     // The state streams through the per-thread cp.async ring unless register prefetch is
     // asked for.
@@ -281,7 +293,7 @@ cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de, int32_t
     p.g = deferred_g >= 0 ? deferred_g : 0;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(q, dim3(q->grid), q->smem, attr);
-    return cudaLaunchKernelEx(&cfg, kernel_of<PickGen>(q, q->gp.ring != 0), p);
+    return cudaLaunchKernelEx(&cfg, gen_fn(q, q->gp.ring != 0), p);
 }
 
 cudaError_t launch_run(const qieo_instance *q, int32_t G)
@@ -603,12 +615,13 @@ namespace {
 //  server arena with a fixed number of generations)
 constexpr int kParts = 18;
 
-size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size_t *off)
+size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size_t *off,
+                       bool state8 = false)
 {
     const size_t svec = (size_t)(ng + 7) / 8;
     const size_t xstride = align_up(svec, 16);
     const size_t ngp = svec * 8;
-    const size_t sizes[kParts] = {(size_t)np * svec * sizeof(uint4),
+    const size_t sizes[kParts] = {(size_t)np * svec * (state8 ? sizeof(uint2) : sizeof(uint4)),
                                   2 * (size_t)np * xstride,
                                   ngp * 6,
                                   ngp * 8,
@@ -660,6 +673,12 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     if (pr->capacity < 0) return fail(QIEO_ERR_INVALID, "capacity must be >= 0");
     if ((pa->flags & QIEO_FLAG_UNFUSED) && (pa->elite_on_host || (pa->flags & QIEO_FLAG_COOPERATIVE)))
         return fail(QIEO_ERR_INVALID, "QIEO_FLAG_UNFUSED excludes elite_on_host and QIEO_FLAG_COOPERATIVE");
+    if ((pa->flags & QIEO_FLAG_STATE_I8) &&
+        (pa->dtheta_den > 120 || (pa->flags & (QIEO_FLAG_REGISTER_PREFETCH | QIEO_FLAG_COOPERATIVE |
+                                               QIEO_FLAG_UNFUSED | QIEO_FLAG_FORCE_WIDE))))
+        return fail(QIEO_ERR_INVALID, "QIEO_FLAG_STATE_I8 needs dtheta_den <= 120 and excludes "
+                    "QIEO_FLAG_REGISTER_PREFETCH, QIEO_FLAG_COOPERATIVE, QIEO_FLAG_UNFUSED and "
+                    "QIEO_FLAG_FORCE_WIDE");
     if ((pa->flags & QIEO_FLAG_CONVERGE) &&
         (pa->elite_on_host || (pa->flags & (QIEO_FLAG_COOPERATIVE | QIEO_FLAG_UNFUSED))))
         return fail(QIEO_ERR_INVALID, "QIEO_FLAG_CONVERGE excludes elite_on_host, QIEO_FLAG_COOPERATIVE "
@@ -691,6 +710,7 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     q->rule = pa->rotate_rule;
     q->host_de = pa->elite_on_host;
     q->flags = pa->flags;
+    q->state8 = (pa->flags & QIEO_FLAG_STATE_I8) != 0;
     q->capacity = pr->capacity;
     q->lambda = pa->penalty_lambda;
     q->seed = pa->seed;
@@ -725,7 +745,7 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
 
     const size_t ngp = (size_t)q->svec * 8;
     size_t off[kParts];
-    const size_t total = instance_layout(q->ng, q->np, q->D, ext ? ext->hist_cap : 0, off);
+    const size_t total = instance_layout(q->ng, q->np, q->D, ext ? ext->hist_cap : 0, off, q->state8);
     if (ext) {
         if (!ext->block || ext->bytes < total) return bail(fail(QIEO_ERR_INVALID, "placement too small"));
         q->block = ext->block;
@@ -739,6 +759,7 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     char *b = (char *)q->block;
     qieo::GenParams &g = q->gp;
     g.state = (uint4 *)(b + off[0]);
+    g.state8 = q->state8 ? 1 : 0;
     g.xbits = (uint8_t *)(b + off[1]);
     q->items_narrow = (const uint4 *)(b + off[2]);
     g.w4 = (const int4 *)(b + off[3]);
@@ -869,7 +890,7 @@ qieo_status qieo_reset(qieo_instance *q)
     if (st != QIEO_OK) return st;
     st = set_device(q);
     if (st != QIEO_OK) return st;
-    const size_t words = (size_t)q->np * q->svec * 4;
+    const size_t words = (size_t)q->np * q->svec * (q->state8 ? 2 : 4);
     const size_t xbytes = 2 * (size_t)q->np * q->xstride;
     const int blocks = std::max(1, std::min(q->sm_count * 4, (int)((words + 255) / 256)));
     qieo::init_kernel<<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, words, xbytes,
@@ -963,7 +984,15 @@ qieo_status qieo_get_state(qieo_instance *q, int16_t *k_out, int32_t *t_out)
     if (st != QIEO_OK) return st;
     st = set_device(q);
     if (st != QIEO_OK) return st;
-    if (k_out) {
+    if (k_out && q->state8) {
+        std::vector<uint8_t> s((size_t)q->np * q->svec * 8);
+        st = fetch(q, s.data(), q->gp.state, s.size());
+        if (st != QIEO_OK) return st;
+        for (int32_t c = 0; c < q->np; ++c)
+            for (int32_t j = 0; j < q->ng; ++j)
+                k_out[(size_t)c * q->ng + j] =
+                    (int16_t)((int32_t)(s[(size_t)c * q->svec * 8 + j] >> 2) - q->K);
+    } else if (k_out) {
         std::vector<uint16_t> s((size_t)q->np * q->svec * 8);
         st = fetch(q, s.data(), q->gp.state, s.size() * 2);
         if (st != QIEO_OK) return st;
@@ -1313,6 +1342,8 @@ qieo_status qieo_create_batch(qieo_instance *const *instances, int32_t n, qieo_b
         if (!members[(size_t)i]) return fail(QIEO_ERR_INVALID, "instance %d is NULL", i);
         if (members[(size_t)i]->host_de)
             return fail(QIEO_ERR_INVALID, "instance %d uses elite_on_host; batches pick the elite on the device", i);
+        if (members[(size_t)i]->state8)
+            return fail(QIEO_ERR_INVALID, "instance %d stores its state as bytes; batches use 16-bit state", i);
         if (members[(size_t)i]->device != members[0]->device)
             return fail(QIEO_ERR_INVALID, "instance %d is on another device", i);
         for (int32_t j = 0; j < i; ++j)

@@ -32,6 +32,8 @@
 // reloads items only at a tile change and keeps the same share in every generation.
 #pragma once
 
+#include <type_traits>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -141,6 +143,7 @@ struct GenParams {
     int32_t g;                    // generation of this launch within its run (deferred
                                   // close: t = *gen + g; otherwise 0 and t = *gen)
     int32_t deferred;             // 1: deferred close (see generation_kernel)
+    int32_t state8;               // 1: angle indices stored as bytes (8 B per 8 genes)
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -676,6 +679,26 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t 
                  :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
 }
 
+// 8-byte global->shared copy (byte state); src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// Byte state <-> the 16-bit lanes the kernels compute on: 8 bytes (4n of genes 0..7) to
+// four words of two 16-bit halves, and back (every value is at most 8K <= 240).
+__device__ __forceinline__ uint4 unpack8(uint2 w)
+{
+    return make_uint4(__byte_perm(w.x, 0u, 0x4140), __byte_perm(w.x, 0u, 0x4342),
+                      __byte_perm(w.y, 0u, 0x4140), __byte_perm(w.y, 0u, 0x4342));
+}
+
+__device__ __forceinline__ uint2 pack8(uint4 v)
+{
+    return make_uint2(__byte_perm(v.x, v.y, 0x6420), __byte_perm(v.z, v.w, 0x6420));
+}
+
 __device__ __forceinline__ void cp_async_commit()
 {
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -687,8 +710,9 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-// One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation.
-template <bool kNarrow, int kRule, bool kCip, class Keys>
+// One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation. kS8:
+// the state is stored as bytes (copied 8 bytes per pass, widened to 16-bit lanes).
+template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false>
 __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &keys, const BlockShare &b,
                                              int tile, int ra, int seg_rows, int32_t t,
                                              const uint8_t *x_prev, uint8_t *x_cur,
@@ -703,7 +727,8 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     SegCtx g;
     seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
     const size_t row0 = (size_t)ra + b.r_sub;
-    uint4 *sptr = p.state + row0 * p.svec + g.vec;
+    using SV = typename std::conditional<kS8, uint2, uint4>::type;
+    SV *sptr = reinterpret_cast<SV *>(p.state) + row0 * p.svec + g.vec;
     const size_t sstep = (size_t)rpp * p.svec;
     uint8_t *xptr = x_cur + row0 * p.xstride + g.vec;
     const uint8_t *xoptr = x_prev + row0 * p.xstride + g.vec;
@@ -711,18 +736,22 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 
     // Incremental addressing (no multiplies in the pass loop): the copy cursor runs
     // kRingStages - 1 rows ahead of the compute cursor.
-    const uint4 *ld_ptr = sptr;                 // next row to copy
+    const SV *ld_ptr = sptr;                    // next row to copy
     int ld_rr = b.r_sub;                        // its row within the segment
     uint32_t ld_slot = 0;                       // its slot
-    uint4 *st_ptr = sptr;                       // row being computed
+    SV *st_ptr = sptr;                          // row being computed
     uint8_t *xst_ptr = xptr;
     const uint8_t *xo_ptr = xoptr;
     int rr = b.r_sub;
     uint32_t slot = 0;
     auto issue = [&]() {
         const bool v = g.active && ld_rr < seg_rows;
-        cp_async16(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
-                   v ? 16u : 0u);
+        if constexpr (kS8)
+            cp_async8(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
+                      v ? 8u : 0u);
+        else
+            cp_async16(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
+                       v ? 16u : 0u);
         cp_async_commit();
         ld_ptr += sstep;
         ld_rr += rpp;
@@ -744,7 +773,9 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         xb1 = load_xold(xo_ptr + 2 * xstep, rr + 2 * rpp);
         xo_ptr += xstep;
         cp_async_wait<kRingStages - 1>();
-        uint4 sv = slots[(size_t)slot * kThreads];
+        uint4 sv;
+        if constexpr (kS8) sv = unpack8(*reinterpret_cast<const uint2 *>(slots + (size_t)slot * kThreads));
+        else sv = slots[(size_t)slot * kThreads];
         slot = (slot + 1) & (kRingStages - 1);
 
         const bool ok = rr < seg_rows;
@@ -754,7 +785,10 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         sv = qubit_pass<kNarrow, kRule, kCip>(p, keys, g, sv, xo, ra + rr, t, thr_bytes, fixed,
                                               countdown, xbits, accn, acw, acv);
         if (g.active && ok) {
-            if (!fixed) *st_ptr = sv;   // a fixed pass leaves the state as it is
+            if (!fixed) {               // a fixed pass leaves the state as it is
+                if constexpr (kS8) *st_ptr = pack8(sv);
+                else *st_ptr = sv;
+            }
             *xst_ptr = (uint8_t)xbits;
         }
         add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
@@ -777,7 +811,7 @@ __device__ __forceinline__ void clear_row_sums(int seg_rows_max, uint32_t *s_acc
     __syncthreads();
 }
 
-template <bool kNarrow, int kRule, bool kCip>
+template <bool kNarrow, int kRule, bool kCip, bool kS8 = false>
 __device__ __forceinline__ void generation_body_ring(const GenParams &p, const BlockShare &b,
                                                      int32_t t, int32_t e_prev, uint4 *ring,
                                                      const uint32_t *s_thr, uint32_t *s_acc32,
@@ -795,13 +829,14 @@ __device__ __forceinline__ void generation_body_ring(const GenParams &p, const B
         const int ra = (int)(u0 - (int64_t)tile * p.np);
         const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
         u0 += seg_rows;
-        ring_segment<kNarrow, kRule, kCip>(p, ParamKeys{p}, b, tile, ra, seg_rows, t, x_prev, x_cur,
-                                           elite_row, thr_bytes, slots, s_acc32, s_acc64, countdown);
+        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8>(p, ParamKeys{p}, b, tile, ra, seg_rows, t, x_prev,
+                                                           x_cur, elite_row, thr_bytes, slots, s_acc32,
+                                                           s_acc64, countdown);
     }
 }
 
 // CIP with elite e of generation t over this block's share (the final rotation of a run).
-template <int kRule>
+template <int kRule, bool kS8 = false>
 __device__ __forceinline__ void final_cip_body(const GenParams &p, const BlockShare &b,
                                                int32_t t, int32_t e)
 {
@@ -825,15 +860,20 @@ __device__ __forceinline__ void final_cip_body(const GenParams &p, const BlockSh
                 const int r2 = rr + k * b.rows_per_pass;
                 if (r2 < seg_rows) {
                     const size_t c = (size_t)ra + r2;
-                    v[k] = p.state[c * p.svec + vec];
+                    if constexpr (kS8) v[k] = unpack8(reinterpret_cast<const uint2 *>(p.state)[c * p.svec + vec]);
+                    else v[k] = p.state[c * p.svec + vec];
                     m8[k] = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + vec]) : 0xffu;
                 }
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int r2 = rr + k * b.rows_per_pass;
-                if (r2 < seg_rows)
-                    p.state[((size_t)ra + r2) * p.svec + vec] = rotate_vec(v[k], e8, m8[k], k8);
+                if (r2 < seg_rows) {
+                    const size_t i = ((size_t)ra + r2) * p.svec + vec;
+                    const uint4 r = rotate_vec(v[k], e8, m8[k], k8);
+                    if constexpr (kS8) reinterpret_cast<uint2 *>(p.state)[i] = pack8(r);
+                    else p.state[i] = r;
+                }
             }
         }
     }
@@ -900,12 +940,12 @@ __device__ __forceinline__ SmemParts carve_smem(unsigned char *raw)
     return m;
 }
 
-template <bool kNarrow, int kRule, bool kCip, bool kRing>
+template <bool kNarrow, int kRule, bool kCip, bool kRing, bool kS8 = false>
 __device__ __forceinline__ void one_generation(const GenParams &p, const BlockShare &b, int32_t t,
                                                int32_t e_prev, SmemParts &m, const uint32_t *s_thr)
 {
-    if (kRing)
-        generation_body_ring<kNarrow, kRule, kCip>(p, b, t, e_prev, m.ring, s_thr, m.acc32, m.acc64);
+    if constexpr (kRing)
+        generation_body_ring<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32, m.acc64);
     else
         generation_body<kNarrow, kRule, kCip>(p, b, t, e_prev, s_thr, m.acc32, m.acc64);
 }
@@ -1014,7 +1054,7 @@ __device__ __forceinline__ int deferred_skip(const GenParams &p, int32_t t)
 // Otherwise (elite by a scan of fitness[] when the fitness does not fit the key, or the
 // host DetermineElite variant): the last block to finish closes the generation.
 // ---------------------------------------------------------------------------------------
-template <bool kNarrow, int kRule, bool kRing>
+template <bool kNarrow, int kRule, bool kRing, bool kS8 = false>
 __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) generation_kernel(const GenParams p)
 {
     __shared__ uint32_t s_thr[kMaxThr];
@@ -1060,11 +1100,11 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
             if (threadIdx.x == 0) *key_slot(p, t + 1) = 0ull;
         }
         if (stop == kStopPending) {
-            final_cip_body<kRule>(p, b, t - 1, e_prev);   // the CIP of the converged generation
+            final_cip_body<kRule, kS8>(p, b, t - 1, e_prev);   // the CIP of the converged generation
             return;
         }
-        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing>(p, b, t, e_prev, m, s_thr);
-        else one_generation<kNarrow, kRule, false, kRing>(p, b, t, e_prev, m, s_thr);
+        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing, kS8>(p, b, t, e_prev, m, s_thr);
+        else one_generation<kNarrow, kRule, false, kRing, kS8>(p, b, t, e_prev, m, s_thr);
         allow_dependent_launch();
         return;
     }
@@ -1078,11 +1118,11 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
     const int32_t e_prev = *p.elite_idx;
     if (stop == kStopPending) {
         // the generation before met the convergence test: its CIP alone, then stopped
-        final_cip_body<kRule>(p, b, t - 1, e_prev);
+        final_cip_body<kRule, kS8>(p, b, t - 1, e_prev);
     } else if (p.apply_cip) {
-        one_generation<kNarrow, kRule, true, kRing>(p, b, t, e_prev, m, s_thr);
+        one_generation<kNarrow, kRule, true, kRing, kS8>(p, b, t, e_prev, m, s_thr);
     } else {
-        one_generation<kNarrow, kRule, false, kRing>(p, b, t, e_prev, m, s_thr);
+        one_generation<kNarrow, kRule, false, kRing, kS8>(p, b, t, e_prev, m, s_thr);
     }
 
     // The next generation's blocks may start their prologue now.
@@ -1163,6 +1203,18 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
 }
 
 // CIP of the last generation of a run launched generation by generation.
+// CIP of the 8-gene vector i of the state in place (16-bit or byte storage).
+__device__ __forceinline__ void rotate_state(const GenParams &p, size_t i, uint32_t e8, uint32_t m8,
+                                             uint32_t k8)
+{
+    if (p.state8) {
+        uint2 *s8 = reinterpret_cast<uint2 *>(p.state) + i;
+        *s8 = pack8(rotate_vec(unpack8(*s8), e8, m8, k8));
+    } else {
+        p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+    }
+}
+
 template <int kRule>
 __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
 {
@@ -1204,7 +1256,7 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
             const size_t v = i - c * (size_t)p.svec;
             const uint32_t e8 = elite[v];
             const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
-            p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+            rotate_state(p, i, e8, m8, k8);
         }
         return;
     }
@@ -1224,7 +1276,7 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
         const size_t v = i - c * (size_t)p.svec;
         const uint32_t e8 = elite[v];
         const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
-        p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+        rotate_state(p, i, e8, m8, k8);
     }
     if (stop == kStopPending) {   // the run's last generation met the convergence test
         __threadfence();
@@ -1510,7 +1562,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
                                                         size_t xbytes, size_t acc_words)
 {
     grid_dependency_wait();
-    const uint32_t kk = (uint32_t)(4 * p.K) * 0x00010001u;
+    const uint32_t kk = (uint32_t)(4 * p.K) * (p.state8 ? 0x01010101u : 0x00010001u);
     uint32_t *s = reinterpret_cast<uint32_t *>(p.state);
     const size_t stride = (size_t)gridDim.x * kThreads;
     const size_t i0 = (size_t)blockIdx.x * kThreads + threadIdx.x;

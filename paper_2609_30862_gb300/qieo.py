@@ -33,6 +33,7 @@ QIEO_FLAG_REGISTER_PREFETCH = 0x20
 QIEO_FLAG_UNFUSED = 0x40
 QIEO_FLAG_CONVERGE = 0x80
 QIEO_CONVERGE_WINDOW = 20
+QIEO_FLAG_STATE_I8 = 0x100
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (

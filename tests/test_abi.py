@@ -68,6 +68,11 @@ def test_defaults_and_errors_without_gpu(lib):
         Q.qieo_create_instance([1, 2], [3, 4], 2,
                                _params(p, flags=Q.QIEO_FLAG_UNFUSED | Q.QIEO_FLAG_COOPERATIVE))
     assert e.value.status == Q.QIEO_ERR_INVALID
+    for bad in (dict(flags=Q.QIEO_FLAG_STATE_I8, dtheta_den=124),
+                dict(flags=Q.QIEO_FLAG_STATE_I8 | Q.QIEO_FLAG_REGISTER_PREFETCH)):
+        with pytest.raises(Q.QieoError) as e:
+            Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, **bad))
+        assert e.value.status == Q.QIEO_ERR_INVALID and "STATE_I8" in str(e.value)
     for bad in (dict(flags=Q.QIEO_FLAG_CONVERGE, elite_on_host=1),
                 dict(flags=Q.QIEO_FLAG_CONVERGE | Q.QIEO_FLAG_UNFUSED),
                 dict(flags=Q.QIEO_FLAG_CONVERGE | Q.QIEO_FLAG_COOPERATIVE)):

@@ -326,3 +326,33 @@ def test_convergence_flag_off_runs_every_generation():
         stopped, stable = I.convergence()
         ref = O.run(prob, 30, 10, seed=3, window=20)
         assert not stopped and stable == int(ref.conv[0])
+
+
+@pytest.mark.parametrize("rule,D,ng", [(0, 100, 1003), (1, 100, 777), (0, 120, 64), (0, 4, 33)])
+def test_byte_state_equals_oracle(rule, D, ng):
+    """QIEO_FLAG_STATE_I8 stores every angle index in one byte: the same trajectory as the
+    16-bit state (oracle), across split runs, ragged sizes and other rotation steps."""
+    prob = W.knapsack(ng, 40 + D)
+    compare(prob, 29, [7, 6, 7], seed=40, rule=rule, D=D, flags=Q.QIEO_FLAG_STATE_I8)
+
+
+def test_byte_state_with_convergence_and_saturation():
+    """Byte state through the saturated phase (fixed-allele passes) and the convergence stop."""
+    from oracle import oracle as O
+    prob, np_, seed = W.knapsack(200, 3), 30, 3
+    compare(prob, np_, [150, 60], seed=seed, flags=Q.QIEO_FLAG_STATE_I8)
+    ref = O.run(prob, np_, 400, seed=seed, window=20)
+    with Q.Instance(prob, np_, seed=seed, flags=Q.QIEO_FLAG_STATE_I8 | Q.QIEO_FLAG_CONVERGE) as I:
+        I.run(400)
+        k, t = I.state()
+        assert t == int(ref.t[0]) and np.array_equal(k, ref.k)
+        bits, bf, bg, bc = I.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in ref.best)
+
+
+def test_byte_state_needs_packed_item_sums():
+    w = np.full(40, 300, dtype=np.int32)
+    prob = W.custom_problem(w, w.copy(), 3000)
+    with pytest.raises(Q.QieoError) as e:
+        Q.Instance(prob, 8, flags=Q.QIEO_FLAG_STATE_I8)
+    assert e.value.status == Q.QIEO_ERR_INVALID and "STATE_I8" in str(e.value)
