@@ -1203,15 +1203,27 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
 }
 
 // CIP of the last generation of a run launched generation by generation.
-// CIP of the 8-gene vector i of the state in place (16-bit or byte storage).
-__device__ __forceinline__ void rotate_state(const GenParams &p, size_t i, uint32_t e8, uint32_t m8,
-                                             uint32_t k8)
+// CIP toward elite e of generation t over the whole state (grid-stride), 16-bit or byte
+// storage.
+template <int kRule, bool kS8>
+__device__ __forceinline__ void rotate_all(const GenParams &p, int32_t t, int32_t e)
 {
-    if (p.state8) {
-        uint2 *s8 = reinterpret_cast<uint2 *>(p.state) + i;
-        *s8 = pack8(rotate_vec(unpack8(*s8), e8, m8, k8));
-    } else {
-        p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+    const uint8_t *xl = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint8_t *elite = xl + (size_t)e * p.xstride;
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    const size_t total = (size_t)p.np * p.svec;
+    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * kThreads) {
+        const size_t c = i / (size_t)p.svec;
+        const size_t v = i - c * (size_t)p.svec;
+        const uint32_t e8 = elite[v];
+        const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
+        if constexpr (kS8) {
+            uint2 *s8 = reinterpret_cast<uint2 *>(p.state) + i;
+            *s8 = pack8(rotate_vec(unpack8(*s8), e8, m8, k8));
+        } else {
+            p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
+        }
     }
 }
 
@@ -1246,18 +1258,8 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
                 st_release(p.conv + 2, kStopped);
             }
         }
-        const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
-        const uint8_t *elite = xl + (size_t)e * p.xstride;
-        const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
-        const size_t total = (size_t)p.np * p.svec;
-        for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
-             i += (size_t)gridDim.x * kThreads) {
-            const size_t c = i / (size_t)p.svec;
-            const size_t v = i - c * (size_t)p.svec;
-            const uint32_t e8 = elite[v];
-            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
-            rotate_state(p, i, e8, m8, k8);
-        }
+        if (p.state8) rotate_all<kRule, true>(p, t_last, e);
+        else rotate_all<kRule, false>(p, t_last, e);
         return;
     }
     if (threadIdx.x == 0) s_stop = stop_state(p);
@@ -1266,18 +1268,8 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
     if (stop == kStopped) return;
     const int32_t t_last = *p.gen - 1;
     const int32_t e = *p.elite_idx;
-    const uint8_t *xl = p.xbits + (size_t)(t_last & 1) * p.xplane;
-    const uint8_t *elite = xl + (size_t)e * p.xstride;
-    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
-    const size_t total = (size_t)p.np * p.svec;
-    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * kThreads) {
-        const size_t c = i / (size_t)p.svec;
-        const size_t v = i - c * (size_t)p.svec;
-        const uint32_t e8 = elite[v];
-        const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[c * p.xstride + v]) : 0xffu;
-        rotate_state(p, i, e8, m8, k8);
-    }
+    if (p.state8) rotate_all<kRule, true>(p, t_last, e);
+    else rotate_all<kRule, false>(p, t_last, e);
     if (stop == kStopPending) {   // the run's last generation met the convergence test
         __threadfence();
         __syncthreads();
