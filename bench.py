@@ -390,7 +390,8 @@ def run_gpu(a):
                     SM_COUNT, LANES_PER_SM, max_mhz)}
     roof["state_in_l2"] = l2_resident
     roof["traffic"] = None if a.state_i8 else profile_traffic("generation_kernel", a.workload)
-    roof["kernel"] = "generation_kernel (one launch per generation)"
+    roof["kernel"] = ("run_kernel (one cooperative launch per run)" if shape.persistent
+                      else "generation_kernel (one launch per generation)")
     roof["us_per_generation"] = launch_s * 1e6
 
     # end to end through the C ABI with host buffers: create (uploads the items), run,
@@ -423,15 +424,19 @@ def run_gpu(a):
                        else "state larger than L2 (no flush)",
                        parallelism="one independent instance per GPU",
                        launch_shape="%d lanes x %d warps per row tile, %d tiles per row, "
-                                    "%d persistent blocks, <= %d tile-rows per block" % (
+                                    "%d persistent blocks, <= %d tile-rows per block, %s" % (
                            shape.lanes_per_row, shape.warps_per_row, shape.tiles,
-                           shape.grid_ctas, shape.rows_per_cta)),
+                           shape.grid_ctas, shape.rows_per_cta,
+                           "one cooperative launch per run" if shape.persistent
+                           else "one launch per generation")),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "what": "qieo_create_instance from host arrays + qieo_run + qieo_get_best + "
                         "qieo_destroy_instance per step"},
-        "gpu_launches": a.steps * (G + 2),
+        # per step: the reset's init launch, then either one cooperative launch + the
+        # end-of-run launch, or G generation launches + the final CIP + the end-of-run launch
+        "gpu_launches": a.steps * (1 + (2 if shape.persistent else G + 2)),
         "clocks": clocks,
         "wall_s_timed": wall,
     }

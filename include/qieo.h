@@ -69,7 +69,9 @@ typedef struct {
 #define QIEO_FLAG_TIME_KERNELS  0x8   /* time the generation kernels with CUDA events */
 #define QIEO_FLAG_COOPERATIVE   0x10  /* one cooperative launch per run (a bounded grid
                                          barrier between generations) instead of one launch
-                                         per generation */
+                                         per generation. The library also picks it by itself
+                                         for instances of at most 2^22 genes whose fitness
+                                         fits the packed elite key (there it is faster) */
 #define QIEO_FLAG_REGISTER_PREFETCH 0x20 /* stream the state with register prefetch instead
                                             of asynchronous copies into shared memory */
 #define QIEO_FLAG_UNFUSED       0x40  /* run each generation as four launches, one per step
@@ -85,6 +87,8 @@ typedef struct {
                                          server only: not with elite_on_host,
                                          QIEO_FLAG_COOPERATIVE or QIEO_FLAG_UNFUSED */
 #define QIEO_CONVERGE_WINDOW    20
+#define QIEO_FLAG_PER_GENERATION 0x200 /* always one launch per generation (never the
+                                          cooperative form picked for small instances) */
 #define QIEO_FLAG_STATE_I8      0x100 /* store each angle index in one byte instead of two
                                          (k in [-K, K] fits when dtheta_den <= 120), halving
                                          the state's memory traffic; identical results.
@@ -176,6 +180,9 @@ typedef struct {
     int32_t narrow;          /* out: 1 when 16-bit packed item sums are in use */
     int32_t tiles;           /* out: gene tiles per row */
     int32_t rows_per_cta;    /* out: most tile-rows one block sums in shared memory at once */
+    int32_t persistent;      /* out: 1 when a run is one cooperative launch (see
+                                QIEO_FLAG_COOPERATIVE), 0 when it is one launch per
+                                generation */
 } qieo_launch_shape;
 
 qieo_status qieo_get_launch_shape(qieo_instance *inst, qieo_launch_shape *shape);

@@ -296,8 +296,14 @@ cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de, int32_t
     return cudaLaunchKernelEx(&cfg, gen_fn(q, q->gp.ring != 0), p);
 }
 
+// One cooperative launch for a run of G generations. With the packed elite key the run uses
+// the deferred close (a plain grid barrier between generations) and a one-thread launch
+// then advances the generation counter; otherwise the last block closes each generation.
 cudaError_t launch_run(const qieo_instance *q, int32_t G)
 {
+    qieo::GenParams p = q->gp;
+    p.deferred = q->key_ok ? 1 : 0;
+    p.g = 0;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(q->grid);
@@ -308,7 +314,12 @@ cudaError_t launch_run(const qieo_instance *q, int32_t G)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel_of<PickRun>(q, q->gp.ring != 0), q->gp, G);
+    cudaError_t ce = cudaLaunchKernelEx(&cfg, kernel_of<PickRun>(q, q->gp.ring != 0), p, G);
+    if (ce != cudaSuccess || !p.deferred) return ce;
+    cudaLaunchAttribute attr1[1];
+    cudaLaunchConfig_t one = launch_config(q, dim3(1), 0, attr1);
+    one.blockDim = dim3(32);
+    return cudaLaunchKernelEx(&one, qieo::end_run_kernel, p, G);
 }
 
 cudaError_t launch_final_cip(const qieo_instance *q, int32_t deferred_G = 0)
@@ -409,11 +420,28 @@ qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
     return QIEO_OK;
 }
 
+// A run as one cooperative launch: when asked for, or by default for small instances
+// (at most 2^22 genes) with the packed elite key, where the grid barrier costs less than a
+// launch per generation (measured: 64 x 100 genes 2.86 vs 3.44 us per generation; at
+// 1,024 x 10,000 the two are within 1 %, at 4,096 x 100,000 the cooperative form is 2 %
+// slower). Not with the convergence test or byte state.
+bool use_cooperative(const qieo_instance *q)
+{
+    if (!q->coop || q->host_de || (q->flags & (QIEO_FLAG_UNFUSED | QIEO_FLAG_PER_GENERATION)))
+        return false;
+    if (q->flags & QIEO_FLAG_COOPERATIVE) return true;
+    return q->key_ok && !(q->flags & QIEO_FLAG_CONVERGE) && !q->state8 &&
+           (int64_t)q->np * q->svec * 8 <= ((int64_t)1 << 22);
+}
+
 qieo_status run_cooperative(qieo_instance *q, int32_t G)
 {
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     if (timing) CUDA_TRY(cudaEventRecord(q->ev0, q->stream));
-    CUDA_TRY(launch_run(q, G));
+    // the barrier counts G x grid arrivals in 32 bits: split longer runs (run(a) + run(b)
+    // equals run(a + b))
+    const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(G, ((int64_t)1 << 30) / std::max(1, q->grid)));
+    for (int32_t done = 0; done < G; done += chunk) CUDA_TRY(launch_run(q, std::min(chunk, G - done)));
     if (timing) {
         CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
         qieo_status st = wait_stream(q->stream);
@@ -428,7 +456,7 @@ qieo_status run_cooperative(qieo_instance *q, int32_t G)
 
 qieo_status run_device(qieo_instance *q, int32_t G)
 {
-    if (q->coop && (q->flags & QIEO_FLAG_COOPERATIVE)) return run_cooperative(q, G);
+    if (use_cooperative(q)) return run_cooperative(q, G);
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
     if ((q->flags & QIEO_FLAG_NO_GRAPH) || (first_time && !q->graphs.count(G))) {
@@ -1083,6 +1111,7 @@ qieo_status qieo_get_launch_shape(qieo_instance *q, qieo_launch_shape *s)
     s->narrow = q->narrow;
     s->tiles = q->gp.ntile;
     s->rows_per_cta = q->gp.seg_rows_max;
+    s->persistent = use_cooperative(q) ? 1 : 0;
     return QIEO_OK;
 }
 

@@ -919,6 +919,37 @@ __device__ __forceinline__ bool generation_barrier(const GenParams &p, int32_t t
     return s_flag != 0;
 }
 
+// Plain grid barrier of a cooperative deferred-close run: each block's arrival is one
+// release add to p.ticket (after a block barrier, so the add publishes every thread's
+// writes); a block waits, bounded, until `target` arrivals are visible.
+__device__ __forceinline__ void grid_arrive(const GenParams &p)
+{
+    __syncthreads();
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(p.ticket) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(const GenParams &p, unsigned int target)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const uint64_t deadline = global_ns() + p.wait_ns;
+        int ok = 0;
+        for (uint32_t it = 0; it < (1u << 30); ++it) {
+            if (ld_acquire(reinterpret_cast<const int32_t *>(p.ticket)) >= (int32_t)target) {
+                ok = 1;
+                break;
+            }
+            if (ld_acquire(p.error) != 0 || global_ns() > deadline) break;
+            __nanosleep(32);
+        }
+        if (!ok) atomicOr(p.error, kErrBarrierTimeout);
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // Dynamic shared memory: [per-thread copy ring (kRingStages x kThreads x 16 B)] when the
 // asynchronous-copy form is used, then the per-row sums of a segment.
 constexpr size_t kRingBytes = (size_t)kRingStages * kThreads * 16;
@@ -948,32 +979,6 @@ __device__ __forceinline__ void one_generation(const GenParams &p, const BlockSh
         generation_body_ring<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32, m.acc64);
     else
         generation_body<kNarrow, kRule, kCip>(p, b, t, e_prev, s_thr, m.acc32, m.acc64);
-}
-
-// ---------------------------------------------------------------------------------------
-// run_kernel: generations t0 .. t0+G-1 and the final CIP in one cooperative launch. The
-// first generation applies no CIP (a run starts from a rotated state or from t = 0).
-// ---------------------------------------------------------------------------------------
-template <bool kNarrow, int kRule, bool kRing>
-__global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_kernel(const GenParams p, int32_t G)
-{
-    __shared__ uint32_t s_thr[kMaxThr];
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    SmemParts m = carve_smem<kRing>(smem_raw);
-    load_thresholds(p, s_thr);
-    grid_dependency_wait();
-    __syncthreads();
-    const BlockShare b = block_share(p);
-    const int32_t t0 = *p.gen;
-    int32_t e = 0;
-    for (int32_t g = 0; g < G; ++g) {
-        const int32_t t = t0 + g;
-        if (g == 0) one_generation<kNarrow, kRule, false, kRing>(p, b, t, 0, m, s_thr);
-        else one_generation<kNarrow, kRule, true, kRing>(p, b, t, e, m, s_thr);
-        if (!generation_barrier(p, t)) return;
-        e = __ldcg(p.elite_idx);
-    }
-    final_cip_body<kRule>(p, b, t0 + G - 1, e);
 }
 
 // Records of generation t with elite e of fitness f: the history, the elite index, the
@@ -1036,6 +1041,65 @@ __device__ __forceinline__ int deferred_skip(const GenParams &p, int32_t t)
     const int32_t state = ld_acquire(p.conv + 2);
     if (state != kStopped) return 0;
     return (p.g == 0 || *(volatile const int32_t *)(p.conv + 3) <= t - 2) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// run_kernel: generations t0 .. t0+G-1 and the final CIP in one cooperative launch. The
+// first generation applies no CIP (a run starts from a rotated state or from t = 0).
+// ---------------------------------------------------------------------------------------
+template <bool kNarrow, int kRule, bool kRing>
+__global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_kernel(const GenParams p, int32_t G)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemParts m = carve_smem<kRing>(smem_raw);
+    load_thresholds(p, s_thr);
+    grid_dependency_wait();
+    __syncthreads();
+    const BlockShare b = block_share(p);
+    const int32_t t0 = *p.gen;
+    int32_t e = 0;
+    if (p.deferred) {
+        // Deferred close: a plain grid barrier between generations (arrivals counted in
+        // p.ticket over the whole run, cleared by the end-of-run launch); after it every
+        // block reads the elite of the generation before from its key slot, and block 0
+        // writes that generation's records.
+        __shared__ int s_e;
+        __shared__ long long s_f;
+        for (int32_t g = 0; g <= G; ++g) {
+            const int32_t t = t0 + g;
+            int64_t f = 0;
+            if (g > 0) {
+                if (!grid_wait(p, (unsigned int)g * gridDim.x)) return;
+                if (threadIdx.x == 0) {
+                    int32_t ee;
+                    int64_t ff;
+                    elite_from_key(p, t - 1, ee, ff);
+                    s_e = ee;
+                    s_f = ff;
+                }
+                __syncthreads();
+                e = s_e;
+                f = s_f;
+                if (blockIdx.x == 0) record_generation(p, t - 1, e, f);
+            }
+            if (g == G) break;
+            if (blockIdx.x == 0 && threadIdx.x == 0) *key_slot(p, t + 1) = 0ull;
+            if (g == 0) one_generation<kNarrow, kRule, false, kRing>(p, b, t, 0, m, s_thr);
+            else one_generation<kNarrow, kRule, true, kRing>(p, b, t, e, m, s_thr);
+            grid_arrive(p);
+        }
+        final_cip_body<kRule>(p, b, t0 + G - 1, e);
+        return;
+    }
+    for (int32_t g = 0; g < G; ++g) {
+        const int32_t t = t0 + g;
+        if (g == 0) one_generation<kNarrow, kRule, false, kRing>(p, b, t, 0, m, s_thr);
+        else one_generation<kNarrow, kRule, true, kRing>(p, b, t, e, m, s_thr);
+        if (!generation_barrier(p, t)) return;
+        e = __ldcg(p.elite_idx);
+    }
+    final_cip_body<kRule>(p, b, t0 + G - 1, e);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1165,6 +1229,7 @@ __global__ void end_run_kernel(const GenParams p, int32_t G)
     if (p.converge && p.conv[2] == kStopped) next = min(next, p.conv[3] + 1);
     *p.gen = next;
     *p.bar_gen = next;
+    *p.ticket = 0u;   // the arrival counter of a cooperative run
     p.keys[0] = p.keys[1] = p.keys[2] = 0ull;
 }
 

@@ -34,6 +34,7 @@ QIEO_FLAG_UNFUSED = 0x40
 QIEO_FLAG_CONVERGE = 0x80
 QIEO_CONVERGE_WINDOW = 20
 QIEO_FLAG_STATE_I8 = 0x100
+QIEO_FLAG_PER_GENERATION = 0x200
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
@@ -77,7 +78,7 @@ class qieo_params(C.Structure):
 class qieo_launch_shape(C.Structure):
     _fields_ = [("lanes_per_row", C.c_int32), ("warps_per_row", C.c_int32),
                 ("grid_ctas", C.c_int32), ("narrow", C.c_int32), ("tiles", C.c_int32),
-                ("rows_per_cta", C.c_int32)]
+                ("rows_per_cta", C.c_int32), ("persistent", C.c_int32)]
 
 
 class qieo_server_config(C.Structure):
@@ -249,7 +250,7 @@ def qieo_get_launch_shape(h) -> qieo_launch_shape:
 
 
 def qieo_set_launch_shape(h, lanes_per_row: int, warps_per_row: int, grid_ctas: int = 0) -> None:
-    s = qieo_launch_shape(int(lanes_per_row), int(warps_per_row), int(grid_ctas), 0, 0, 0)
+    s = qieo_launch_shape(int(lanes_per_row), int(warps_per_row), int(grid_ctas), 0, 0, 0, 0)
     _check(load().qieo_set_launch_shape(h, C.byref(s)))
 
 

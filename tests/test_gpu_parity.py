@@ -65,11 +65,14 @@ def test_device_philox_matches_oracle():
         assert np.array_equal(got, O.philox4x32_10(row[:4], row[4:]))
 
 
-def test_c1_full_run():
-    """Ng = 100, Np = 64, 500 generations, Philox seed 1: the small named workload."""
+@pytest.mark.parametrize("flags", [0, Q.QIEO_FLAG_PER_GENERATION])
+def test_c1_full_run(flags):
+    """Ng = 100, Np = 64, 500 generations, Philox seed 1: the small named workload, as one
+    cooperative launch (the default at this size) and as one launch per generation."""
     c = W.WORKLOADS["c1"]
-    compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
-            inst=c["inst"])
+    shape = compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
+                    inst=c["inst"], flags=flags)
+    assert shape.persistent == (0 if flags else 1)
 
 
 def test_c1_rule_r2():
@@ -79,7 +82,11 @@ def test_c1_rule_r2():
 
 @pytest.mark.parametrize("flags", [Q.QIEO_FLAG_NO_GRAPH, Q.QIEO_FLAG_FORCE_WIDE,
                                    Q.QIEO_FLAG_SYNC_RUN | Q.QIEO_FLAG_TIME_KERNELS,
-                                   Q.QIEO_FLAG_COOPERATIVE | Q.QIEO_FLAG_FORCE_WIDE])
+                                   Q.QIEO_FLAG_COOPERATIVE | Q.QIEO_FLAG_FORCE_WIDE,
+                                   Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_NO_GRAPH,
+                                   Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_FORCE_WIDE,
+                                   Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_SYNC_RUN |
+                                   Q.QIEO_FLAG_TIME_KERNELS])
 def test_flags_do_not_change_results(flags):
     compare(W.knapsack(700, 5), 48, [60], seed=5, rule=0, flags=flags)
 
@@ -99,20 +106,27 @@ def test_host_determine_elite_variant(rule):
     compare(W.knapsack(500, 2), 40, [25, 15], seed=2, rule=rule, host=1)
 
 
-def test_split_runs():
-    compare(W.knapsack(333, 8), 37, [1, 10, 29, 7], seed=8, rule=1)
+@pytest.mark.parametrize("flags", [0, Q.QIEO_FLAG_PER_GENERATION])
+def test_split_runs(flags):
+    compare(W.knapsack(333, 8), 37, [1, 10, 29, 7], seed=8, rule=1, flags=flags)
 
 
 @pytest.mark.parametrize("rule", [0, 1])
 def test_repeated_run_length_uses_graph(rule):
-    """The second and later runs of the same length replay a captured CUDA graph."""
-    compare(W.knapsack(1200, 6), 50, [6, 6, 6, 6, 3, 6], seed=6, rule=rule)
+    """The second and later runs of the same length replay a captured CUDA graph (one launch
+    per generation)."""
+    compare(W.knapsack(1200, 6), 50, [6, 6, 6, 6, 3, 6], seed=6, rule=rule,
+            flags=Q.QIEO_FLAG_PER_GENERATION)
 
 
 @pytest.mark.parametrize("ng", [1, 7, 8, 9, 31, 33, 127, 255, 257, 2048, 2055, 4099])
 @pytest.mark.parametrize("np_", [1, 3, 19])
 def test_ragged_sizes(ng, np_):
+    """Ragged gene and chromosome counts, through the default (cooperative at these sizes)
+    and the one-launch-per-generation forms."""
     compare(W.knapsack(ng, ng + np_), np_, [12], seed=ng, inst=np_, rule=(ng + np_) % 2)
+    compare(W.knapsack(ng, ng + np_), np_, [5, 7], seed=ng, inst=np_, rule=(ng + np_) % 2,
+            flags=Q.QIEO_FLAG_PER_GENERATION)
 
 
 @pytest.mark.parametrize("shape", [(32, 8, 0), (32, 8, 1), (32, 8, 7), (32, 4, 3), (32, 2, 50),
