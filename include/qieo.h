@@ -229,6 +229,11 @@ qieo_status qieo_batch_run(qieo_batch *batch, int32_t generations);
 /* Frees the batch (not its members). NULL is accepted. */
 qieo_status qieo_destroy_batch(qieo_batch *batch);
 
+/* One call: qieo_create_batch, qieo_batch_run(generations), qieo_destroy_batch. Returns
+ * when the generations have run. For repeated runs of the same members keep a batch (its
+ * work list and graphs are built once). */
+qieo_status qieo_run_batch(qieo_instance *const *instances, int32_t n, int32_t generations);
+
 /* Picks the launch shape (tile of lanes x warps vectors) of an instance at generation 0 by
  * timing `trial_generations` generations of each candidate shape, keeps the fastest, and
  * records it in a process-wide table keyed by (ng, np, D, rule, sum form) so that

@@ -45,7 +45,7 @@ EXPORTS = (
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
     "qieo_get_phase_times", "qieo_get_convergence", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
-    "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
+    "qieo_run_batch", "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
     "qieo_server_get_stats", "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
 )
 
@@ -140,6 +140,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_create_batch": ([P, i32, P], C.c_int),
         "qieo_batch_run": ([P, i32], C.c_int),
         "qieo_destroy_batch": ([P], C.c_int),
+        "qieo_run_batch": ([P, i32, i32], C.c_int),
         "qieo_autotune": ([P, i32, P], C.c_int),
         "qieo_server_create": ([P, P], C.c_int),
         "qieo_server_submit": ([P, P, P, i32, P], C.c_int),
@@ -305,6 +306,13 @@ def qieo_batch_run(b, generations: int) -> None:
 
 def qieo_destroy_batch(b) -> None:
     _check(load().qieo_destroy_batch(b))
+
+
+def qieo_run_batch(instances, generations: int) -> None:
+    """One call: a temporary batch over the Instance objects, `generations` generations."""
+    hs = [i.h for i in instances]
+    arr = (C.c_void_p * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    _check(load().qieo_run_batch(arr, len(hs), int(generations)))
 
 
 def qieo_autotune(h, trial_generations: int) -> qieo_launch_shape:

@@ -146,3 +146,13 @@ def test_batch_with_converging_members():
         inst.close()
     check_against_oracle(plain, plain_prob, 24, total, 77, 0)
     plain.close()
+
+
+def test_one_call_batched_run():
+    """qieo_run_batch equals a kept batch (and each member's oracle run)."""
+    made = [make(s, i) for i, s in enumerate(SPECS[:5])]
+    Q.qieo_run_batch([m[1] for m in made], 9)
+    Q.qieo_run_batch([m[1] for m in made], 4)
+    for i, (s, (prob, inst)) in enumerate(zip(SPECS[:5], made)):
+        check_against_oracle(inst, prob, s[1], 13, i + 1, i, s[3], s[4], s[2])
+        inst.close()
