@@ -28,6 +28,7 @@
 #ifndef QIEO_H
 #define QIEO_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -200,6 +201,19 @@ qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launc
  * the launch that records the elite, measured after the generation kernel finished).
  * qieo_reset clears neither. */
 qieo_status qieo_get_phase_times(qieo_instance *inst, double ms[4], int64_t *generations);
+
+/* Checkpoint / resume (the paper has none). A checkpoint holds everything a later run of
+ * the instance reads: the angle indices, the generation counter, the best-so-far record
+ * and row, the elite history and the convergence words. Loading it into an instance
+ * created with the same problem and params (ng, np, D, rule, seed, instance_id, capacity,
+ * lambda, byte state or not) makes every later run bit-identical to the uninterrupted
+ * instance's, because all draws are keyed by the absolute generation. The buffer is host
+ * memory owned by the caller; qieo_checkpoint_size gives its size for the current
+ * generation. QIEO_ERR_INVALID for a short buffer, another instance's checkpoint or a
+ * corrupt header. Loading resets the instance first. */
+qieo_status qieo_checkpoint_size(qieo_instance *inst, size_t *bytes);
+qieo_status qieo_checkpoint_save(qieo_instance *inst, void *buffer, size_t bytes);
+qieo_status qieo_checkpoint_load(qieo_instance *inst, const void *buffer, size_t bytes);
 
 /* Convergence test of an instance created with QIEO_FLAG_CONVERGE: *stopped = 1 once it
  * stopped (no later generation runs; qieo_get_state's t is one past the generation that

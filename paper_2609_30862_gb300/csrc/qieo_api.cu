@@ -1144,6 +1144,146 @@ qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches
     return QIEO_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Checkpoint / resume: everything a later run reads, so that load + run(b) equals the
+// uninterrupted run bit for bit (the draws are keyed by the absolute generation).
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct CheckpointHeader {
+    char magic[8];
+    int32_t ng, np, D, rule;
+    uint32_t seed, inst;
+    int32_t state8, t;
+    int64_t capacity, lambda;
+    int32_t conv[4];
+    int64_t best[3];
+    int32_t elite_idx, xstride;
+    uint64_t state_bytes;
+};
+
+const char kCheckpointMagic[8] = {'Q', 'I', 'E', 'O', 'C', 'K', 'P', '1'};
+
+size_t state_bytes_of(const qieo_instance *q)
+{
+    return (size_t)q->np * q->svec * (q->state8 ? 8 : 16);
+}
+
+size_t checkpoint_bytes(const qieo_instance *q, int32_t t)
+{
+    return sizeof(CheckpointHeader) + (size_t)q->xstride + (size_t)t * (sizeof(int32_t) + sizeof(int64_t)) +
+           state_bytes_of(q);
+}
+
+qieo_status upload(qieo_instance *q, void *dst, const void *src, size_t bytes)
+{
+    if (bytes == 0) return QIEO_OK;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, q->stream));
+    return wait_stream(q->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+qieo_status qieo_checkpoint_size(qieo_instance *q, size_t *bytes)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!bytes) return fail(QIEO_ERR_INVALID, "bytes is NULL");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    int32_t t = 0;
+    st = fetch(q, &t, q->gp.gen, sizeof t);
+    if (st != QIEO_OK) return st;
+    *bytes = checkpoint_bytes(q, t);
+    return QIEO_OK;
+}
+
+qieo_status qieo_checkpoint_save(qieo_instance *q, void *buffer, size_t bytes)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!buffer) return fail(QIEO_ERR_INVALID, "buffer is NULL");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    CheckpointHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kCheckpointMagic, sizeof h.magic);
+    h.ng = q->ng;
+    h.np = q->np;
+    h.D = q->D;
+    h.rule = q->rule;
+    h.seed = q->seed;
+    h.inst = q->inst_id;
+    h.state8 = q->state8 ? 1 : 0;
+    h.capacity = q->capacity;
+    h.lambda = q->lambda;
+    h.xstride = q->xstride;
+    h.state_bytes = state_bytes_of(q);
+    st = fetch(q, &h.t, q->gp.gen, sizeof h.t);
+    if (st == QIEO_OK) st = fetch(q, h.conv, q->gp.conv, sizeof h.conv);
+    if (st == QIEO_OK) st = fetch(q, h.best, q->gp.best, sizeof h.best);
+    if (st == QIEO_OK) st = fetch(q, &h.elite_idx, q->gp.elite_idx, sizeof h.elite_idx);
+    if (st != QIEO_OK) return st;
+    if (bytes < checkpoint_bytes(q, h.t))
+        return fail(QIEO_ERR_INVALID, "buffer of %zu bytes; the checkpoint needs %zu", bytes,
+                    checkpoint_bytes(q, h.t));
+    char *p = (char *)buffer;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    st = fetch(q, p, q->gp.best_row, (size_t)q->xstride);
+    p += q->xstride;
+    if (st == QIEO_OK && h.t > 0) st = fetch(q, p, q->hist_e, (size_t)h.t * sizeof(int32_t));
+    p += (size_t)h.t * sizeof(int32_t);
+    if (st == QIEO_OK && h.t > 0) st = fetch(q, p, q->hist_f, (size_t)h.t * sizeof(int64_t));
+    p += (size_t)h.t * sizeof(int64_t);
+    if (st == QIEO_OK) st = fetch(q, p, q->gp.state, h.state_bytes);
+    return st;
+}
+
+qieo_status qieo_checkpoint_load(qieo_instance *q, const void *buffer, size_t bytes)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!buffer || bytes < sizeof(CheckpointHeader)) return fail(QIEO_ERR_INVALID, "buffer too small");
+    CheckpointHeader h;
+    std::memcpy(&h, buffer, sizeof h);
+    if (std::memcmp(h.magic, kCheckpointMagic, sizeof h.magic) != 0)
+        return fail(QIEO_ERR_INVALID, "not a QIEO checkpoint");
+    if (h.ng != q->ng || h.np != q->np || h.D != q->D || h.rule != q->rule || h.seed != q->seed ||
+        h.inst != q->inst_id || h.state8 != (q->state8 ? 1 : 0) || h.capacity != q->capacity ||
+        h.lambda != q->lambda || h.xstride != q->xstride || h.state_bytes != state_bytes_of(q))
+        return fail(QIEO_ERR_INVALID, "the checkpoint belongs to another problem or other params");
+    if (h.t < 0 || bytes < checkpoint_bytes(q, h.t)) return fail(QIEO_ERR_INVALID, "truncated checkpoint");
+    st = qieo_reset(q);
+    if (st == QIEO_OK) st = wait_checked(q);
+    if (st == QIEO_OK) st = ensure_history(q, std::max(h.t, 1));
+    if (st != QIEO_OK) return st;
+    const char *p = (const char *)buffer + sizeof h;
+    st = upload(q, q->gp.best_row, p, (size_t)q->xstride);
+    p += q->xstride;
+    if (st == QIEO_OK) st = upload(q, q->hist_e, p, (size_t)h.t * sizeof(int32_t));
+    p += (size_t)h.t * sizeof(int32_t);
+    if (st == QIEO_OK) st = upload(q, q->hist_f, p, (size_t)h.t * sizeof(int64_t));
+    p += (size_t)h.t * sizeof(int64_t);
+    if (st == QIEO_OK) st = upload(q, q->gp.state, p, h.state_bytes);
+    if (st == QIEO_OK) st = upload(q, q->gp.conv, h.conv, sizeof h.conv);
+    if (st == QIEO_OK) st = upload(q, q->gp.best, h.best, sizeof h.best);
+    if (st == QIEO_OK) st = upload(q, q->gp.elite_idx, &h.elite_idx, sizeof h.elite_idx);
+    if (st == QIEO_OK) st = upload(q, q->gp.gen, &h.t, sizeof h.t);
+    if (st == QIEO_OK) st = upload(q, q->gp.bar_gen, &h.t, sizeof h.t);
+    if (st != QIEO_OK) return st;
+    q->t = h.t;
+    return QIEO_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 qieo_status qieo_get_convergence(qieo_instance *q, int32_t *stopped, int32_t *stable)
 {
     qieo_status st = check_inst(q);

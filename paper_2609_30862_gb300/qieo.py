@@ -43,7 +43,8 @@ EXPORTS = (
     "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
-    "qieo_get_phase_times", "qieo_get_convergence", "qieo_philox",
+    "qieo_get_phase_times", "qieo_get_convergence", "qieo_checkpoint_size",
+    "qieo_checkpoint_save", "qieo_checkpoint_load", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
     "qieo_run_batch", "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
     "qieo_server_get_stats", "qieo_server_cancel", "qieo_server_destroy", "qieo_last_error",
@@ -135,6 +136,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
         "qieo_get_phase_times": ([P, P, P], C.c_int),
         "qieo_get_convergence": ([P, P, P], C.c_int),
+        "qieo_checkpoint_size": ([P, P], C.c_int),
+        "qieo_checkpoint_save": ([P, P, C.c_size_t], C.c_int),
+        "qieo_checkpoint_load": ([P, P, C.c_size_t], C.c_int),
         "qieo_philox": ([P, P, i32], C.c_int),
         "qieo_generation_noalloc": ([P, P, i32, P, P, P, P], C.c_int),
         "qieo_create_batch": ([P, i32, P], C.c_int),
@@ -268,6 +272,20 @@ def qieo_get_convergence(h):
     a, b = C.c_int32(), C.c_int32()
     _check(load().qieo_get_convergence(h, C.byref(a), C.byref(b)))
     return bool(a.value), int(b.value)
+
+
+def qieo_checkpoint_save(h) -> bytes:
+    """The instance's checkpoint as bytes."""
+    n = C.c_size_t()
+    _check(load().qieo_checkpoint_size(h, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(load().qieo_checkpoint_save(h, buf, n.value))
+    return buf.raw
+
+
+def qieo_checkpoint_load(h, data: bytes) -> None:
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(load().qieo_checkpoint_load(h, buf, len(data)))
 
 
 def qieo_get_kernel_time(h):
@@ -513,6 +531,12 @@ class Instance:
 
     def convergence(self):
         return qieo_get_convergence(self.h)
+
+    def save(self) -> bytes:
+        return qieo_checkpoint_save(self.h)
+
+    def load(self, data: bytes) -> None:
+        qieo_checkpoint_load(self.h, data)
 
     def autotune(self, trial_generations: int = 8) -> qieo_launch_shape:
         return qieo_autotune(self.h, trial_generations)

@@ -398,3 +398,42 @@ def test_byte_state_needs_packed_item_sums():
     with pytest.raises(Q.QieoError) as e:
         Q.Instance(prob, 8, flags=Q.QIEO_FLAG_STATE_I8)
     assert e.value.status == Q.QIEO_ERR_INVALID and "STATE_I8" in str(e.value)
+
+
+@pytest.mark.parametrize("flags", [0, Q.QIEO_FLAG_PER_GENERATION, Q.QIEO_FLAG_STATE_I8,
+                                   Q.QIEO_FLAG_CONVERGE])
+def test_checkpoint_resume_is_bit_exact(flags):
+    """Save after 30 generations, load into a fresh instance of the same problem and run up
+    to 120 more: the state, the whole elite history, the best record and the convergence
+    stop (here at generation 106) equal one uninterrupted run (and the oracle)."""
+    from oracle import oracle as O
+    prob, np_, seed = W.knapsack(200, 3), 30, 3
+    window = 20 if flags == Q.QIEO_FLAG_CONVERGE else 0
+    ref = O.run(prob, np_, 150, seed=seed, window=window)
+    with Q.Instance(prob, np_, seed=seed, flags=flags) as a:
+        a.run(30)
+        blob = a.save()
+    with Q.Instance(prob, np_, seed=seed, flags=flags) as b:
+        b.run(3)                                   # overwritten by the load
+        b.load(blob)
+        assert b.state()[1] == 30
+        b.run(120)
+        k, t = b.state()
+        assert t == int(ref.t[0]) and np.array_equal(k, ref.k)
+        e, f = b.history(0, t)
+        assert np.array_equal(e, ref.hist_e) and np.array_equal(f, ref.hist_f)
+        bits, bf, bg, bc = b.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in ref.best)
+        assert np.array_equal(bits, ref.best_x)
+
+
+def test_checkpoint_rejects_another_problem():
+    with Q.Instance(W.knapsack(200, 3), 30, seed=3) as a:
+        a.run(5)
+        blob = a.save()
+    with Q.Instance(W.knapsack(200, 3), 30, seed=4) as b:   # other Philox seed
+        with pytest.raises(Q.QieoError) as e:
+            b.load(blob)
+        assert e.value.status == Q.QIEO_ERR_INVALID
+        with pytest.raises(Q.QieoError):
+            b.load(blob[:100])
