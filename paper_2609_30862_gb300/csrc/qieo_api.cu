@@ -197,6 +197,88 @@ const void *run_kernel_of(const qieo_instance *q, bool ring)
     return reinterpret_cast<const void *>(kernel_of<PickRun>(q, ring));
 }
 
+// Lets the device's default memory pool keep up to 1 GiB of released blocks, so that
+// creating and destroying instances in a loop reuses memory instead of mapping it anew
+// (set once per device).
+void keep_pool_memory(int device)
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return;
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = (uint64_t)1 << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done.push_back(device);
+}
+
+// A pinned host buffer of at least `bytes` for small device-to-host reads, one per host
+// thread, grown on demand (pinned memory makes the copies asynchronous, so a read waits
+// once).
+qieo_status pinned_scratch(size_t bytes, char **out)
+{
+    struct Scratch {
+        char *p = nullptr;
+        size_t n = 0;
+        ~Scratch()
+        {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    thread_local Scratch s;
+    if (s.n < bytes) {
+        if (s.p) cudaFreeHost(s.p);
+        s.p = nullptr;
+        s.n = 0;
+        const size_t n = std::max<size_t>(bytes, 4096);
+        CUDA_TRY(cudaMallocHost(&s.p, n));
+        s.n = n;
+    }
+    *out = s.p;
+    return QIEO_OK;
+}
+
+// The two timing events, made on first use.
+qieo_status ensure_events(qieo_instance *q)
+{
+    if (!q->ev0) CUDA_TRY(cudaEventCreate(&q->ev0));
+    if (!q->ev1) CUDA_TRY(cudaEventCreate(&q->ev1));
+    return QIEO_OK;
+}
+
+// Resident blocks per SM of a kernel at a dynamic shared-memory size (after raising the
+// kernel's shared-memory limit to it), cached per (device, kernel, size): instances of the
+// same kind then configure without querying the runtime again.
+qieo_status resident_blocks(int device, const void *fn, size_t smem, int *bps)
+{
+    struct Key {
+        int device;
+        const void *fn;
+        size_t smem;
+        bool operator<(const Key &o) const { return std::tie(device, fn, smem) < std::tie(o.device, o.fn, o.smem); }
+    };
+    static std::mutex mu;
+    static std::map<Key, int> cache;
+    const Key key{device, fn, smem};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *bps = it->second;
+            return QIEO_OK;
+        }
+    }
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int n = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, qieo::kThreads, smem));
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = n;
+    *bps = n;
+    return QIEO_OK;
+}
+
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
 // fills the launch fields of gp.
 qieo_status configure(qieo_instance *q)
@@ -222,13 +304,10 @@ qieo_status configure(qieo_instance *q)
 
     // Blocks resident at once, for the larger of the shared-memory sizes used.
     const size_t smem0 = ring + (size_t)qieo::kMaxSegRows * row_bytes;
-    for (const void *fn : {gen_kernel_of(q, use_ring), run_kernel_of(q, use_ring)})
-        CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0));
     int bps_gen = 0, bps_run = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_gen, gen_kernel_of(q, use_ring),
-                                                           qieo::kThreads, smem0));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_run, run_kernel_of(q, use_ring),
-                                                           qieo::kThreads, smem0));
+    qieo_status ost = resident_blocks(q->device, gen_kernel_of(q, use_ring), smem0, &bps_gen);
+    if (ost == QIEO_OK) ost = resident_blocks(q->device, run_kernel_of(q, use_ring), smem0, &bps_run);
+    if (ost != QIEO_OK) return ost;
     const int64_t resident = (int64_t)q->sm_count * std::max(1, std::min(bps_gen, bps_run));
     int grid = q->grid_override;
     if (grid <= 0) {
@@ -353,7 +432,10 @@ qieo_status wait_stream(cudaStream_t s)
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > kWaitSeconds)
             return fail(QIEO_ERR_TIMEOUT, "device work did not finish within %.0f s", kWaitSeconds);
-        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+        // poll without sleeping for the first 200 us (a sleep is at least tens of us on
+        // Linux, longer than most short waits), then back off
+        if (el < 2e-4) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 20 : 200));
     }
 }
 
@@ -383,10 +465,11 @@ qieo_status ensure_history(qieo_instance *q, int32_t need)
     int32_t cap = std::max<int32_t>(need, std::max<int32_t>(1024, q->hist_cap * 2));
     int32_t *e = nullptr;
     int64_t *f = nullptr;
-    CUDA_TRY(cudaMalloc(&e, (size_t)cap * sizeof(int32_t)));
-    cudaError_t err = cudaMalloc(&f, (size_t)cap * sizeof(int64_t));
+    keep_pool_memory(q->device);
+    CUDA_TRY(cudaMallocAsync(&e, (size_t)cap * sizeof(int32_t), q->stream));
+    cudaError_t err = cudaMallocAsync(&f, (size_t)cap * sizeof(int64_t), q->stream);
     if (err != cudaSuccess) {
-        cudaFree(e);
+        cudaFreeAsync(e, q->stream);
         return fail(QIEO_ERR_OOM, "history buffer: %s", cudaGetErrorString(err));
     }
     if (q->hist_cap > 0) {
@@ -394,10 +477,8 @@ qieo_status ensure_history(qieo_instance *q, int32_t need)
                                  cudaMemcpyDeviceToDevice, q->stream));
         CUDA_TRY(cudaMemcpyAsync(f, q->hist_f, (size_t)q->hist_cap * sizeof(int64_t),
                                  cudaMemcpyDeviceToDevice, q->stream));
-        qieo_status st = wait_stream(q->stream);
-        if (st != QIEO_OK) return st;
-        cudaFree(q->hist_e);
-        cudaFree(q->hist_f);
+        cudaFreeAsync(q->hist_e, q->stream);
+        cudaFreeAsync(q->hist_f, q->stream);
     }
     q->hist_e = e;
     q->hist_f = f;
@@ -456,6 +537,10 @@ qieo_status run_cooperative(qieo_instance *q, int32_t G)
 
 qieo_status run_device(qieo_instance *q, int32_t G)
 {
+    if (q->flags & QIEO_FLAG_TIME_KERNELS) {
+        qieo_status st = ensure_events(q);
+        if (st != QIEO_OK) return st;
+    }
     if (use_cooperative(q)) return run_cooperative(q, G);
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
@@ -767,10 +852,6 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
         if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "stream: %s", cudaGetErrorString(ce)));
         q->own_stream = true;
     }
-    ce = cudaEventCreate(&q->ev0);
-    if (ce == cudaSuccess) ce = cudaEventCreate(&q->ev1);
-    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "events: %s", cudaGetErrorString(ce)));
-
     const size_t ngp = (size_t)q->svec * 8;
     size_t off[kParts];
     const size_t total = instance_layout(q->ng, q->np, q->D, ext ? ext->hist_cap : 0, off, q->state8);
@@ -779,7 +860,10 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
         q->block = ext->block;
         q->owns_block = false;
     } else {
-        ce = cudaMalloc(&q->block, total);
+        // stream-ordered allocation from the device's pool: no device-wide synchronisation
+        // at allocation or release, and a freed block is reused by the next instance
+        keep_pool_memory(q->device);
+        ce = cudaMallocAsync(&q->block, total, q->stream);
         if (ce != cudaSuccess)
             return bail(fail(ce == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA,
                              "device allocation of %zu bytes: %s", total, cudaGetErrorString(ce)));
@@ -841,12 +925,17 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     std::vector<uint32_t> T32(T.size());
     for (size_t i = 0; i < T.size(); ++i) T32[i] = (uint32_t)(T[i] & 0xffffffffull);
 
-    ce = cudaMemcpyAsync(b + off[2], packed.data(), packed.size() * 4, cudaMemcpyHostToDevice, q->stream);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(b + off[3], wide.data(), wide.size() * 4, cudaMemcpyHostToDevice, q->stream);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(b + off[13], T32.data(), T32.size() * 4, cudaMemcpyHostToDevice, q->stream);
-    if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "upload: %s", cudaGetErrorString(ce)));
+    // One copy for the items (both layouts) and the thresholds: the parts between them are
+    // sent as zeros and set by the generation-0 initialisation that follows on the stream.
+    {
+        const size_t lo = off[2], hi = off[13] + T32.size() * 4;
+        std::vector<char> stage(hi - lo, 0);
+        std::memcpy(stage.data() + (off[2] - lo), packed.data(), packed.size() * 4);
+        std::memcpy(stage.data() + (off[3] - lo), wide.data(), wide.size() * 4);
+        std::memcpy(stage.data() + (off[13] - lo), T32.data(), T32.size() * 4);
+        ce = cudaMemcpyAsync(b + lo, stage.data(), stage.size(), cudaMemcpyHostToDevice, q->stream);
+        if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "upload: %s", cudaGetErrorString(ce)));
+    }
 
     if (q->host_de) {
         ce = cudaMallocHost(&q->h_fit, (size_t)q->np * sizeof(int64_t));
@@ -900,14 +989,17 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     cudaSetDevice(q->device);
     if (q->stream) cudaStreamSynchronize(q->stream);
     drop_graphs(q);
-    if (q->block) cudaFree(q->block);
-    if (q->hist_e) cudaFree(q->hist_e);
-    if (q->hist_f) cudaFree(q->hist_f);
+    if (q->block && q->owns_block) cudaFreeAsync(q->block, q->stream);
+    if (q->hist_e && !q->fixed_history) cudaFreeAsync(q->hist_e, q->stream);
+    if (q->hist_f && !q->fixed_history) cudaFreeAsync(q->hist_f, q->stream);
     if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
     for (cudaEvent_t e : q->phase_ev) cudaEventDestroy(e);
-    if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
+    if (q->own_stream && q->stream) {
+        cudaStreamSynchronize(q->stream);   // the block's release is ordered on it
+        cudaStreamDestroy(q->stream);
+    }
     delete q;
     return QIEO_OK;
 }
@@ -991,15 +1083,23 @@ qieo_status qieo_get_best(qieo_instance *q, uint8_t *bits_out, int64_t *fitness,
     if (st != QIEO_OK) return st;
     st = set_device(q);
     if (st != QIEO_OK) return st;
-    int64_t best[3];
-    st = fetch(q, best, q->gp.best, sizeof best);
+    // the error word, the record and the row in one round: copies into a pinned bounce
+    // buffer queued behind the instance's work, one wait
+    char *pin = nullptr;
+    st = pinned_scratch(64 + (size_t)q->xstride, &pin);
     if (st != QIEO_OK) return st;
-    if (bits_out) {
-        std::vector<uint8_t> row((size_t)q->xstride);
-        st = fetch(q, row.data(), q->gp.best_row, row.size());
-        if (st != QIEO_OK) return st;
-        unpack_row(row.data(), q->ng, bits_out);
-    }
+    int32_t *err_h = reinterpret_cast<int32_t *>(pin);
+    int64_t *best_h = reinterpret_cast<int64_t *>(pin + 8);
+    uint8_t *row_h = reinterpret_cast<uint8_t *>(pin + 64);
+    CUDA_TRY(cudaMemcpyAsync(err_h, q->gp.error, sizeof(int32_t), cudaMemcpyDeviceToHost, q->stream));
+    CUDA_TRY(cudaMemcpyAsync(best_h, q->gp.best, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, q->stream));
+    if (bits_out)
+        CUDA_TRY(cudaMemcpyAsync(row_h, q->gp.best_row, (size_t)q->xstride, cudaMemcpyDeviceToHost, q->stream));
+    st = wait_stream(q->stream);
+    if (st != QIEO_OK) return st;
+    if (*err_h) return wait_checked(q);   // reports the recorded device error
+    const int64_t best[3] = {best_h[0], best_h[1], best_h[2]};
+    if (bits_out) unpack_row(row_h, q->ng, bits_out);
     if (fitness) *fitness = best[0];
     if (generation) *generation = (int32_t)best[1];
     if (chromosome) *chromosome = (int32_t)best[2];
@@ -1630,6 +1730,8 @@ qieo_status qieo_autotune(qieo_instance *q, int32_t trials, qieo_launch_shape *s
     if (trials < 1 || trials > 1000) return fail(QIEO_ERR_INVALID, "trial_generations must be in [1, 1000]");
     if (q->host_de) return fail(QIEO_ERR_INVALID, "autotune times the device path; elite_on_host is set");
     st = set_device(q);
+    if (st != QIEO_OK) return st;
+    st = ensure_events(q);
     if (st != QIEO_OK) return st;
     std::vector<std::pair<int, int>> cands;
     const int span = pow2_ceil(q->svec);
