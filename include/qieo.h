@@ -130,11 +130,12 @@ qieo_status qieo_reset(qieo_instance *inst);
 
 /* Runs `generations` >= 0 generations from the current one (Fig. 1: QIP, Evaluation,
  * DetermineElite, CIP, per generation; the CIP of the last generation is applied before
- * returning, so run(a) followed by run(b) equals run(a + b)). By default each generation
- * is one kernel launch, chained to the next by programmatic dependent launch and replayed
- * from a CUDA graph when a run length repeats; QIEO_FLAG_COOPERATIVE runs the whole run as
- * one cooperative launch whose blocks meet at a bounded grid barrier after each
- * generation. Stream-ordered: returns after enqueueing unless QIEO_FLAG_SYNC_RUN is set or
+ * returning, so run(a) followed by run(b) equals run(a + b)). Each generation is one kernel
+ * launch, chained to the next by programmatic dependent launch and replayed from a CUDA
+ * graph when a run length repeats; instances of at most 2^22 genes (or any instance with
+ * QIEO_FLAG_COOPERATIVE) run the whole run as one cooperative launch whose blocks meet at
+ * a bounded grid barrier after each generation (qieo_launch_shape.persistent tells which).
+ * Stream-ordered: returns after enqueueing unless QIEO_FLAG_SYNC_RUN is set or
  * elite_on_host is 1. A barrier wait that runs out is reported as QIEO_ERR_TIMEOUT by the
  * next call that waits for the device; the state is then undefined until qieo_reset. */
 qieo_status qieo_run(qieo_instance *inst, int32_t generations);
@@ -294,9 +295,9 @@ qieo_status qieo_server_create(const qieo_server_config *config, qieo_server **o
 /* Queues one solve: `generations` generations of problem (host arrays, copied) with params
  * (np, D, lambda, seed, instance_id, rotate_rule, and of the flags QIEO_FLAG_CONVERGE, with
  * which `generations` is a cap and the solve leaves as soon as it converged; stream, the
- * other flags and elite_on_host are ignored). *id_out receives the request id. QIEO_ERR_OOM when the solve needs more device
- * memory than the whole arena (it could never be admitted); QIEO_ERR_INVALID for bad
- * arguments. Thread-safe. */
+ * other flags and elite_on_host are ignored). *id_out receives the request id.
+ * QIEO_ERR_OOM when the solve needs more device memory than the whole arena (it could
+ * never be admitted); QIEO_ERR_INVALID for bad arguments. Thread-safe. */
 qieo_status qieo_server_submit(qieo_server *server, const qieo_problem *problem,
                                const qieo_params *params, int32_t generations, int64_t *id_out);
 
