@@ -156,3 +156,35 @@ def test_one_call_batched_run():
     for i, (s, (prob, inst)) in enumerate(zip(SPECS[:5], made)):
         check_against_oracle(inst, prob, s[1], 13, i + 1, i, s[3], s[4], s[2])
         inst.close()
+
+
+def test_batch_from_saturated_states():
+    """Batched members that start fully saturated (fixed-allele passes from the first
+    generation, rows that disagree with the elite drawing again), against the oracle run
+    on each alone."""
+    from saturated import load_state, saturated_start
+    from oracle import oracle as O
+    specs = [(3001, 83, 0), (1500, 40, 1), (5000, 64, 0)]
+    made = []
+    for i, (ng, np_, rule) in enumerate(specs):
+        prob = W.knapsack(ng, 50 + i)
+        k0 = saturated_start(ng, np_, 60 + i, n_odd=5, flips=30)
+        inst = Q.Instance(prob, np_, seed=i + 3, rule=rule)
+        load_state(inst, k0)
+        made.append((prob, k0, inst))
+    with Q.Batch([m[2] for m in made]) as b:
+        for g in (30, 30, 11):
+            b.run(g)
+    for i, ((ng, np_, rule), (prob, k0, inst)) in enumerate(zip(specs, made)):
+        st = O.State(np_, ng)
+        st.k[:] = k0
+        O.run(prob, np_, 71, seed=i + 3, rule=rule, state=st)
+        k, t = inst.state()
+        assert t == 71
+        assert np.array_equal(k, st.k)
+        e, f = inst.history(0, 71)
+        assert np.array_equal(e, st.hist_e) and np.array_equal(f, st.hist_f)
+        assert np.array_equal(inst.alleles(), st.x)
+        bits, bf, bg, bc = inst.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in st.best)
+        inst.close()

@@ -9,6 +9,7 @@ import pytest
 
 from paper_2609_30862_gb300 import qieo as Q
 from paper_2609_30862_gb300 import workload as W
+from saturated import load_state, saturated_start
 
 pytestmark = pytest.mark.gpu
 
@@ -437,3 +438,55 @@ def test_checkpoint_rejects_another_problem():
         assert e.value.status == Q.QIEO_ERR_INVALID
         with pytest.raises(Q.QieoError):
             b.load(blob[:100])
+
+
+def compare_from(prob, k0, chunks, seed=1, rule=0, flags=0, shape=None, D=100):
+    from oracle import oracle as O
+    np_, ng = k0.shape
+    gens = int(sum(chunks))
+    st = O.State(np_, ng)
+    st.k[:] = k0
+    O.run(prob, np_, gens, seed=seed, D=D, rule=rule, state=st)
+    with Q.Instance(prob, np_, seed=seed, D=D, rule=rule, flags=flags) as I:
+        if shape is not None:
+            I.set_shape(*shape)
+        load_state(I, k0, D, byte_state=bool(flags & Q.QIEO_FLAG_STATE_I8))
+        for g in chunks:
+            I.run(g)
+        k, t = I.state()
+        assert t == gens
+        assert np.array_equal(k, st.k), "angle indices differ"
+        e, f = I.history(0, gens)
+        assert np.array_equal(e, st.hist_e) and np.array_equal(f, st.hist_f)
+        assert np.array_equal(I.fitness(), st.f)
+        assert np.array_equal(I.alleles(), st.x)
+        bits, bf, bg, bc = I.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in st.best)
+        assert np.array_equal(bits, st.best_x)
+
+
+@pytest.mark.parametrize("flags,shape", [
+    (0, None),                                              # cooperative at this size
+    (Q.QIEO_FLAG_PER_GENERATION, None),
+    (Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_FORCE_WIDE, None),
+    (Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_STATE_I8, None),
+    (Q.QIEO_FLAG_PER_GENERATION, (32, 2)),                  # four rows per pass
+    (Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_NO_GRAPH, (32, 8, 37)),   # odd grid
+])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_fixed_allele_passes_from_a_saturated_state(flags, shape, rule):
+    """Every qubit starts at a bound, so passes are fixed-allele passes from the first
+    generation on, except where a row disagrees with the elite: those rows rotate away from
+    the bound, draw again, and come back. Runs split into several lengths, through each
+    launch form, sum form, state width and tile shape."""
+    k0 = saturated_start(3001, 83, 31 + rule, n_odd=9, flips=40)
+    compare_from(W.knapsack(3001, 31), k0, [1, 2, 37, 25], seed=31, rule=rule, flags=flags,
+                 shape=shape)
+
+
+def test_fixed_allele_passes_through_natural_saturation():
+    """A population that saturates on its own within a run: spread generations, the
+    fixed-allele passes once qubits reach the bounds, and later elite changes."""
+    compare(W.knapsack(4000, 41), 128, [180, 220], seed=41, rule=0,
+            flags=Q.QIEO_FLAG_PER_GENERATION)
+    compare(W.knapsack(4000, 42), 96, [400], seed=42, rule=1)
