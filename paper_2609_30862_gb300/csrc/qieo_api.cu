@@ -116,6 +116,8 @@ struct qieo_instance {
     bool fixed_history = false;     // history lives inside an arena block of fixed capacity
     qieo::GenParams gp{};
     const uint4 *items_narrow = nullptr;
+    int4 *segq = nullptr;            // segment queue of the deferred forms (own allocation)
+    int32_t segq_cap = 0;
     int32_t *hist_e = nullptr;
     int64_t *hist_f = nullptr;
     int32_t hist_cap = 0;
@@ -279,6 +281,47 @@ qieo_status resident_blocks(int device, const void *fn, size_t smem, int *bps)
     return QIEO_OK;
 }
 
+// Segment queue of the deferred forms: the units (tile-rows) in order, cut into segments
+// within one tile of at most seg_max rows whose size follows the remaining work (guided
+// self-scheduling: remaining / (2 grid), at least kQueueMinRows), so that the first
+// segments are large and the last ones small. Only when a block's equal share is at least
+// kQueueMinShare tile-rows: with smaller shares the latency each extra segment adds (the
+// queue's atomic, the segment's first copies, its flush) costs more than the balance
+// gains (measured: 1,024 x 10,000 genes, 8 rows per block, 10.1 -> 12.2 us per generation
+// with a queue; 4,096 x 100,000, 330 rows per block, 396 -> 367 us). Instances placed in
+// a server arena run in batches only and keep none.
+constexpr int64_t kQueueMinRows = 4;
+constexpr int64_t kQueueMinShare = 64;
+
+qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring)
+{
+    q->gp.segq = nullptr;
+    q->gp.nsegs = 0;
+    if (!use_ring || !q->owns_block || units < kQueueMinShare * (int64_t)grid) return QIEO_OK;
+    std::vector<int4> segs;
+    for (int64_t u = 0; u < units;) {
+        const int64_t tile = u / q->np, ra = u - tile * q->np;
+        const int64_t rem = units - u;
+        int64_t rows = std::max<int64_t>(kQueueMinRows, (rem + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid));
+        rows = std::min<int64_t>(rows, std::min<int64_t>((int64_t)seg_max, (int64_t)q->np - ra));
+        segs.push_back(make_int4((int)tile, (int)ra, (int)rows, 0));
+        u += rows;
+    }
+    if ((int64_t)segs.size() > q->segq_cap) {
+        if (q->segq) cudaFreeAsync(q->segq, q->stream);
+        q->segq = nullptr;
+        q->segq_cap = 0;
+        keep_pool_memory(q->device);
+        CUDA_TRY(cudaMallocAsync(&q->segq, segs.size() * sizeof(int4), q->stream));
+        q->segq_cap = (int32_t)segs.size();
+    }
+    CUDA_TRY(cudaMemcpyAsync(q->segq, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                             q->stream));
+    q->gp.segq = q->segq;
+    q->gp.nsegs = (int32_t)segs.size();
+    return QIEO_OK;
+}
+
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
 // fills the launch fields of gp.
 qieo_status configure(qieo_instance *q)
@@ -329,6 +372,8 @@ qieo_status configure(qieo_instance *q)
     g.warps = q->warps;
     g.seg_rows_max = seg_max;
     g.key_mode = q->key_ok ? 1 : 0;
+    qieo_status qst = build_segment_queue(q, units, grid, seg_max, use_ring);
+    if (qst != QIEO_OK) return qst;
     drop_graphs(q);
     return QIEO_OK;
 }
@@ -749,7 +794,8 @@ size_t instance_layout(int32_t ng, int32_t np, int32_t D, int32_t hist_cap, size
                                   sizeof(int32_t),
                                   (size_t)(D / 2 + 1) * sizeof(uint32_t),
                                   sizeof(int32_t),
-                                  5 * sizeof(int32_t),   // error word, convergence words
+                                  8 * sizeof(int32_t),   // error word, convergence words,
+                                                         // segment-queue counters
                                   (size_t)hist_cap * sizeof(int32_t),
                                   (size_t)hist_cap * sizeof(int64_t)};
     size_t total = 0;
@@ -889,6 +935,7 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     g.bar_gen = (int32_t *)(b + off[14]);
     g.error = (int32_t *)(b + off[15]);
     g.conv = g.error + 1;
+    g.qctr = reinterpret_cast<unsigned int *>(g.error + 5);
     g.converge = (q->flags & QIEO_FLAG_CONVERGE) ? 1 : 0;
     g.wait_ns = kDefaultBarrierWaitNs;
     g.np = q->np;
@@ -992,6 +1039,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->block && q->owns_block) cudaFreeAsync(q->block, q->stream);
     if (q->hist_e && !q->fixed_history) cudaFreeAsync(q->hist_e, q->stream);
     if (q->hist_f && !q->fixed_history) cudaFreeAsync(q->hist_f, q->stream);
+    if (q->segq) cudaFreeAsync(q->segq, q->stream);
     if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);

@@ -144,6 +144,10 @@ struct GenParams {
                                   // close: t = *gen + g; otherwise 0 and t = *gen)
     int32_t deferred;             // 1: deferred close (see generation_kernel)
     int32_t state8;               // 1: angle indices stored as bytes (8 B per 8 genes)
+    const int4 *segq;             // segment queue (tile, first row, rows, 0) of the deferred
+                                  // forms, in order of decreasing size; nsegs = 0: none
+    unsigned int *qctr;           // [3] next queue index of generation t in slot t % 3
+    int32_t nsegs;
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -835,6 +839,41 @@ __device__ __forceinline__ void generation_body_ring(const GenParams &p, const B
     }
 }
 
+// One generation over segments taken from the instance's queue (deferred forms). The blocks
+// that share an SM do not get equal issue slots (the schedulers favour older warps), so
+// with equal static shares the blocks launched first finish early and leave their SM part
+// empty while the others finish; taken from a queue in order of decreasing size, the
+// segments keep every block busy until the work runs out. Any split gives the same
+// results: each tile-row's sums are exact integers added once per segment.
+template <bool kNarrow, int kRule, bool kCip, bool kS8 = false>
+__device__ __forceinline__ void generation_body_queue(const GenParams &p, const BlockShare &b,
+                                                      int32_t t, int32_t e_prev, uint4 *ring,
+                                                      const uint32_t *s_thr, uint32_t *s_acc32,
+                                                      unsigned long long *s_acc64)
+{
+    __shared__ int32_t s_qi;
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+    uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
+    uint4 *slots = ring + threadIdx.x;
+    unsigned int *ctr = p.qctr + (t % 3);
+    int countdown = 0;
+    clear_row_sums<kNarrow>(p.seg_rows_max, s_acc32, s_acc64);
+    for (;;) {
+        // every thread reads the index before the segment's first barrier, after which
+        // thread 0 may overwrite it
+        if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
+        __syncthreads();
+        const int32_t qi = s_qi;
+        if (qi >= p.nsegs) break;
+        const int4 sg = __ldg(p.segq + qi);
+        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8>(p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t, x_prev,
+                                                           x_cur, elite_row, thr_bytes, slots, s_acc32,
+                                                           s_acc64, countdown);
+    }
+}
+
 // CIP with elite e of generation t over this block's share (the final rotation of a run).
 template <int kRule, bool kS8 = false>
 __device__ __forceinline__ void final_cip_body(const GenParams &p, const BlockShare &b,
@@ -971,14 +1010,22 @@ __device__ __forceinline__ SmemParts carve_smem(unsigned char *raw)
     return m;
 }
 
+// queued: take the segments from the instance's queue (deferred forms with a queue).
 template <bool kNarrow, int kRule, bool kCip, bool kRing, bool kS8 = false>
 __device__ __forceinline__ void one_generation(const GenParams &p, const BlockShare &b, int32_t t,
-                                               int32_t e_prev, SmemParts &m, const uint32_t *s_thr)
+                                               int32_t e_prev, SmemParts &m, const uint32_t *s_thr,
+                                               bool queued = false)
 {
-    if constexpr (kRing)
-        generation_body_ring<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32, m.acc64);
-    else
+    if constexpr (kRing) {
+        if (queued && p.nsegs > 0)
+            generation_body_queue<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32,
+                                                             m.acc64);
+        else
+            generation_body_ring<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32,
+                                                            m.acc64);
+    } else {
         generation_body<kNarrow, kRule, kCip>(p, b, t, e_prev, s_thr, m.acc32, m.acc64);
+    }
 }
 
 // Records of generation t with elite e of fitness f: the history, the elite index, the
@@ -1084,9 +1131,12 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_k
                 if (blockIdx.x == 0) record_generation(p, t - 1, e, f);
             }
             if (g == G) break;
-            if (blockIdx.x == 0 && threadIdx.x == 0) *key_slot(p, t + 1) = 0ull;
-            if (g == 0) one_generation<kNarrow, kRule, false, kRing>(p, b, t, 0, m, s_thr);
-            else one_generation<kNarrow, kRule, true, kRing>(p, b, t, e, m, s_thr);
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                *key_slot(p, t + 1) = 0ull;
+                p.qctr[(t + 1) % 3] = 0u;
+            }
+            if (g == 0) one_generation<kNarrow, kRule, false, kRing>(p, b, t, 0, m, s_thr, true);
+            else one_generation<kNarrow, kRule, true, kRing>(p, b, t, e, m, s_thr, true);
             grid_arrive(p);
         }
         final_cip_body<kRule>(p, b, t0 + G - 1, e);
@@ -1161,14 +1211,17 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
                     st_release(p.conv + 2, kStopped);
                 }
             }
-            if (threadIdx.x == 0) *key_slot(p, t + 1) = 0ull;
+            if (threadIdx.x == 0) {
+                *key_slot(p, t + 1) = 0ull;
+                p.qctr[(t + 1) % 3] = 0u;
+            }
         }
         if (stop == kStopPending) {
             final_cip_body<kRule, kS8>(p, b, t - 1, e_prev);   // the CIP of the converged generation
             return;
         }
-        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing, kS8>(p, b, t, e_prev, m, s_thr);
-        else one_generation<kNarrow, kRule, false, kRing, kS8>(p, b, t, e_prev, m, s_thr);
+        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing, kS8>(p, b, t, e_prev, m, s_thr, true);
+        else one_generation<kNarrow, kRule, false, kRing, kS8>(p, b, t, e_prev, m, s_thr, true);
         allow_dependent_launch();
         return;
     }
@@ -1219,7 +1272,7 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
 
 // End of a deferred-close run of G generations: advances the generation counter (to one past
 // the generation that met the convergence test, if the instance stopped) and clears the
-// three key slots. One thread.
+// three key slots and segment-queue counters. One thread.
 __global__ void end_run_kernel(const GenParams p, int32_t G)
 {
     grid_dependency_wait();
@@ -1231,6 +1284,7 @@ __global__ void end_run_kernel(const GenParams p, int32_t G)
     *p.bar_gen = next;
     *p.ticket = 0u;   // the arrival counter of a cooperative run
     p.keys[0] = p.keys[1] = p.keys[2] = 0ull;
+    p.qctr[0] = p.qctr[1] = p.qctr[2] = 0u;
 }
 
 // Records of a generation whose elite e was picked on the host (host DetermineElite).
@@ -1635,6 +1689,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
         *p.gen = 0;
         *p.ticket = 0u;
         p.keys[0] = p.keys[1] = p.keys[2] = 0ull;
+        p.qctr[0] = p.qctr[1] = p.qctr[2] = 0u;
         *p.elite_idx = 0;
         *p.bar_gen = 0;
         *p.error = 0;

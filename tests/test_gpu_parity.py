@@ -490,3 +490,42 @@ def test_fixed_allele_passes_through_natural_saturation():
     compare(W.knapsack(4000, 41), 128, [180, 220], seed=41, rule=0,
             flags=Q.QIEO_FLAG_PER_GENERATION)
     compare(W.knapsack(4000, 42), 96, [400], seed=42, rule=1)
+
+
+@pytest.mark.parametrize("flags,shape", [
+    (0, (32, 8, 3)),                                        # cooperative, 134 rows per block
+    (Q.QIEO_FLAG_PER_GENERATION, (32, 8, 3)),
+    (Q.QIEO_FLAG_PER_GENERATION, (32, 2, 5)),               # four rows per pass, 6 tiles
+    (Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_FORCE_WIDE, (32, 8, 2)),
+    (Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_STATE_I8, (32, 4, 4)),
+    (Q.QIEO_FLAG_PER_GENERATION | Q.QIEO_FLAG_NO_GRAPH, (32, 8, 1)),   # one block, whole queue
+])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_segment_queue(flags, shape, rule):
+    """Grids small enough that each block's share is at least 64 tile-rows, so the deferred
+    forms take their segments from the guided queue (large segments first, 4-row ones
+    last) instead of equal static shares."""
+    compare(W.knapsack(3001, 51), 200, [1, 30, 45], seed=51, rule=rule, flags=flags, shape=shape)
+    k0 = saturated_start(3001, 200, 52 + rule, n_odd=11, flips=60)
+    compare_from(W.knapsack(3001, 52), k0, [2, 40], seed=52, rule=rule, flags=flags, shape=shape)
+
+
+def test_segment_queue_with_convergence_stop():
+    """The convergence stop through queued per-generation launches (the stopping launch
+    applies the last CIP alone; later launches do nothing)."""
+    from oracle import oracle as O
+    prob, np_, seed = W.knapsack(1200, 7), 256, 7
+    ref = O.run(prob, np_, 600, seed=seed, window=20)
+    assert ref.stopped
+    tc = int(ref.t[0]) - 1
+    with Q.Instance(prob, np_, seed=seed, flags=Q.QIEO_FLAG_CONVERGE) as I:
+        I.set_shape(32, 8, 2)            # 1 tile x 256 rows: 128 rows per block
+        for g in (tc - 7, 40, 40):
+            I.run(g)
+        k, t = I.state()
+        assert t == tc + 1
+        assert np.array_equal(k, ref.k)
+        e, f = I.history(0, t)
+        assert np.array_equal(e, ref.hist_e) and np.array_equal(f, ref.hist_f)
+        bits, bf, bg, bc = I.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in ref.best)
