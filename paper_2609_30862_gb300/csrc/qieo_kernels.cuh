@@ -382,8 +382,14 @@ struct SegCtx {
 };
 
 __shared__ uint4 s_item_bytes[kThreads];   // per thread: w4a, w4b, v4a, v4b
+// Rule R1 moves every qubit toward the elite's allele, so the CIP deltas of a vector depend
+// only on the elite's 8 alleles: they are formed once per segment (four delta_pair words)
+// into this per-thread slot, and a pass reads them with one 16-byte shared load (measured:
+// c3 366 -> 358 us per generation, c2 10.05 -> 9.93 us, against forming them every pass).
+__shared__ uint4 s_delta[kThreads];
 
-template <bool kNarrow, bool kCip>
+// kSegDelta: form the rule R1 delta words of the segment (s_delta).
+template <bool kNarrow, bool kCip, bool kSegDelta = true>
 __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int tile, int v_in,
                                           int tile_vecs, const uint8_t *elite_row)
 {
@@ -413,6 +419,9 @@ __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int til
         g.vi[4] = e.x; g.vi[5] = e.y; g.vi[6] = e.z; g.vi[7] = e.w;
     }
     g.e8 = (kCip && g.active) ? (uint32_t)__ldcg(elite_row + g.vec) : 0u;
+    if (kCip && kSegDelta)   // read back by this thread only (rule R1 passes)
+        s_delta[threadIdx.x] = make_uint4(delta_pair(g.e8 & 3u, 3u), delta_pair((g.e8 >> 2) & 3u, 3u),
+                                          delta_pair((g.e8 >> 4) & 3u, 3u), delta_pair((g.e8 >> 6) & 3u, 3u));
     g.ctr0 = 2u * (uint32_t)g.vec;
 }
 
@@ -463,7 +472,7 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
 // needed, and the state is unchanged (fixed = true: the caller skips its store). The test
 // is skipped for 15 passes after it fails, which keeps its cost low while the population
 // is still spread out.
-template <bool kNarrow, int kRule, bool kCip, class Keys>
+template <bool kNarrow, int kRule, bool kCip, class Keys, bool kSegDelta = true>
 __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys, const SegCtx &g, uint4 s,
                                             uint32_t xo, int32_t c, int32_t t,
                                             const unsigned char *thr_bytes, bool &fixed,
@@ -510,7 +519,17 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
         --countdown;
     }
 
-    if (kCip) s = rotate_vec(s, g.e8, m8, k8);
+    if (kCip) {
+        if (kRule == 0 && kSegDelta) {  // R1: the segment's delta words
+            const uint4 d = s_delta[threadIdx.x];
+            s.x = rotate_pair(s.x, d.x, k8);
+            s.y = rotate_pair(s.y, d.y, k8);
+            s.z = rotate_pair(s.z, d.z, k8);
+            s.w = rotate_pair(s.w, d.w, k8);
+        } else {
+            s = rotate_vec(s, g.e8, m8, k8);
+        }
+    }
     const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
     const Draw4 r0 = keys(g.ctr0, (uint32_t)c, (uint32_t)t);
     const Draw4 r1 = keys(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t);
@@ -716,7 +735,9 @@ __device__ __forceinline__ void cp_async_wait()
 
 // One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation. kS8:
 // the state is stored as bytes (copied 8 bytes per pass, widened to 16-bit lanes).
-template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false>
+// kSegDelta: rule R1 deltas formed once per segment (the batched kernel, whose segments are
+// many and short, forms them every pass: measured 4,592 vs 4,338 solves/s on c4).
+template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false, bool kSegDelta = true>
 __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &keys, const BlockShare &b,
                                              int tile, int ra, int seg_rows, int32_t t,
                                              const uint8_t *x_prev, uint8_t *x_cur,
@@ -729,7 +750,7 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     const int passes = (seg_rows + rpp - 1) / rpp;
 
     SegCtx g;
-    seg_setup<kNarrow, kCip>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
+    seg_setup<kNarrow, kCip, kSegDelta>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
     const size_t row0 = (size_t)ra + b.r_sub;
     using SV = typename std::conditional<kS8, uint2, uint4>::type;
     SV *sptr = reinterpret_cast<SV *>(p.state) + row0 * p.svec + g.vec;
@@ -786,8 +807,8 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         uint32_t xbits, accn;
         int64_t acw, acv;
         bool fixed;
-        sv = qubit_pass<kNarrow, kRule, kCip>(p, keys, g, sv, xo, ra + rr, t, thr_bytes, fixed,
-                                              countdown, xbits, accn, acw, acv);
+        sv = qubit_pass<kNarrow, kRule, kCip, Keys, kSegDelta>(p, keys, g, sv, xo, ra + rr, t, thr_bytes,
+                                                               fixed, countdown, xbits, accn, acw, acv);
         if (g.active && ok) {
             if (!fixed) {               // a fixed pass leaves the state as it is
                 if constexpr (kS8) *st_ptr = pack8(sv);
@@ -1587,10 +1608,9 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
         if (stop == kStopPending)            // the CIP of the generation that converged
             rotate_segment<kRule>(p, b, sg.tile, sg.ra, sg.rows, t - 1, e_prev);
         else
-            ring_segment<kNarrow, kRule, kCip>(p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra,
-                                               sg.rows, t, x_prev, x_cur,
-                                               x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots,
-                                               m.acc32, m.acc64, countdown);
+            ring_segment<kNarrow, kRule, kCip, InlineKeys, false, false>(
+                p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra, sg.rows, t, x_prev, x_cur,
+                x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots, m.acc32, m.acc64, countdown);
         // the block that finishes an instance's last segment closes its generation (barrier
         // + release by thread 0, acquire by the last block's thread 0 + barrier)
         __syncthreads();
