@@ -118,6 +118,7 @@ struct qieo_instance {
     const uint4 *items_narrow = nullptr;
     int4 *segq = nullptr;            // segment queue of the deferred forms (own allocation)
     int32_t segq_cap = 0;
+    bool seg_delta = false;          // generation kernel forms the R1 deltas once per segment
     int32_t *hist_e = nullptr;
     int64_t *hist_f = nullptr;
     int32_t hist_cap = 0;
@@ -181,17 +182,29 @@ struct PickRun {
     static type get() { return &qieo::run_kernel<N, R, T>; }
 };
 
-// The generation kernel of an instance (byte-state instances: narrow sums, ring form).
-PickGen<true, 0, true>::type gen_fn(const qieo_instance *q, bool ring)
+// The generation kernel of an instance (byte-state instances: narrow sums, ring form). With
+// seg_delta (rule R1, ring form, segment queue) the variant that forms the CIP deltas once
+// per segment.
+PickGen<true, 0, true>::type gen_fn(const qieo_instance *q, bool ring, bool seg_delta)
 {
+    if (seg_delta && ring && q->rule == 0) {
+        if (q->state8) return &qieo::generation_kernel<true, 0, true, true, true>;
+        return q->narrow ? &qieo::generation_kernel<true, 0, true, false, true>
+                         : &qieo::generation_kernel<false, 0, true, false, true>;
+    }
     if (q->state8)
         return q->rule ? &qieo::generation_kernel<true, 1, true, true> : &qieo::generation_kernel<true, 0, true, true>;
     return kernel_of<PickGen>(q, ring);
 }
 
-const void *gen_kernel_of(const qieo_instance *q, bool ring)
+PickGen<true, 0, true>::type gen_fn(const qieo_instance *q, bool ring)
 {
-    return reinterpret_cast<const void *>(gen_fn(q, ring));
+    return gen_fn(q, ring, q->seg_delta);
+}
+
+const void *gen_kernel_of(const qieo_instance *q, bool ring, bool seg_delta)
+{
+    return reinterpret_cast<const void *>(gen_fn(q, ring, seg_delta));
 }
 
 const void *run_kernel_of(const qieo_instance *q, bool ring)
@@ -322,6 +335,13 @@ qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int s
     return QIEO_OK;
 }
 
+// Persistent blocks per SM of the single-instance kernels. The schedulers favour older
+// warps, so blocks sharing an SM do not progress equally; measured on the GB300 (per
+// 25-generation timing, c2 = 1,024 x 10,000 genes with equal static shares, c3 = 4,096 x
+// 100,000 with the segment queue): 4 blocks 10.06 / 366 us per generation, 3 blocks 9.61 /
+// 364 us (per-pass deltas), 2 blocks worse (10.7 / 387 us with per-segment deltas).
+constexpr int kBlocksPerSm = 3;
+
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
 // fills the launch fields of gp.
 qieo_status configure(qieo_instance *q)
@@ -345,13 +365,16 @@ qieo_status configure(qieo_instance *q)
     const bool use_ring = !(q->flags & QIEO_FLAG_REGISTER_PREFETCH);
     const size_t ring = use_ring ? qieo::kRingBytes : 0;
 
-    // Blocks resident at once, for the larger of the shared-memory sizes used.
+    // Blocks resident at once, for the larger of the shared-memory sizes used and either
+    // generation-kernel variant, capped at kBlocksPerSm.
     const size_t smem0 = ring + (size_t)qieo::kMaxSegRows * row_bytes;
-    int bps_gen = 0, bps_run = 0;
-    qieo_status ost = resident_blocks(q->device, gen_kernel_of(q, use_ring), smem0, &bps_gen);
+    int bps_gen = 0, bps_sd = 0, bps_run = 0;
+    qieo_status ost = resident_blocks(q->device, gen_kernel_of(q, use_ring, false), smem0, &bps_gen);
+    if (ost == QIEO_OK) ost = resident_blocks(q->device, gen_kernel_of(q, use_ring, true), smem0, &bps_sd);
     if (ost == QIEO_OK) ost = resident_blocks(q->device, run_kernel_of(q, use_ring), smem0, &bps_run);
     if (ost != QIEO_OK) return ost;
-    const int64_t resident = (int64_t)q->sm_count * std::max(1, std::min(bps_gen, bps_run));
+    const int bps = std::min(kBlocksPerSm, std::min(bps_gen, std::min(bps_sd, bps_run)));
+    const int64_t resident = (int64_t)q->sm_count * std::max(1, bps);
     int grid = q->grid_override;
     if (grid <= 0) {
         const int64_t by_work = (units + rpp - 1) / rpp;
@@ -374,6 +397,7 @@ qieo_status configure(qieo_instance *q)
     g.key_mode = q->key_ok ? 1 : 0;
     qieo_status qst = build_segment_queue(q, units, grid, seg_max, use_ring);
     if (qst != QIEO_OK) return qst;
+    q->seg_delta = g.nsegs > 0 && q->rule == 0;   // long queued segments: deltas per segment
     drop_graphs(q);
     return QIEO_OK;
 }

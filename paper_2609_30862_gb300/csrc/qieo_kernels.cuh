@@ -383,13 +383,13 @@ struct SegCtx {
 
 __shared__ uint4 s_item_bytes[kThreads];   // per thread: w4a, w4b, v4a, v4b
 // Rule R1 moves every qubit toward the elite's allele, so the CIP deltas of a vector depend
-// only on the elite's 8 alleles: they are formed once per segment (four delta_pair words)
-// into this per-thread slot, and a pass reads them with one 16-byte shared load (measured:
-// c3 366 -> 358 us per generation, c2 10.05 -> 9.93 us, against forming them every pass).
+// only on the elite's 8 alleles: kernels built with kSegDelta form them once per segment
+// (four delta_pair words) into this per-thread slot, and a pass reads them with one 16-byte
+// shared load instead of forming them (see ring_segment for where it pays).
 __shared__ uint4 s_delta[kThreads];
 
 // kSegDelta: form the rule R1 delta words of the segment (s_delta).
-template <bool kNarrow, bool kCip, bool kSegDelta = true>
+template <bool kNarrow, bool kCip, bool kSegDelta = false>
 __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int tile, int v_in,
                                           int tile_vecs, const uint8_t *elite_row)
 {
@@ -472,7 +472,7 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
 // needed, and the state is unchanged (fixed = true: the caller skips its store). The test
 // is skipped for 15 passes after it fails, which keeps its cost low while the population
 // is still spread out.
-template <bool kNarrow, int kRule, bool kCip, class Keys, bool kSegDelta = true>
+template <bool kNarrow, int kRule, bool kCip, class Keys, bool kSegDelta = false>
 __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys, const SegCtx &g, uint4 s,
                                             uint32_t xo, int32_t c, int32_t t,
                                             const unsigned char *thr_bytes, bool &fixed,
@@ -735,9 +735,11 @@ __device__ __forceinline__ void cp_async_wait()
 
 // One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation. kS8:
 // the state is stored as bytes (copied 8 bytes per pass, widened to 16-bit lanes).
-// kSegDelta: rule R1 deltas formed once per segment (the batched kernel, whose segments are
-// many and short, forms them every pass: measured 4,592 vs 4,338 solves/s on c4).
-template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false, bool kSegDelta = true>
+// kSegDelta: rule R1 deltas formed once per segment into s_delta. The host selects it with
+// the segment queue (long segments): measured on c3 358 vs 364 us per generation; with
+// c2's short static segments it costs (9.99 vs 9.61 us), and the batched kernel, whose
+// segments are many and short, forms the deltas every pass (4,618 vs 4,338 solves/s on c4).
+template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false, bool kSegDelta = false>
 __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &keys, const BlockShare &b,
                                              int tile, int ra, int seg_rows, int32_t t,
                                              const uint8_t *x_prev, uint8_t *x_cur,
@@ -836,7 +838,7 @@ __device__ __forceinline__ void clear_row_sums(int seg_rows_max, uint32_t *s_acc
     __syncthreads();
 }
 
-template <bool kNarrow, int kRule, bool kCip, bool kS8 = false>
+template <bool kNarrow, int kRule, bool kCip, bool kS8 = false, bool kSegDelta = false>
 __device__ __forceinline__ void generation_body_ring(const GenParams &p, const BlockShare &b,
                                                      int32_t t, int32_t e_prev, uint4 *ring,
                                                      const uint32_t *s_thr, uint32_t *s_acc32,
@@ -854,9 +856,9 @@ __device__ __forceinline__ void generation_body_ring(const GenParams &p, const B
         const int ra = (int)(u0 - (int64_t)tile * p.np);
         const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
         u0 += seg_rows;
-        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8>(p, ParamKeys{p}, b, tile, ra, seg_rows, t, x_prev,
-                                                           x_cur, elite_row, thr_bytes, slots, s_acc32,
-                                                           s_acc64, countdown);
+        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta>(p, ParamKeys{p}, b, tile, ra, seg_rows, t,
+                                                                      x_prev, x_cur, elite_row, thr_bytes, slots,
+                                                                      s_acc32, s_acc64, countdown);
     }
 }
 
@@ -866,7 +868,7 @@ __device__ __forceinline__ void generation_body_ring(const GenParams &p, const B
 // empty while the others finish; taken from a queue in order of decreasing size, the
 // segments keep every block busy until the work runs out. Any split gives the same
 // results: each tile-row's sums are exact integers added once per segment.
-template <bool kNarrow, int kRule, bool kCip, bool kS8 = false>
+template <bool kNarrow, int kRule, bool kCip, bool kS8 = false, bool kSegDelta = false>
 __device__ __forceinline__ void generation_body_queue(const GenParams &p, const BlockShare &b,
                                                       int32_t t, int32_t e_prev, uint4 *ring,
                                                       const uint32_t *s_thr, uint32_t *s_acc32,
@@ -889,9 +891,9 @@ __device__ __forceinline__ void generation_body_queue(const GenParams &p, const 
         const int32_t qi = s_qi;
         if (qi >= p.nsegs) break;
         const int4 sg = __ldg(p.segq + qi);
-        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8>(p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t, x_prev,
-                                                           x_cur, elite_row, thr_bytes, slots, s_acc32,
-                                                           s_acc64, countdown);
+        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta>(p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t,
+                                                                      x_prev, x_cur, elite_row, thr_bytes, slots,
+                                                                      s_acc32, s_acc64, countdown);
     }
 }
 
@@ -1032,18 +1034,18 @@ __device__ __forceinline__ SmemParts carve_smem(unsigned char *raw)
 }
 
 // queued: take the segments from the instance's queue (deferred forms with a queue).
-template <bool kNarrow, int kRule, bool kCip, bool kRing, bool kS8 = false>
+template <bool kNarrow, int kRule, bool kCip, bool kRing, bool kS8 = false, bool kSegDelta = false>
 __device__ __forceinline__ void one_generation(const GenParams &p, const BlockShare &b, int32_t t,
                                                int32_t e_prev, SmemParts &m, const uint32_t *s_thr,
                                                bool queued = false)
 {
     if constexpr (kRing) {
         if (queued && p.nsegs > 0)
-            generation_body_queue<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32,
-                                                             m.acc64);
+            generation_body_queue<kNarrow, kRule, kCip, kS8, kSegDelta>(p, b, t, e_prev, m.ring, s_thr,
+                                                                        m.acc32, m.acc64);
         else
-            generation_body_ring<kNarrow, kRule, kCip, kS8>(p, b, t, e_prev, m.ring, s_thr, m.acc32,
-                                                            m.acc64);
+            generation_body_ring<kNarrow, kRule, kCip, kS8, kSegDelta>(p, b, t, e_prev, m.ring, s_thr,
+                                                                       m.acc32, m.acc64);
     } else {
         generation_body<kNarrow, kRule, kCip>(p, b, t, e_prev, s_thr, m.acc32, m.acc64);
     }
@@ -1189,7 +1191,7 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_k
 // Otherwise (elite by a scan of fitness[] when the fitness does not fit the key, or the
 // host DetermineElite variant): the last block to finish closes the generation.
 // ---------------------------------------------------------------------------------------
-template <bool kNarrow, int kRule, bool kRing, bool kS8 = false>
+template <bool kNarrow, int kRule, bool kRing, bool kS8 = false, bool kSegDelta = false>
 __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) generation_kernel(const GenParams p)
 {
     __shared__ uint32_t s_thr[kMaxThr];
@@ -1241,8 +1243,8 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) gener
             final_cip_body<kRule, kS8>(p, b, t - 1, e_prev);   // the CIP of the converged generation
             return;
         }
-        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing, kS8>(p, b, t, e_prev, m, s_thr, true);
-        else one_generation<kNarrow, kRule, false, kRing, kS8>(p, b, t, e_prev, m, s_thr, true);
+        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing, kS8, kSegDelta>(p, b, t, e_prev, m, s_thr, true);
+        else one_generation<kNarrow, kRule, false, kRing, kS8, kSegDelta>(p, b, t, e_prev, m, s_thr, true);
         allow_dependent_launch();
         return;
     }
