@@ -174,11 +174,13 @@ qieo_status qieo_get_threshold_table(qieo_instance *inst, uint64_t *t_out);
 /* Launch shape of the fused generation kernel. Results do not depend on it (all sums are
  * exact integers and every draw is keyed by gene, chromosome and generation). A row is cut
  * into tiles of lanes_per_row * warps_per_row vectors of 8 genes; a persistent grid of
- * grid_ctas blocks splits the ntile * np tile-rows into equal contiguous shares. */
+ * grid_ctas blocks covers the ntile * np tile-rows, in equal contiguous shares when a share
+ * is below 64 tile-rows, otherwise (runs with the packed elite key) by taking segments of
+ * decreasing size from a queue. */
 typedef struct {
     int32_t lanes_per_row;   /* 1, 2, 4, 8, 16 or 32 threads of a warp on one row tile */
     int32_t warps_per_row;   /* 1, 2, 4 or 8 warps on one row tile (lanes_per_row 32 only) */
-    int32_t grid_ctas;       /* thread blocks; 0 = one per resident slot of the device */
+    int32_t grid_ctas;       /* thread blocks; 0 = three per SM (or fewer if fewer fit) */
     int32_t narrow;          /* out: 1 when 16-bit packed item sums are in use */
     int32_t tiles;           /* out: gene tiles per row */
     int32_t rows_per_cta;    /* out: most tile-rows one block sums in shared memory at once */
