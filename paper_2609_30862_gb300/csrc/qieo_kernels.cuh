@@ -739,7 +739,10 @@ __device__ __forceinline__ void cp_async_wait()
 // the segment queue (long segments): measured on c3 358 vs 364 us per generation; with
 // c2's short static segments it costs (9.99 vs 9.61 us), and the batched kernel, whose
 // segments are many and short, forms the deltas every pass (4,618 vs 4,338 solves/s on c4).
-template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false, bool kSegDelta = false>
+// kUnroll2: the pass loop unrolled twice (the batched kernel: c4 4,692 vs 4,593 solves/s;
+// no gain for the single-instance kernels, c2 9.90 vs 9.70 us per generation).
+template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false, bool kSegDelta = false,
+          bool kUnroll2 = false>
 __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &keys, const BlockShare &b,
                                              int tile, int ra, int seg_rows, int32_t t,
                                              const uint8_t *x_prev, uint8_t *x_cur,
@@ -764,25 +767,19 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     // Incremental addressing (no multiplies in the pass loop): the copy cursor runs
     // kRingStages - 1 rows ahead of the compute cursor.
     const SV *ld_ptr = sptr;                    // next row to copy
-    int ld_rr = b.r_sub;                        // its row within the segment
-    uint32_t ld_slot = 0;                       // its slot
     SV *st_ptr = sptr;                          // row being computed
     uint8_t *xst_ptr = xptr;
     const uint8_t *xo_ptr = xoptr;
     int rr = b.r_sub;
-    uint32_t slot = 0;
-    auto issue = [&]() {
-        const bool v = g.active && ld_rr < seg_rows;
+    auto issue = [&](uint32_t stage, bool v) {
         if constexpr (kS8)
-            cp_async8(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
+            cp_async8(slots + (size_t)stage * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
                       v ? 8u : 0u);
         else
-            cp_async16(slots + (size_t)ld_slot * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
+            cp_async16(slots + (size_t)stage * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
                        v ? 16u : 0u);
         cp_async_commit();
         ld_ptr += sstep;
-        ld_rr += rpp;
-        ld_slot = (ld_slot + 1) & (kRingStages - 1);
     };
     auto load_xold = [&](const uint8_t *ptr, int r) -> uint32_t {
         if (kRule != 1 || !kCip) return 0u;
@@ -791,19 +788,21 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     };
 
 #pragma unroll
-    for (int k = 0; k < kRingStages - 1; ++k) issue();
+    for (int k = 0; k < kRingStages - 1; ++k) issue((uint32_t)k, g.active && b.r_sub + k * rpp < seg_rows);
+    const int lim = seg_rows - (kRingStages - 1) * rpp;
     uint32_t xa = load_xold(xo_ptr, rr), xb1 = load_xold(xo_ptr + xstep, rr + rpp);
+#pragma unroll(kUnroll2 ? 2 : 1)
     for (int pass = 0; pass < passes; ++pass) {
-        issue();
+        issue((uint32_t)(pass + kRingStages - 1) & (kRingStages - 1), g.active && rr < lim);
         const uint32_t xo = xa;
         xa = xb1;
         xb1 = load_xold(xo_ptr + 2 * xstep, rr + 2 * rpp);
         xo_ptr += xstep;
         cp_async_wait<kRingStages - 1>();
         uint4 sv;
+        const uint32_t slot = (uint32_t)pass & (kRingStages - 1);
         if constexpr (kS8) sv = unpack8(*reinterpret_cast<const uint2 *>(slots + (size_t)slot * kThreads));
         else sv = slots[(size_t)slot * kThreads];
-        slot = (slot + 1) & (kRingStages - 1);
 
         const bool ok = rr < seg_rows;
         uint32_t xbits, accn;
@@ -1613,7 +1612,7 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
         if (stop == kStopPending)            // the CIP of the generation that converged
             rotate_segment<kRule>(p, b, sg.tile, sg.ra, sg.rows, t - 1, e_prev);
         else
-            ring_segment<kNarrow, kRule, kCip, InlineKeys, false, false>(
+            ring_segment<kNarrow, kRule, kCip, InlineKeys, false, false, true>(
                 p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra, sg.rows, t, x_prev, x_cur,
                 x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots, m.acc32, m.acc64, countdown);
         // the block that finishes an instance's last segment closes its generation (barrier
