@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import platform
 import os
 import re
 import statistics
@@ -68,6 +69,9 @@ def parse():
                     help="--sweep: skip pairs whose instance needs more device memory")
     ap.add_argument("--ref-budget-s", type=float, default=150.0,
                     help="--impl reference: seconds of oracle work over warm-up + timed steps")
+    ap.add_argument("--oracle-scan", action="store_true",
+                    help="the oracle's rate on --workload at 1 thread (serial build) and at 1, 8, "
+                         "16 and all threads (OpenMP build), on the host cores")
     return ap.parse_args()
 
 
@@ -210,6 +214,34 @@ def oracle_sample(name: str, target_s: float = 10.0):
     sample = "first %d of %d generations of %s (Np=%d, Ng=%d), OpenMP build, %d threads" % (
         gens, c["gens"], name, c["np"], c["ng"], cores)
     return rate, cores, sample, gens, dt
+
+
+def run_oracle_scan(a):
+    """The oracle, as it stands, on the host cores: its serial build and its OpenMP build
+    (parallel over chromosomes, the same results) at 1, 8, 16 and all threads, each over
+    the first generations of the workload that fill about 8 seconds. One JSON line."""
+    from oracle import oracle as O
+    name = a.workload if a.workload in WL.WORKLOADS else "c2"
+    c = WL.WORKLOADS[name]
+    prob = WL.knapsack(c["ng"], c["item_seed"])
+    O.build()
+    cores = os.cpu_count() or 1
+    runs = [("serial", 1)] + [("omp", n) for n in sorted({1, 8, 16, cores}) if n <= cores]
+    out = []
+    for kind, n in runs:
+        if kind == "omp":
+            O.set_threads(n)
+        t0 = time.perf_counter()
+        O.run(prob, c["np"], 1, seed=c["seed"], inst=c["inst"], kind=kind, threads=n)
+        t1 = time.perf_counter() - t0
+        gens = int(max(1, min(c["gens"], round(8.0 / max(t1, 1e-6)))))
+        t0 = time.perf_counter()
+        O.run(prob, c["np"], gens, seed=c["seed"], inst=c["inst"], kind=kind, threads=n)
+        dt = time.perf_counter() - t0
+        out.append({"build": kind, "threads": n, "generations": gens, "seconds": round(dt, 3),
+                    "gene_updates_per_s": c["np"] * c["ng"] * gens / dt})
+    print(json.dumps({"oracle_scan": name, "np": c["np"], "ng": c["ng"], "host_cores": cores,
+                      "cpu": platform.processor() or platform.machine(), "runs": out}), flush=True)
 
 
 def run_reference(a):
@@ -878,6 +910,8 @@ def run_sweep(a):
 
 def main():
     a = parse()
+    if a.oracle_scan:
+        return run_oracle_scan(a)
     if a.impl != "reference" and a.sweep:
         run_sweep(a)
         return

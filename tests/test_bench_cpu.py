@@ -1,6 +1,6 @@
 """bench.py's host logic without a GPU: the max-over-ranks reduction under world size 2
 (gloo), and the reference arm under torchrun with two ranks (rank 0 prints one JSON line,
-rank 1 exits 0 without output)."""
+rank 1 exits 0 without output), and the oracle thread scan."""
 import json
 import os
 import socket
@@ -59,3 +59,20 @@ def test_reference_arm_under_torchrun_two_ranks(workload, unit):
     assert d["n_gpus"] == 2 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_oracle_scan_on_host_cores():
+    """--oracle-scan: the oracle's serial build and its OpenMP build at 1, 8, 16 and all
+    threads (those the host has), one JSON line with a positive rate per run."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-scan", "--workload", "c1"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    cores = os.cpu_count() or 1
+    assert d["oracle_scan"] == "c1" and d["host_cores"] == cores
+    got = [(x["build"], x["threads"]) for x in d["runs"]]
+    assert got[0] == ("serial", 1)
+    assert got[1:] == [("omp", n) for n in sorted({1, 8, 16, cores}) if n <= cores]
+    assert all(x["gene_updates_per_s"] > 0 and x["generations"] >= 1 for x in d["runs"])
