@@ -79,6 +79,26 @@ def test_philox_matches_pytorch_header(oracle_mod):
         assert [int(x) for x in got] == [int(x) for x in want], row
 
 
+def read_philox_kat():
+    """The published Philox4x32-10 known-answer vectors (tests/golden)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                rows.append((w[:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answers(oracle_mod):
+    """The three known-answer vectors published with Philox4x32-10."""
+    rows = read_philox_kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        assert [int(x) for x in oracle_mod.philox4x32_10(ctr, key)] == want
+
+
 def test_philox_uniform_bytes(oracle_mod):
     """Chi-square on the bytes of 16k Philox words: no bias at the 1e-6 level."""
     out = np.concatenate([oracle_mod.philox4x32_10([i, 7, 3, 0], [1, 0]) for i in range(4096)])
