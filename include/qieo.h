@@ -225,8 +225,8 @@ qieo_status qieo_checkpoint_load(qieo_instance *inst, const void *buffer, size_t
 qieo_status qieo_get_convergence(qieo_instance *inst, int32_t *stopped, int32_t *stable);
 
 /* A batch: many instances advanced together, one persistent kernel launch per generation
- * for all of them (survey-level "batching" of independent QIEO solves; the paper runs one
- * problem at a time). The instances keep their own state, records and generation
+ * for all of them (batching of independent QIEO solves; the paper runs one problem at a
+ * time). The instances keep their own state, records and generation
  * counters; qieo_batch_run(b, G) is equivalent to qieo_run(inst, G) on every member, bit for
  * bit. The work of a generation (every member's tiles of rows) is cut into segments
  * balanced over a grid of one block per resident slot; members are grouped by item-sum
