@@ -456,9 +456,13 @@ def run_gpu(a):
                        else "state larger than L2 (no flush)",
                        parallelism="one independent instance per GPU",
                        launch_shape="%d lanes x %d warps per row tile, %d tiles per row, "
-                                    "%d persistent blocks, <= %d tile-rows per block, %s" % (
+                                    "%d persistent blocks, %s, %s" % (
                            shape.lanes_per_row, shape.warps_per_row, shape.tiles,
-                           shape.grid_ctas, shape.rows_per_cta,
+                           shape.grid_ctas,
+                           # the library queues segments when a block's share is >= 64 rows
+                           ("segments of decreasing size (<= %d tile-rows) from a queue"
+                            % shape.rows_per_cta) if shape.rows_per_cta >= 64
+                           else "equal static shares of <= %d tile-rows" % shape.rows_per_cta,
                            "one cooperative launch per run" if shape.persistent
                            else "one launch per generation")),
         "roofline": roof,
