@@ -7,7 +7,7 @@ final CIP (a5). The metric is gene-updates/s = Np * Ng * generations / time, sum
 all ranks (each rank solves its own independent instance: weak scaling, no collective on
 the data path).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1]
   python bench.py --workload c4           # 256 uneven instances, batched (solves/s)
   python bench.py --workload c5           # served Poisson stream (solves/s, p50/p99)
   python bench.py --impl reference ...    # the CPU oracle timed on the host cores
@@ -35,13 +35,12 @@ from paper_2609_30862_gb300 import workload as WL  # noqa: E402
 METRIC = "gene-updates/s (Np*Ng*gens) & % roofline"
 UNIT = "gene-updates/s"
 SM_COUNT = 152
-LANES_PER_SM = 128
-# Integer operations per gene-update that the method itself needs:
-# Philox4x32-10 = 10 rounds x (2 wide multiplies + 2 three-input xors) per 4 genes = 10,
-# CIP (packed add/max/sub/min on 2 genes) = 2, observation (index extract + compare) = 2,
-# evaluation (packed item add) = 1, allele packing = 1.
-ALU_OPS_PER_GENE = 16
 STATE_BYTES_PER_GENE = 4          # int16 angle index read + written once per generation
+# Generations whose single-launch times represent the two phases of a run of the
+# HBM-resident instance: every qubit still drawn (the population spread) and every qubit
+# saturated on the elite's side (fixed-allele passes).
+SPREAD_WINDOW = (45, 55)
+SATURATED_WINDOW = (185, 195)
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -51,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WL.WORKLOADS) + ["c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WL.WORKLOADS) + ["c4", "c5"])
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--rate", type=float, default=0.0,
                     help="c5 arrivals per second (0: 0.8 x the measured batched capacity)")
@@ -60,6 +59,8 @@ def parse():
                     help="c1-c3: store the angle indices as bytes (QIEO_FLAG_STATE_I8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-phases", action="store_true",
+                    help="c1-c3: skip the per-generation timing run and the integer ceiling")
     ap.add_argument("--phases", action="store_true",
                     help="per-step breakdown (CIP, QIP, Evaluation, DetermineElite) of the "
                          "unfused form, and device vs host DetermineElite, on --workload")
@@ -397,34 +398,50 @@ def run_gpu(a):
 
     # Roofline of the fused generation kernel. A run is G launches of generation_kernel +
     # one final CIP launch, timed with events on its stream; the per-generation duration is
-    # that time / G (an upper bound on one launch: it includes the CIP pass and the gaps). Bound: the slower of the state bytes at the
-    # measured HBM bandwidth (4 B/gene-update) and the integer work at the derived ALU peak
-    # (16 ops/gene-update); for these workloads the state bytes are the slower one.
+    # that time / G (an upper bound on one launch: it includes the CIP pass and the gaps).
+    # Per gene-update the kernel moves 4 B of state (int16 read + written) and does the
+    # drawn pass's integer work (a quarter Philox4x32-10 call, CIP, the compare, the allele
+    # bit, the item sums); its two ceilings are the measured HBM copy bandwidth and the
+    # measured integer ceiling (qieo_measure_integer_ceiling, the same per-gene arithmetic
+    # with nothing streamed), and the bound is the slower of the two.
     launch_s = run_total_ms / 1e3 / (a.steps * G)
     peaks, peak_src = load_peaks()
     genes_per_launch = np_ * ng
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * LANES_PER_SM * max_mhz * 1e6 / 1e12
     hbm_peak = float(peaks["hbm_gbs"])
     state_bpg = 2 if a.state_i8 else STATE_BYTES_PER_GENE   # byte state: 1 B read + 1 B written
     t_hbm = state_bpg * genes_per_launch / (hbm_peak * 1e9)
-    t_alu = ALU_OPS_PER_GENE * genes_per_launch / (alu_peak * 1e12)
+    ceiling = None if a.no_phases else Q.qieo_measure_integer_ceiling(5)
+    int_peak = ceiling.drawn_genes_per_s if ceiling is not None else None
+    t_int = genes_per_launch / int_peak if int_peak else 0.0
     l2_resident = state_bytes < L2_BYTES
-    if t_hbm >= t_alu:
-        achieved = state_bpg * genes_per_launch / launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src}
+    hbm_achieved = state_bpg * genes_per_launch / launch_s / 1e9
+    if t_hbm >= t_int:
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src}
     else:
-        achieved = ALU_OPS_PER_GENE * genes_per_launch / launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak,
-                "peak_source": "derived: %d SMs x %d int32 lanes x %.0f MHz" % (
-                    SM_COUNT, LANES_PER_SM, max_mhz)}
+        achieved = genes_per_launch / launch_s / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": int_peak / 1e9,
+                "unit": "Ggene-updates/s", "frac": achieved / (int_peak / 1e9),
+                "peak_source": "measured: qieo_measure_integer_ceiling (the drawn pass's per-gene "
+                               "integer work, state in registers, %d blocks, best of %d)" % (
+                                   ceiling.grid_ctas, ceiling.reps)}
+    roof["frac_hbm_4B_formula"] = hbm_achieved / hbm_peak
+    roof["hbm_peak_gbs"] = hbm_peak
+    if int_peak:
+        roof["int_ceiling_gene_updates_per_s"] = int_peak
+        roof["philox_only_gene_updates_per_s"] = ceiling.philox_genes_per_s
+        roof["t_hbm_us"] = t_hbm * 1e6
+        roof["t_int_us"] = t_int * 1e6
     roof["state_in_l2"] = l2_resident
     roof["traffic"] = None if a.state_i8 else profile_traffic("generation_kernel", a.workload)
+    if roof["traffic"]:
+        roof["frac_dram_measured"] = roof["traffic"] / launch_s / 1e9 / hbm_peak
     roof["kernel"] = ("run_kernel (one cooperative launch per run)" if shape.persistent
                       else "generation_kernel (one launch per generation)")
     roof["us_per_generation"] = launch_s * 1e6
+    if not a.no_phases and not shape.persistent:
+        roof["phases"] = generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch,
+                                           hbm_peak, int_peak)
 
     # end to end through the C ABI with host buffers: create (uploads the items), run,
     # read the best record back, destroy -- every step
@@ -487,6 +504,42 @@ def run_gpu(a):
         dist.barrier()
         dist.destroy_process_group()
     return np
+
+
+def generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch, hbm_peak, int_peak):
+    """Device time of every generation of one run (QIEO_FLAG_TIME_GENERATIONS: an event
+    before each launch, so each time is that launch alone), summarised per window of 25
+    generations and for the two phase windows. Run after the timed region."""
+    import numpy as np
+    ng = c["ng"]
+    with torch.cuda.stream(stream):
+        inst = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank, stream=stream.cuda_stream,
+                          flags=flags | Q.QIEO_FLAG_TIME_GENERATIONS)
+        inst.run(G)                        # warm-up run
+        inst.reset()
+        inst.run(G)
+        ms = inst.generation_times(G)
+        inst.close()
+    genes = np_ * ng
+
+    def window(lo, hi):
+        lo, hi = min(lo, len(ms)), min(hi, len(ms))
+        if hi <= lo:
+            return None
+        us = 1e3 * float(np.mean(ms[lo:hi]))
+        rate = genes / (us * 1e-6)
+        out = {"generations": "%d-%d" % (lo, hi - 1), "us_per_generation": us,
+               "gene_updates_per_s": rate,
+               "frac_hbm_4B_formula": STATE_BYTES_PER_GENE * rate / 1e9 / hbm_peak}
+        if int_peak:
+            out["frac_int_ceiling"] = rate / int_peak
+        return out
+
+    step = 25
+    return {"spread": window(*SPREAD_WINDOW), "saturated": window(*SATURATED_WINDOW),
+            "per_25": [round(1e3 * float(np.mean(ms[i:i + step])), 2) for i in range(0, len(ms), step)],
+            "sum_of_launches_us": 1e3 * float(np.sum(ms)),
+            "what": "CUDA events before every generation launch of one run (launches serialised)"}
 
 
 def batch_oracle_sample(specs, G: int, target_s: float = 10.0):

@@ -97,6 +97,15 @@ typedef struct {
                                          QIEO_FLAG_REGISTER_PREFETCH, QIEO_FLAG_COOPERATIVE,
                                          QIEO_FLAG_UNFUSED or QIEO_FLAG_FORCE_WIDE, and not in
                                          batches */
+#define QIEO_FLAG_TIME_GENERATIONS 0x400 /* record a CUDA event before every generation
+                                            launch of a run and after the last one, so that
+                                            qieo_get_generation_times can report each
+                                            generation's device time (one launch per
+                                            generation, no CUDA graph; the events keep
+                                            consecutive launches from overlapping, so each
+                                            time is the launch alone). Not with
+                                            elite_on_host, QIEO_FLAG_COOPERATIVE or
+                                            QIEO_FLAG_UNFUSED */
 
 typedef struct {
     int32_t np;              /* chromosomes, >= 1 */
@@ -195,6 +204,35 @@ qieo_status qieo_set_launch_shape(qieo_instance *inst, const qieo_launch_shape *
 /* Accumulated device time of the generation kernels (QIEO_FLAG_TIME_KERNELS) and the
  * number of generation-kernel launches it covers; qieo_reset clears neither. */
 qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launches);
+
+/* Device time of each generation of the last run of an instance created with
+ * QIEO_FLAG_TIME_GENERATIONS: ms_out[i] = the time (ms, CUDA events on the instance's
+ * stream) from the start of the launch of the run's generation i to the start of the next
+ * launch (for the last generation: to its end), for i < min(n, generations of that run);
+ * *count = that number. Waits (bounded) for the run to finish. The times cover one fused
+ * generation kernel each (CIP of the generation before, QIP, Evaluation, DetermineElite);
+ * the run's final CIP launch is not included. QIEO_ERR_INVALID without the flag. */
+qieo_status qieo_get_generation_times(qieo_instance *inst, int32_t n, float *ms_out, int32_t *count);
+
+/* Measured integer ceiling of the generation kernel's per-gene work (a roofline bound
+ * next to the state's 4 bytes of memory traffic per gene-update). Runs, on the current
+ * device, (a) the per-gene arithmetic of the kernel's drawn pass -- CIP of the angle
+ * indices, two Philox4x32-10 calls per 8 genes, the threshold compares, the allele bits and
+ * the packed item sums, with the kernel's own device helpers, D = 100 -- with the state in
+ * registers and nothing streamed, and (b) Philox4x32-10 alone, each in the generation
+ * kernel's launch shape (256 threads, three blocks per SM), reps timed launches after one
+ * warm-up launch (CUDA events; the best is kept). Allocates and frees a small device
+ * buffer and a stream of its own; synchronous. QIEO_ERR_INVALID for reps outside
+ * [1, 1000]. */
+typedef struct {
+    double drawn_genes_per_s;    /* (a): gene-updates per second */
+    double philox_genes_per_s;   /* (b): genes per second at a quarter call per gene */
+    int64_t genes_per_launch;
+    int32_t grid_ctas;
+    int32_t reps;
+} qieo_integer_ceiling;
+
+qieo_status qieo_measure_integer_ceiling(int32_t reps, qieo_integer_ceiling *out);
 
 /* Accumulated time per step of a generation, ms[4] = {CIP, QIP, Evaluation,
  * DetermineElite}, and the number of generations it covers. Filled by runs with

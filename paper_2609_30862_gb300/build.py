@@ -1,7 +1,7 @@
 """In-tree build of the CUDA library (libqieo.so) for sm_103a with nvcc.
 
-One translation unit, one -gencode: the library is rebuilt when a source or the public
-header is newer than the shared object.
+One -gencode; the translation units compile in parallel and are linked into one shared
+object. The library is rebuilt when a source or the public header is newer than it.
 """
 from __future__ import annotations
 
@@ -42,15 +42,31 @@ def stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit to an object in parallel, then link the library."""
     if not force and not stale():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17",
-           "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           *(["-Xptxas", "-v"] if verbose else []), *sources(), "-o", tmp]
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = "%d" % os.getpid()
+    common = [nvcc(), "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+              *(["-Xptxas", "-v"] if verbose else [])]
+    objs = [os.path.join(BUILD, os.path.basename(src)[:-3] + ".%s.o" % tag) for src in sources()]
+
+    def compile_one(pair):
+        src, obj = pair
+        subprocess.check_call(common + ["-c", src, "-o", obj])
+
+    try:
+        with ThreadPoolExecutor(max_workers=max(1, len(objs))) as ex:
+            list(ex.map(compile_one, zip(sources(), objs)))
+        tmp = LIB + ".tmp" + tag
+        subprocess.check_call([nvcc(), "-gencode", GENCODE, "-shared", *objs, "-o", tmp])
+        os.replace(tmp, LIB)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 

@@ -148,6 +148,11 @@ struct qieo_instance {
     std::vector<cudaEvent_t> phase_ev;
     double phase_ms[4] = {0.0, 0.0, 0.0, 0.0};
     int64_t phase_gens = 0;
+
+    // per-generation timing (QIEO_FLAG_TIME_GENERATIONS): gen_ev[i] is recorded before the
+    // launch of the last run's generation i, gen_ev[gen_ev_n] after its last launch
+    std::vector<cudaEvent_t> gen_ev;
+    int32_t gen_ev_n = 0;
 };
 
 namespace {
@@ -525,6 +530,15 @@ void build_thresholds(int32_t D, std::vector<uint64_t> &T)
     for (int32_t n = K + 1; n <= 2 * K; ++n) T[(size_t)n] = (1ull << 32) - T[(size_t)(2 * K - n)];
 }
 
+}  // namespace
+
+namespace qieo_internal {
+// The threshold table for the library's other translation units.
+void build_thresholds(int32_t D, std::vector<uint64_t> &T) { ::build_thresholds(D, T); }
+}  // namespace qieo_internal
+
+namespace {
+
 qieo_status ensure_history(qieo_instance *q, int32_t need)
 {
     if (need <= q->hist_cap) return QIEO_OK;
@@ -564,7 +578,23 @@ qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
     // Deferred close whenever the elite key holds the fitness (the generation counter then
     // advances once per run); otherwise the last block of each generation closes it.
     const bool deferred = q->key_ok;
-    for (int32_t g = 0; g < G; ++g) CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 1, deferred ? g : -1));
+    const bool per_gen = (q->flags & QIEO_FLAG_TIME_GENERATIONS) != 0;
+    if (per_gen) {
+        while (q->gen_ev.size() < (size_t)G + 1) {
+            cudaEvent_t e = nullptr;
+            CUDA_TRY(cudaEventCreate(&e));
+            q->gen_ev.push_back(e);
+        }
+        q->gen_ev_n = 0;
+    }
+    for (int32_t g = 0; g < G; ++g) {
+        if (per_gen) CUDA_TRY(cudaEventRecord(q->gen_ev[(size_t)g], q->stream));
+        CUDA_TRY(launch_gen(q, g > 0 ? 1 : 0, 1, deferred ? g : -1));
+    }
+    if (per_gen) {
+        CUDA_TRY(cudaEventRecord(q->gen_ev[(size_t)G], q->stream));
+        q->gen_ev_n = G;
+    }
     if (q->flags & QIEO_FLAG_TIME_KERNELS) CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
     CUDA_TRY(launch_final_cip(q, deferred ? G : 0));
     return QIEO_OK;
@@ -577,7 +607,8 @@ qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
 // slower). Not with the convergence test or byte state.
 bool use_cooperative(const qieo_instance *q)
 {
-    if (!q->coop || q->host_de || (q->flags & (QIEO_FLAG_UNFUSED | QIEO_FLAG_PER_GENERATION)))
+    if (!q->coop || q->host_de ||
+        (q->flags & (QIEO_FLAG_UNFUSED | QIEO_FLAG_PER_GENERATION | QIEO_FLAG_TIME_GENERATIONS)))
         return false;
     if (q->flags & QIEO_FLAG_COOPERATIVE) return true;
     return q->key_ok && !(q->flags & QIEO_FLAG_CONVERGE) && !q->state8 &&
@@ -613,7 +644,7 @@ qieo_status run_device(qieo_instance *q, int32_t G)
     if (use_cooperative(q)) return run_cooperative(q, G);
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
-    if ((q->flags & QIEO_FLAG_NO_GRAPH) || (first_time && !q->graphs.count(G))) {
+    if ((q->flags & (QIEO_FLAG_NO_GRAPH | QIEO_FLAG_TIME_GENERATIONS)) || (first_time && !q->graphs.count(G))) {
         qieo_status st = enqueue_device_run(q, G);
         if (st != QIEO_OK) return st;
     } else {
@@ -862,6 +893,10 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
         return fail(QIEO_ERR_INVALID, "QIEO_FLAG_STATE_I8 needs dtheta_den <= 120 and excludes "
                     "QIEO_FLAG_REGISTER_PREFETCH, QIEO_FLAG_COOPERATIVE, QIEO_FLAG_UNFUSED and "
                     "QIEO_FLAG_FORCE_WIDE");
+    if ((pa->flags & QIEO_FLAG_TIME_GENERATIONS) &&
+        (pa->elite_on_host || (pa->flags & (QIEO_FLAG_COOPERATIVE | QIEO_FLAG_UNFUSED))))
+        return fail(QIEO_ERR_INVALID, "QIEO_FLAG_TIME_GENERATIONS excludes elite_on_host, "
+                    "QIEO_FLAG_COOPERATIVE and QIEO_FLAG_UNFUSED");
     if ((pa->flags & QIEO_FLAG_CONVERGE) &&
         (pa->elite_on_host || (pa->flags & (QIEO_FLAG_COOPERATIVE | QIEO_FLAG_UNFUSED))))
         return fail(QIEO_ERR_INVALID, "QIEO_FLAG_CONVERGE excludes elite_on_host, QIEO_FLAG_COOPERATIVE "
@@ -1068,6 +1103,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
     for (cudaEvent_t e : q->phase_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : q->gen_ev) cudaEventDestroy(e);
     if (q->own_stream && q->stream) {
         cudaStreamSynchronize(q->stream);   // the block's release is ordered on it
         cudaStreamDestroy(q->stream);
@@ -1313,6 +1349,24 @@ qieo_status qieo_get_kernel_time(qieo_instance *q, double *ms, int64_t *launches
     if (st != QIEO_OK) return st;
     if (ms) *ms = q->kernel_ms;
     if (launches) *launches = q->kernel_launches;
+    return QIEO_OK;
+}
+
+qieo_status qieo_get_generation_times(qieo_instance *q, int32_t n, float *ms_out, int32_t *count)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!(q->flags & QIEO_FLAG_TIME_GENERATIONS))
+        return fail(QIEO_ERR_INVALID, "the instance was not created with QIEO_FLAG_TIME_GENERATIONS");
+    if (n < 0 || (n > 0 && !ms_out)) return fail(QIEO_ERR_INVALID, "n must be >= 0 with room in ms_out");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    st = wait_stream(q->stream);
+    if (st != QIEO_OK) return st;
+    const int32_t m = std::min(n, q->gen_ev_n);
+    for (int32_t i = 0; i < m; ++i)
+        CUDA_TRY(cudaEventElapsedTime(ms_out + i, q->gen_ev[(size_t)i], q->gen_ev[(size_t)i + 1]));
+    if (count) *count = m;
     return QIEO_OK;
 }
 

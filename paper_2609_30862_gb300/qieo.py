@@ -35,6 +35,7 @@ QIEO_FLAG_CONVERGE = 0x80
 QIEO_CONVERGE_WINDOW = 20
 QIEO_FLAG_STATE_I8 = 0x100
 QIEO_FLAG_PER_GENERATION = 0x200
+QIEO_FLAG_TIME_GENERATIONS = 0x400
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
@@ -43,7 +44,8 @@ EXPORTS = (
     "qieo_get_state", "qieo_get_fitness",
     "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
-    "qieo_get_phase_times", "qieo_get_convergence", "qieo_checkpoint_size",
+    "qieo_get_phase_times", "qieo_get_generation_times", "qieo_measure_integer_ceiling",
+    "qieo_get_convergence", "qieo_checkpoint_size",
     "qieo_checkpoint_save", "qieo_checkpoint_load", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
     "qieo_run_batch", "qieo_autotune", "qieo_server_create", "qieo_server_submit", "qieo_server_poll",
@@ -84,6 +86,11 @@ class qieo_launch_shape(C.Structure):
 
 class qieo_server_config(C.Structure):
     _fields_ = [("memory_bytes", C.c_int64), ("max_active", C.c_int32), ("gens_per_step", C.c_int32)]
+
+
+class qieo_integer_ceiling(C.Structure):
+    _fields_ = [("drawn_genes_per_s", C.c_double), ("philox_genes_per_s", C.c_double),
+                ("genes_per_launch", C.c_int64), ("grid_ctas", C.c_int32), ("reps", C.c_int32)]
 
 
 class qieo_server_stats(C.Structure):
@@ -135,6 +142,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_set_launch_shape": ([P, P], C.c_int),
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
         "qieo_get_phase_times": ([P, P, P], C.c_int),
+        "qieo_get_generation_times": ([P, i32, P, P], C.c_int),
+        "qieo_measure_integer_ceiling": ([i32, P], C.c_int),
         "qieo_get_convergence": ([P, P, P], C.c_int),
         "qieo_checkpoint_size": ([P, P], C.c_int),
         "qieo_checkpoint_save": ([P, P, C.c_size_t], C.c_int),
@@ -292,6 +301,19 @@ def qieo_get_kernel_time(h):
     ms, n = C.c_double(), C.c_int64()
     _check(load().qieo_get_kernel_time(h, C.byref(ms), C.byref(n)))
     return float(ms.value), int(n.value)
+
+
+def qieo_get_generation_times(h, n: int) -> np.ndarray:
+    ms = np.zeros(max(0, int(n)), dtype=np.float32)
+    cnt = C.c_int32()
+    _check(load().qieo_get_generation_times(h, int(n), _ptr(ms), C.byref(cnt)))
+    return ms[:cnt.value]
+
+
+def qieo_measure_integer_ceiling(reps: int = 5) -> qieo_integer_ceiling:
+    out = qieo_integer_ceiling()
+    _check(load().qieo_measure_integer_ceiling(int(reps), C.byref(out)))
+    return out
 
 
 def qieo_philox(ctr_key) -> np.ndarray:
@@ -525,6 +547,9 @@ class Instance:
 
     def kernel_time(self):
         return qieo_get_kernel_time(self.h)
+
+    def generation_times(self, n: int) -> np.ndarray:
+        return qieo_get_generation_times(self.h, n)
 
     def phase_times(self):
         return qieo_get_phase_times(self.h)
