@@ -561,6 +561,17 @@ def batch_oracle_sample(specs, G: int, target_s: float = 10.0):
         done, G, cores)
 
 
+def member_result(inst):
+    """A member's result after a run, for comparing two arms: its best record and alleles,
+    its generation counter and a digest of its final angle indices and fitness."""
+    import hashlib
+    bits, bf, bg, bc = inst.best()
+    k, t = inst.state()
+    h = hashlib.sha256(k.tobytes())
+    h.update(inst.fitness().tobytes())
+    return (bf, bg, bc, t, bits.tobytes(), h.hexdigest())
+
+
 def run_batched(a):
     """c4: 256 independent instances (Ng log-uniform in [50, 20000], Np uniform in
     {32..512}, seeds 1..256), 300 generations each. One step = reset + 300 generations of
@@ -633,6 +644,7 @@ def run_batched(a):
         # one launch sequence per instance, same members and results
         single_steps = max(1, a.steps // 5)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        batched_out = [member_result(i) for i in insts]
         barrier()
         ev[0].record(stream)
         for _ in range(single_steps):
@@ -642,7 +654,9 @@ def run_batched(a):
         ev[1].record(stream)
         barrier()
         ts = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, dist)
-        ok = all(i.best()[1] >= 0 for i in insts)
+        single_out = [member_result(i) for i in insts]
+        same = sum(1 for x, y in zip(batched_out, single_out) if x == y)
+        ok = same == len(insts)
     batch.close()
     for i in insts:
         i.close()
@@ -704,6 +718,10 @@ def run_batched(a):
                                     "gene_updates_per_s": world * genes * single_steps / ts},
         "speedup_vs_one_launch_per_instance": (n * a.steps / tb) / (n * single_steps / ts),
         "autotune_s": tune_s, "records_ok": ok,
+        "results_identical": {"checked": n, "equal": same,
+                              "what": "per member: best record, best alleles, generation counter and a "
+                                      "SHA-256 of the final angle indices and fitness, batched arm vs "
+                                      "one launch sequence per instance"},
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rate, cores, sample = batch_oracle_sample(specs, G)
@@ -766,7 +784,8 @@ def run_served(a):
         if delay > 0:
             time.sleep(delay)
         ids.append(srv.submit(probs[i], sp.np_, G, seed=sp.seed, inst=sp.seed))
-    results = [srv.poll(rid, wait_ms=600000)[0] for rid in ids]
+    polled = [srv.poll(rid, wait_ms=600000) for rid in ids]
+    results = [r for r, _ in polled]
     clocks = sampler.stop()
     assert all(r.state == Q.QIEO_SOLVE_DONE for r in results)
     lat = [r.done_s - r.submit_s for r in results]
@@ -777,7 +796,7 @@ def run_served(a):
 
     # serial per-request launches: one instance at a time, in arrival order
     m = min(n, max(200, n // 10))
-    lat_s = []
+    lat_s, solo = [], []
     t_start = time.perf_counter()
     for i in range(m):
         now = time.perf_counter() - t_start
@@ -785,9 +804,13 @@ def run_served(a):
             time.sleep(arrivals[i] - now)
         with Q.Instance(probs[i], specs[i].np_, seed=specs[i].seed, inst=specs[i].seed) as inst:
             inst.run(G)
-            inst.best()
+            solo.append(inst.best())
         lat_s.append(time.perf_counter() - t_start - arrivals[i])
     serial = latency_stats(lat_s, time.perf_counter() - t_start)
+    # identical results: every request the serial arm ran, served vs alone
+    same = sum(1 for i in range(m)
+               if (results[i].fitness, results[i].generation, results[i].chromosome) == tuple(solo[i][1:])
+               and np.array_equal(polled[i][1], solo[i][0]))
 
     genes = sum(sp.np_ * sp.ng for sp in specs) * G
     peaks, peak_src = load_peaks()
@@ -805,6 +828,10 @@ def run_served(a):
                    "l2": "arrival-driven: no flush (the resident set changes every step)"},
         "served": served,
         "serial_per_request": dict(serial, requests=m),
+        "results_identical": {"checked": m, "equal": same,
+                              "what": "best record and alleles of each request the serial arm ran, "
+                                      "served (in the mix) vs solved alone"},
+        "records_ok": same == m,
         "arrival_rate_per_s": rate,
         # the whole stream goes through the public API (submit from host arrays, poll the
         # result back), so value is itself end to end; the bytes are per request

@@ -173,6 +173,9 @@ qieo_status qieo_get_fitness(qieo_instance *inst, int64_t *f_out);
 /* Alleles observed in the last generation run (np*ng bytes of 0/1). */
 qieo_status qieo_get_alleles(qieo_instance *inst, uint8_t *x_out);
 
+/* The same for one chromosome c in [0, np) (ng bytes of 0/1); QIEO_ERR_INVALID otherwise. */
+qieo_status qieo_get_allele_row(qieo_instance *inst, int32_t c, uint8_t *x_out);
+
 /* Elite index and fitness of generations first .. first+n-1 (all < t). */
 qieo_status qieo_get_elite_history(qieo_instance *inst, int32_t first, int32_t n,
                                    int32_t *idx_out, int64_t *fit_out);
@@ -213,6 +216,41 @@ qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launc
  * generation kernel each (CIP of the generation before, QIP, Evaluation, DetermineElite);
  * the run's final CIP launch is not included. QIEO_ERR_INVALID without the flag. */
 qieo_status qieo_get_generation_times(qieo_instance *inst, int32_t n, float *ms_out, int32_t *count);
+
+/* Row blocks: one population sharded by chromosome rows (for example one block per GPU).
+ * A generation's QIP and Evaluation (Sec. III-B) are independent per chromosome, and every
+ * draw is keyed by the global chromosome index, so a block computes its rows exactly as
+ * the whole population would. DetermineElite (the lowest-index best chromosome) and CIP
+ * (toward the elite's alleles) need the whole population: the caller combines the blocks'
+ * best rows (for example an all-reduce MAX of a key ordering (fitness, -row), then a
+ * broadcast of the elite's alleles from the block that holds it) and passes the elite row
+ * to every block.
+ *
+ * qieo_create_row_block: params->np is the number of rows of this block, which holds the
+ * population's chromosomes row0 .. row0 + np - 1; the other params and the problem are
+ * those of the whole population. Same validation and errors as qieo_create_instance, and
+ * QIEO_ERR_INVALID for row0 < 0, elite_on_host, QIEO_FLAG_UNFUSED, QIEO_FLAG_COOPERATIVE,
+ * QIEO_FLAG_CONVERGE, or a problem whose fitness does not fit the packed elite key
+ * (lambda * sum(w) or sum(|v|) >= 2^39). A row block is destroyed, reset and read
+ * (qieo_get_state, _fitness, _alleles) like an instance; qieo_run and batches reject it.
+ *
+ * qieo_rows_observe: QIP and Evaluation of generation t (absolute; it keys the draws) on the
+ * block's current angle indices, without a rotation first; *best_fitness and *best_row
+ * receive the block's lowest-index maximum of eq. (1) (best_row is a global chromosome
+ * index). Waits (bounded) for the device. Either output may be NULL.
+ *
+ * qieo_rows_rotate: CIP of the block's rows after the generation last observed, toward the
+ * elite alleles elite_bits (host memory, ng bytes, each 0 or 1; copied before the call
+ * returns), by the instance's rotation rule (R2 compares each row's alleles of that
+ * generation). QIEO_ERR_INVALID when no generation was observed since creation or reset, or
+ * for a byte other than 0 or 1. Waits (bounded) for the device.
+ *
+ * Observing generations t0, t0 + 1, ... with a rotation toward the population's elite after
+ * each one reproduces qieo_run on the whole population bit for bit. */
+qieo_status qieo_create_row_block(const qieo_problem *problem, const qieo_params *params, int32_t row0,
+                                  qieo_instance **out);
+qieo_status qieo_rows_observe(qieo_instance *block, int32_t t, int64_t *best_fitness, int32_t *best_row);
+qieo_status qieo_rows_rotate(qieo_instance *block, const uint8_t *elite_bits);
 
 /* Measured integer ceiling of the generation kernel's per-gene work (a roofline bound
  * next to the state's 4 bytes of memory traffic per gene-update). Runs, on the current
@@ -384,10 +422,12 @@ qieo_status qieo_philox(const uint32_t *ctr_key, uint32_t *out, int32_t n);
  * instance_id, rotate_rule and stream (elite_on_host and flags are ignored); t is the
  * absolute generation number (it keys the Philox draws). k (np*ng int16, in/out) holds
  * the angle indices before the generation and receives them after its rotation; x
- * (np*ng uint8) receives the alleles, fitness (np int64) the eq. (1) values and elite (one
- * int32) the lowest-index best chromosome. All four are device pointers, row c =
- * chromosome c. Called with t = 0, 1, 2, ... on k starting at 0 it produces what
- * qieo_run(inst, 1) produces for each generation.
+ * (np*ng uint8) receives the alleles, fitness (np int64) the fitness values (penalised
+ * as in qieo_run) and elite (one int32) the lowest-index best chromosome. All four are
+ * device pointers, row c = chromosome c. Called with t = 0, 1, 2, ... on k starting at 0
+ * it produces what qieo_run(inst, 1) produces for each generation. Angle indices outside
+ * [-K, K] are invalid input: such an index is observed as the nearest bound, and its
+ * rotation step is taken only when the step lands inside [-K, K].
  *
  * Working memory: the per-chromosome sums and a block counter live in one file-scope
  * device array of 256 + 16 * QIEO_NOALLOC_MAX_NP bytes (about 1 MB) that every GPU which

@@ -153,6 +153,13 @@ struct qieo_instance {
     // launch of the last run's generation i, gen_ev[gen_ev_n] after its last launch
     std::vector<cudaEvent_t> gen_ev;
     int32_t gen_ev_n = 0;
+
+    // a row block of a population sharded by rows (qieo_create_row_block): its rows are
+    // chromosomes row0 .. row0 + np - 1 of the whole population; ext_elite holds the
+    // packed elite row passed to qieo_rows_rotate; rows_t is the generation last observed
+    bool row_block = false;
+    uint8_t *ext_elite = nullptr;
+    int32_t rows_t = -1;
 };
 
 namespace {
@@ -1099,6 +1106,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->hist_e && !q->fixed_history) cudaFreeAsync(q->hist_e, q->stream);
     if (q->hist_f && !q->fixed_history) cudaFreeAsync(q->hist_f, q->stream);
     if (q->segq) cudaFreeAsync(q->segq, q->stream);
+    if (q->ext_elite) cudaFreeAsync(q->ext_elite, q->stream);
     if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
@@ -1125,6 +1133,7 @@ qieo_status qieo_reset(qieo_instance *q)
                                                                (size_t)q->np * 2);
     CUDA_TRY(cudaGetLastError());
     q->t = 0;
+    q->rows_t = -1;
     if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
     return QIEO_OK;
 }
@@ -1134,6 +1143,8 @@ qieo_status qieo_run(qieo_instance *q, int32_t G)
     qieo_status st = check_inst(q);
     if (st != QIEO_OK) return st;
     if (G < 0) return fail(QIEO_ERR_INVALID, "generations must be >= 0 (got %d)", G);
+    if (q->row_block)
+        return fail(QIEO_ERR_INVALID, "a row block advances through qieo_rows_observe and qieo_rows_rotate");
     if (G == 0) return QIEO_OK;
     if ((int64_t)q->t + G > INT32_MAX / 2) return fail(QIEO_ERR_INVALID, "generation counter overflow");
     st = set_device(q);
@@ -1256,6 +1267,22 @@ qieo_status qieo_get_fitness(qieo_instance *q, int64_t *f_out)
     return fetch(q, f_out, q->gp.fitness, (size_t)q->np * sizeof(int64_t));
 }
 
+qieo_status qieo_get_allele_row(qieo_instance *q, int32_t c, uint8_t *x_out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!x_out) return fail(QIEO_ERR_INVALID, "x_out is NULL");
+    if (c < 0 || c >= q->np) return fail(QIEO_ERR_INVALID, "chromosome %d outside [0, %d)", c, q->np);
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    std::vector<uint8_t> x((size_t)q->xstride);
+    const uint8_t *row = q->gp.xbits + (size_t)((q->t + 1) & 1) * q->gp.xplane + (size_t)c * q->xstride;
+    st = fetch(q, x.data(), row, x.size());
+    if (st != QIEO_OK) return st;
+    unpack_row(x.data(), q->ng, x_out);
+    return QIEO_OK;
+}
+
 qieo_status qieo_get_alleles(qieo_instance *q, uint8_t *x_out)
 {
     qieo_status st = check_inst(q);
@@ -1368,6 +1395,111 @@ qieo_status qieo_get_generation_times(qieo_instance *q, int32_t n, float *ms_out
         CUDA_TRY(cudaEventElapsedTime(ms_out + i, q->gen_ev[(size_t)i], q->gen_ev[(size_t)i + 1]));
     if (count) *count = m;
     return QIEO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Row blocks of one population sharded by chromosome rows. A block observes and evaluates
+// its rows with draws keyed by the global chromosome index and reports its lowest-index
+// best row; the caller finds the population's elite across blocks (an all-reduce of the
+// packed key and a broadcast of the elite's alleles) and passes the elite row back for the
+// rotation. The generation kernel runs the observation (first-generation form: no CIP);
+// the rotation is a separate launch toward the supplied row.
+// ---------------------------------------------------------------------------------------
+qieo_status qieo_create_row_block(const qieo_problem *problem, const qieo_params *params, int32_t row0,
+                                  qieo_instance **out)
+{
+    if (out) *out = nullptr;
+    if (!problem || !params || !out) return fail(QIEO_ERR_INVALID, "NULL argument");
+    if (row0 < 0) return fail(QIEO_ERR_INVALID, "row0 must be >= 0 (got %d)", row0);
+    if (params->np < 1 || (int64_t)row0 + params->np > (int64_t)INT32_MAX)
+        return fail(QIEO_ERR_INVALID, "rows [row0, row0 + np) must lie in [0, 2^31 - 1)");
+    if (params->elite_on_host ||
+        (params->flags & (QIEO_FLAG_UNFUSED | QIEO_FLAG_COOPERATIVE | QIEO_FLAG_CONVERGE)))
+        return fail(QIEO_ERR_INVALID, "a row block excludes elite_on_host, QIEO_FLAG_UNFUSED, "
+                    "QIEO_FLAG_COOPERATIVE and QIEO_FLAG_CONVERGE");
+    qieo_instance *q = nullptr;
+    qieo_status st = qieo_create_instance(problem, params, &q);
+    if (st != QIEO_OK) return st;
+    if (!q->key_ok) {
+        qieo_destroy_instance(q);
+        return fail(QIEO_ERR_INVALID, "a row block needs fitness values that fit the packed elite key "
+                    "(lambda * sum(w) and sum(|v|) below 2^39)");
+    }
+    q->row_block = true;
+    q->gp.row0 = row0;
+    cudaError_t ce = cudaMallocAsync(&q->ext_elite, (size_t)q->xstride, q->stream);
+    if (ce != cudaSuccess) {
+        qieo_destroy_instance(q);
+        return fail(QIEO_ERR_OOM, "elite row buffer: %s", cudaGetErrorString(ce));
+    }
+    drop_graphs(q);
+    *out = q;
+    return QIEO_OK;
+}
+
+qieo_status qieo_rows_observe(qieo_instance *q, int32_t t, int64_t *best_fitness, int32_t *best_row)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!q->row_block) return fail(QIEO_ERR_INVALID, "not a row block (qieo_create_row_block)");
+    if (t < 0 || t > INT32_MAX / 2) return fail(QIEO_ERR_INVALID, "generation t out of range (got %d)", t);
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    // generation t keys its draws and selects its key slot; the slot and the segment-queue
+    // counter of t start at zero
+    char *h = nullptr;
+    st = pinned_scratch(16, &h);
+    if (st != QIEO_OK) return st;
+    st = wait_stream(q->stream);   // the pinned buffer may still feed an earlier copy
+    if (st != QIEO_OK) return st;
+    std::memcpy(h, &t, sizeof t);
+    CUDA_TRY(cudaMemcpyAsync(q->gp.gen, h, sizeof t, cudaMemcpyHostToDevice, q->stream));
+    CUDA_TRY(cudaMemsetAsync(q->gp.keys + (t % 3), 0, sizeof(unsigned long long), q->stream));
+    CUDA_TRY(cudaMemsetAsync(q->gp.qctr + (t % 3), 0, sizeof(unsigned int), q->stream));
+    CUDA_TRY(launch_gen(q, 0, 1, 0));
+    CUDA_TRY(cudaMemcpyAsync(h + 8, q->gp.keys + (t % 3), sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             q->stream));
+    st = wait_checked(q);
+    if (st != QIEO_OK) return st;
+    unsigned long long key = 0;
+    std::memcpy(&key, h + 8, sizeof key);
+    const int32_t e = (int32_t)(0xffffffu - (uint32_t)(key & 0xffffffull));
+    if (e < 0 || e >= q->np)
+        return fail(QIEO_ERR_CUDA, "internal error: generation %d of the row block closed without a best row", t);
+    q->t = t + 1;
+    q->rows_t = t;
+    if (best_fitness) *best_fitness = (int64_t)(key >> 24) - qieo::kKeyBias;
+    if (best_row) *best_row = q->gp.row0 + e;
+    return QIEO_OK;
+}
+
+qieo_status qieo_rows_rotate(qieo_instance *q, const uint8_t *elite_bits)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!q->row_block) return fail(QIEO_ERR_INVALID, "not a row block (qieo_create_row_block)");
+    if (!elite_bits) return fail(QIEO_ERR_INVALID, "elite_bits is NULL");
+    if (q->rows_t < 0) return fail(QIEO_ERR_INVALID, "no generation observed since creation or reset");
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    char *h = nullptr;
+    st = pinned_scratch((size_t)q->xstride, &h);
+    if (st != QIEO_OK) return st;
+    st = wait_stream(q->stream);
+    if (st != QIEO_OK) return st;
+    std::memset(h, 0, (size_t)q->xstride);
+    for (int32_t j = 0; j < q->ng; ++j) {
+        if (elite_bits[j] > 1) return fail(QIEO_ERR_INVALID, "elite_bits[%d] = %d is not 0 or 1", j, elite_bits[j]);
+        h[j >> 3] = (char)((unsigned char)h[j >> 3] | (unsigned char)(elite_bits[j] << (j & 7)));
+    }
+    CUDA_TRY(cudaMemcpyAsync(q->ext_elite, h, (size_t)q->xstride, cudaMemcpyHostToDevice, q->stream));
+    const size_t total = (size_t)q->np * q->svec;
+    const int blocks = (int)std::max<size_t>(
+        1, std::min<size_t>((total + qieo::kThreads - 1) / qieo::kThreads, (size_t)std::max(q->sm_count, 1) * 8));
+    if (q->rule) qieo::rows_cip_kernel<1><<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, q->rows_t, q->ext_elite);
+    else qieo::rows_cip_kernel<0><<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, q->rows_t, q->ext_elite);
+    CUDA_TRY(cudaGetLastError());
+    return wait_checked(q);
 }
 
 }  // extern "C"
@@ -1739,6 +1871,8 @@ qieo_status qieo_create_batch(qieo_instance *const *instances, int32_t n, qieo_b
             return fail(QIEO_ERR_INVALID, "instance %d uses elite_on_host; batches pick the elite on the device", i);
         if (members[(size_t)i]->state8)
             return fail(QIEO_ERR_INVALID, "instance %d stores its state as bytes; batches use 16-bit state", i);
+        if (members[(size_t)i]->row_block)
+            return fail(QIEO_ERR_INVALID, "instance %d is a row block of a sharded population", i);
         if (members[(size_t)i]->device != members[0]->device)
             return fail(QIEO_ERR_INVALID, "instance %d is on another device", i);
         for (int32_t j = 0; j < i; ++j)

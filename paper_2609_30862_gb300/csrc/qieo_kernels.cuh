@@ -148,6 +148,8 @@ struct GenParams {
                                   // forms, in order of decreasing size; nsegs = 0: none
     unsigned int *qctr;           // [3] next queue index of generation t in slot t % 3
     int32_t nsegs;
+    int32_t row0;                 // chromosome index of row 0 in the draws' counters (a row
+                                  // block of a population sharded by rows; 0 otherwise)
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -652,7 +654,7 @@ __device__ __forceinline__ void generation_body(const GenParams &p, const BlockS
             uint32_t xbits, accn;
             int64_t acw, acv;
             bool fixed;
-            sv = qubit_pass<kNarrow, kRule, kCip>(p, ParamKeys{p}, g, sv, xo, ra + rr, t, thr_bytes,
+            sv = qubit_pass<kNarrow, kRule, kCip>(p, ParamKeys{p}, g, sv, xo, ra + p.row0 + rr, t, thr_bytes,
                                                   fixed, countdown, xbits, accn, acw, acv);
             if (g.active && ok) {
                 if (!fixed) sptr[(size_t)pass * sstep] = sv;   // a fixed pass leaves it as it is
@@ -753,6 +755,7 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 {
     const int rpp = b.rows_per_pass;
     const int passes = (seg_rows + rpp - 1) / rpp;
+    const int ra_key = ra + p.row0;             // chromosome index of row ra in the draws
 
     SegCtx g;
     seg_setup<kNarrow, kCip, kSegDelta>(p, g, tile, b.v_in, b.tile_vecs, elite_row);
@@ -808,7 +811,7 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         uint32_t xbits, accn;
         int64_t acw, acv;
         bool fixed;
-        sv = qubit_pass<kNarrow, kRule, kCip, Keys, kSegDelta>(p, keys, g, sv, xo, ra + rr, t, thr_bytes,
+        sv = qubit_pass<kNarrow, kRule, kCip, Keys, kSegDelta>(p, keys, g, sv, xo, ra_key + rr, t, thr_bytes,
                                                                fixed, countdown, xbits, accn, acw, acv);
         if (g.active && ok) {
             if (!fixed) {               // a fixed pass leaves the state as it is
@@ -1350,10 +1353,9 @@ __global__ void __launch_bounds__(kThreads) record_elite_kernel(const GenParams 
 // CIP toward elite e of generation t over the whole state (grid-stride), 16-bit or byte
 // storage.
 template <int kRule, bool kS8>
-__device__ __forceinline__ void rotate_all(const GenParams &p, int32_t t, int32_t e)
+__device__ __forceinline__ void rotate_toward(const GenParams &p, int32_t t, const uint8_t *elite)
 {
     const uint8_t *xl = p.xbits + (size_t)(t & 1) * p.xplane;
-    const uint8_t *elite = xl + (size_t)e * p.xstride;
     const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
     const size_t total = (size_t)p.np * p.svec;
     for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < total;
@@ -1369,6 +1371,22 @@ __device__ __forceinline__ void rotate_all(const GenParams &p, int32_t t, int32_
             p.state[i] = rotate_vec(p.state[i], e8, m8, k8);
         }
     }
+}
+
+template <int kRule, bool kS8>
+__device__ __forceinline__ void rotate_all(const GenParams &p, int32_t t, int32_t e)
+{
+    rotate_toward<kRule, kS8>(p, t, p.xbits + (size_t)(t & 1) * p.xplane + (size_t)e * p.xstride);
+}
+
+// CIP of generation t of a row block toward an elite row supplied from outside (packed
+// alleles, bit i of byte v = gene 8v + i): the rotation step of a population sharded by
+// rows, whose elite may live in another block.
+template <int kRule>
+__global__ void __launch_bounds__(kThreads) rows_cip_kernel(const GenParams p, int32_t t, const uint8_t *elite)
+{
+    if (p.state8) rotate_toward<kRule, true>(p, t, elite);
+    else rotate_toward<kRule, false>(p, t, elite);
 }
 
 template <int kRule>
@@ -1451,8 +1469,9 @@ __global__ void __launch_bounds__(kThreads) qip_kernel(const GenParams p)
         const size_t v = i - c * (size_t)p.svec;
         const uint4 s = p.state[i];
         const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
-        const Draw4 r0 = philox4x32_10_rk(2u * (uint32_t)v, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
-        const Draw4 r1 = philox4x32_10_rk(2u * (uint32_t)v + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const uint32_t ck = (uint32_t)c + (uint32_t)p.row0;
+        const Draw4 r0 = philox4x32_10_rk(2u * (uint32_t)v, ck, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r1 = philox4x32_10_rk(2u * (uint32_t)v + 1u, ck, (uint32_t)t, 0u, p.rk0, p.rk1);
         const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
         uint32_t xbits = 0u;
 #pragma unroll

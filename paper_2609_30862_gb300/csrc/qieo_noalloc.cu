@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(kThreads) noalloc_clear_kernel(unsigned int *c
     for (int j = i; j < n; j += gridDim.x * kThreads) sums[j] = 0;
 }
 
-// QIP + Evaluation of generation t on the caller's int16 angle indices, then (last block)
-// eq. (1) and the lowest-index elite.
+// Observation and the per-chromosome sums of generation t on the caller's int16 angle
+// indices, then (last block) the penalised fitness and the lowest-index elite.
 __global__ void __launch_bounds__(kThreads) noalloc_observe_kernel(const NoallocArgs a)
 {
     __shared__ uint32_t s_thr[kMaxThr];

@@ -42,9 +42,10 @@ EXPORTS = (
     "qieo_default_params", "qieo_create_instance", "qieo_destroy_instance", "qieo_reset",
     "qieo_run", "qieo_set_wait_timeout", "qieo_synchronize", "qieo_get_best",
     "qieo_get_state", "qieo_get_fitness",
-    "qieo_get_alleles", "qieo_get_elite_history", "qieo_get_threshold_table",
+    "qieo_get_alleles", "qieo_get_allele_row", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
     "qieo_get_phase_times", "qieo_get_generation_times", "qieo_measure_integer_ceiling",
+    "qieo_create_row_block", "qieo_rows_observe", "qieo_rows_rotate",
     "qieo_get_convergence", "qieo_checkpoint_size",
     "qieo_checkpoint_save", "qieo_checkpoint_load", "qieo_philox",
     "qieo_generation_noalloc", "qieo_create_batch", "qieo_batch_run", "qieo_destroy_batch",
@@ -136,6 +137,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_get_state": ([P, P, P], C.c_int),
         "qieo_get_fitness": ([P, P], C.c_int),
         "qieo_get_alleles": ([P, P], C.c_int),
+        "qieo_get_allele_row": ([P, i32, P], C.c_int),
         "qieo_get_elite_history": ([P, i32, i32, P, P], C.c_int),
         "qieo_get_threshold_table": ([P, P], C.c_int),
         "qieo_get_launch_shape": ([P, P], C.c_int),
@@ -144,6 +146,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_get_phase_times": ([P, P, P], C.c_int),
         "qieo_get_generation_times": ([P, i32, P, P], C.c_int),
         "qieo_measure_integer_ceiling": ([i32, P], C.c_int),
+        "qieo_create_row_block": ([P, P, i32, P], C.c_int),
+        "qieo_rows_observe": ([P, i32, P, P], C.c_int),
+        "qieo_rows_rotate": ([P, P], C.c_int),
         "qieo_get_convergence": ([P, P, P], C.c_int),
         "qieo_checkpoint_size": ([P, P], C.c_int),
         "qieo_checkpoint_save": ([P, P, C.c_size_t], C.c_int),
@@ -198,6 +203,29 @@ def qieo_create_instance(weights, values, capacity: int, params: qieo_params):
     return h
 
 
+def qieo_create_row_block(weights, values, capacity: int, params: qieo_params, row0: int):
+    """Returns an opaque handle of a row block (rows row0 .. row0 + params.np - 1)."""
+    w = np.ascontiguousarray(weights, dtype=np.int32)
+    v = np.ascontiguousarray(values, dtype=np.int32)
+    if w.shape != v.shape or w.ndim != 1:
+        raise ValueError("weights and values must be 1-D arrays of equal length")
+    pr = qieo_problem(int(w.shape[0]), w.ctypes.data, v.ctypes.data, int(capacity))
+    h = C.c_void_p()
+    _check(load().qieo_create_row_block(C.byref(pr), C.byref(params), int(row0), C.byref(h)))
+    return h
+
+
+def qieo_rows_observe(h, t: int):
+    f, c = C.c_int64(), C.c_int32()
+    _check(load().qieo_rows_observe(h, int(t), C.byref(f), C.byref(c)))
+    return int(f.value), int(c.value)
+
+
+def qieo_rows_rotate(h, elite_bits) -> None:
+    e = np.ascontiguousarray(elite_bits, dtype=np.uint8)
+    _check(load().qieo_rows_rotate(h, _ptr(e)))
+
+
 def qieo_destroy_instance(h) -> None:
     _check(load().qieo_destroy_instance(h))
 
@@ -241,6 +269,12 @@ def qieo_get_fitness(h, np_: int) -> np.ndarray:
 def qieo_get_alleles(h, np_: int, ng: int) -> np.ndarray:
     x = np.zeros((np_, ng), dtype=np.uint8)
     _check(load().qieo_get_alleles(h, _ptr(x)))
+    return x
+
+
+def qieo_get_allele_row(h, c: int, ng: int) -> np.ndarray:
+    x = np.zeros(ng, dtype=np.uint8)
+    _check(load().qieo_get_allele_row(h, int(c), _ptr(x)))
     return x
 
 
@@ -474,11 +508,12 @@ class Batch:
 
 
 class Instance:
-    """Convenience owner of one instance handle (destroyed on close / garbage collection)."""
+    """Convenience owner of one instance handle (destroyed on close / garbage collection).
+    row0 >= 0 makes it a row block (qieo_create_row_block) of np_ rows starting at row0."""
 
     def __init__(self, problem, np_: int, seed: int = 1, inst: int = 0, D: int = 100,
                  lam: int = 1, rule: int = QIEO_RULE_R1, elite_on_host: int = 0,
-                 flags: int = 0, stream: int | None = None):
+                 flags: int = 0, stream: int | None = None, row0: int | None = None):
         p = qieo_default_params()
         p.np = int(np_)
         p.dtheta_den = int(D)
@@ -490,7 +525,10 @@ class Instance:
         p.flags = int(flags)
         p.stream = stream
         self.np_, self.ng, self.D = int(np_), int(problem.ng), int(D)
-        self.h = qieo_create_instance(problem.weights, problem.values, problem.capacity, p)
+        if row0 is None:
+            self.h = qieo_create_instance(problem.weights, problem.values, problem.capacity, p)
+        else:
+            self.h = qieo_create_row_block(problem.weights, problem.values, problem.capacity, p, row0)
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None:
@@ -533,6 +571,9 @@ class Instance:
     def alleles(self) -> np.ndarray:
         return qieo_get_alleles(self.h, self.np_, self.ng)
 
+    def allele_row(self, c: int) -> np.ndarray:
+        return qieo_get_allele_row(self.h, c, self.ng)
+
     def history(self, first: int, n: int):
         return qieo_get_elite_history(self.h, first, n)
 
@@ -547,6 +588,12 @@ class Instance:
 
     def kernel_time(self):
         return qieo_get_kernel_time(self.h)
+
+    def rows_observe(self, t: int):
+        return qieo_rows_observe(self.h, t)
+
+    def rows_rotate(self, elite_bits) -> None:
+        qieo_rows_rotate(self.h, elite_bits)
 
     def generation_times(self, n: int) -> np.ndarray:
         return qieo_get_generation_times(self.h, n)

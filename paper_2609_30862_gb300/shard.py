@@ -8,7 +8,9 @@ the elite's alleles, which every rank needs:
 
   1. an all-reduce MAX of a 64-bit key that orders (fitness, -global index)
      lexicographically: f * 2^32 + (2^32 - 1 - c) for fitness in [-2^31, 2^31); wider
-     fitness takes two reductions (MAX of f, then MIN of c among the ranks holding it);
+     fitness takes two reductions (MAX of f, then MIN of c among the ranks holding it).
+     Which form is used is decided once, from the problem's bounds, identically on every
+     rank (key_is_wide), so no rank can meet a fitness its form cannot carry;
   2. a broadcast of the elite's alleles (ng bytes) from the rank that owns the row.
 
 The per-rank compute is passed in (a callable per step), so this module holds no QIEO
@@ -50,6 +52,15 @@ def unpack_key(key: int) -> tuple[int, int]:
     return f, 0xFFFFFFFF - low
 
 
+def key_is_wide(weights, values, lam: int = 1) -> bool:
+    """True when a fitness of this problem can leave the packed key's range: eq. (1) gives
+    f = sum(v x) <= sum(|v|) for a feasible chromosome and f = -lam (sum(w x) - W) >=
+    -lam sum(w) for an infeasible one (W >= 0)."""
+    sw = int(np.sum(np.asarray(weights, dtype=np.int64)))
+    sv = int(np.sum(np.abs(np.asarray(values, dtype=np.int64))))
+    return int(lam) * sw > -KEY_F_MIN or sv > KEY_F_MAX
+
+
 def local_elite(f_local: np.ndarray, r0: int) -> tuple[int, int]:
     """Lowest-index maximum of this rank's fitness values, as (fitness, global index);
     (None, None) for an empty block."""
@@ -60,13 +71,22 @@ def local_elite(f_local: np.ndarray, r0: int) -> tuple[int, int]:
 
 
 class EliteExchange:
-    """DetermineElite across ranks: one collective for the key, one broadcast for the row."""
+    """DetermineElite across ranks: one collective for the key, one broadcast for the row.
 
-    def __init__(self, np_: int, ng: int, group=None, wide: bool = False):
+    The key form follows from the problem (key_is_wide), the same on every rank; `wide`
+    overrides it (True always works; False only for problems whose fitness fits)."""
+
+    def __init__(self, np_: int, ng: int, problem=None, lam: int = 1, group=None, wide=None):
         import torch
         import torch.distributed as dist
+        if wide is None:
+            if problem is None:
+                raise ValueError("EliteExchange needs the problem (or an explicit key form)")
+            wide = key_is_wide(problem.weights, problem.values, lam)
+        elif not wide and problem is not None and key_is_wide(problem.weights, problem.values, lam):
+            raise ValueError("this problem's fitness does not fit the packed key: use wide=True")
         self.torch, self.dist = torch, dist
-        self.np, self.ng, self.group, self.wide = np_, ng, group, wide
+        self.np, self.ng, self.group, self.wide = np_, ng, group, bool(wide)
         self.world = dist.get_world_size(group)
         self.rank = dist.get_rank(group)
 
@@ -98,11 +118,27 @@ class EliteExchange:
         return f_e, c_e, buf.numpy().copy()
 
 
-def run_sharded(np_: int, ng: int, gens: int, observe_rows, rotate_rows, exchange,
-                r0: int, t0: int = 0):
-    """Runs `gens` generations of one sharded instance from generation t0.
+class _RowOnDemand(dict):
+    """The local best row, fetched only if the exchange reads it (on the owning rank)."""
 
-    observe_rows(t) -> (f_local[nr], x_local[nr, ng]): QIP + Evaluation of this rank's rows.
+    def __init__(self, c, fetch):
+        super().__init__()
+        self.c, self.fetch = c, fetch
+
+    def __getitem__(self, c):
+        if c != self.c:
+            raise KeyError(c)
+        return self.fetch(c)
+
+
+def run_sharded_blocks(gens: int, observe_best, row_of, rotate_rows, exchange, t0: int = 0):
+    """Runs `gens` generations of one sharded instance from generation t0, with the local
+    DetermineElite done by the rank's own compute.
+
+    observe_best(t) -> (f_best, c_best): QIP + Evaluation of this rank's rows and their
+        lowest-index best (c_best a global index), or (None, None) for an empty block.
+    row_of(c) -> alleles (ng) of this rank's row c; called only on the rank that holds the
+        population's elite.
     rotate_rows(x_elite): CIP of this rank's rows toward the elite's alleles.
     exchange: an EliteExchange (or any callable with its signature).
     Returns (hist_e, hist_f, best) where best = (fitness, generation, chromosome, alleles),
@@ -113,12 +149,26 @@ def run_sharded(np_: int, ng: int, gens: int, observe_rows, rotate_rows, exchang
     best = (None, -1, -1, None)
     for g in range(gens):
         t = t0 + g
-        f_loc, x_loc = observe_rows(t)
-        f_b, c_b = local_elite(f_loc, r0)
-        rows = {} if c_b is None else {c_b: x_loc[c_b - r0]}
+        f_b, c_b = observe_best(t)
+        rows = {} if c_b is None else _RowOnDemand(c_b, row_of)
         f_e, c_e, x_e = exchange(f_b, c_b, rows)
         hist_e[g], hist_f[g] = c_e, f_e
         if best[1] < 0 or f_e > best[0]:
             best = (f_e, t, c_e, x_e)
         rotate_rows(x_e)
     return hist_e, hist_f, best
+
+
+def run_sharded(np_: int, ng: int, gens: int, observe_rows, rotate_rows, exchange,
+                r0: int, t0: int = 0):
+    """run_sharded_blocks for a rank whose compute returns all its rows:
+    observe_rows(t) -> (f_local[nr], x_local[nr, ng]); the local DetermineElite is done here."""
+    last = {}
+
+    def observe_best(t):
+        f_loc, x_loc = observe_rows(t)
+        last["x"] = x_loc
+        return local_elite(f_loc, r0)
+
+    return run_sharded_blocks(gens, observe_best, lambda c: last["x"][c - r0], rotate_rows,
+                              exchange, t0)

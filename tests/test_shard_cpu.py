@@ -34,6 +34,15 @@ def test_packed_key_orders_by_fitness_then_lowest_index():
         S.pack_key(0, -1)
 
 
+def test_key_form_follows_the_problem_bounds():
+    """The key form is a function of the problem alone, so every rank picks the same one."""
+    assert not S.key_is_wide([10] * 100, [15] * 100)
+    assert S.key_is_wide([1] * 4, [2**30] * 4)                   # sum |v| beyond 2^31 - 1
+    assert S.key_is_wide([2**29] * 4, [1] * 4, lam=2)             # lam sum w beyond 2^31
+    assert not S.key_is_wide([2**29] * 4, [1] * 4, lam=1)         # exactly 2^31: fits
+    assert S.key_is_wide([1], [-(2**31)])                         # |v| counts
+
+
 @pytest.mark.parametrize("np_,world", [(10, 2), (11, 3), (3, 4), (1024, 8)])
 def test_row_ranges_cover_the_population(np_, world):
     seen = []
@@ -73,7 +82,8 @@ def _rank_main(rank, world, port, case, out_path):
         def rotate_rows(x_e):
             O.rows_rotate(k, last["x"], x_e, D=D, rule=rule)
 
-        ex = S.EliteExchange(np_, ng, wide=wide)
+        ex = S.EliteExchange(np_, ng, problem=prob, lam=lam)
+        assert ex.wide == wide
         he, hf, best = S.run_sharded(np_, ng, gens, observe_rows, rotate_rows, ex, r0)
         blocks = [None] * world
         dist.all_gather_object(blocks, k)
