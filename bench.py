@@ -55,8 +55,13 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="c5 arrivals per second (0: 0.8 x the measured batched capacity)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--per-generation", action="store_true",
+                    help="c4: one batched launch per generation (QIEO_FLAG_PER_GENERATION on the "
+                         "members) instead of one persistent launch per run")
     ap.add_argument("--state-i8", action="store_true",
                     help="c1-c3: store the angle indices as bytes (QIEO_FLAG_STATE_I8)")
+    ap.add_argument("--streamed", action="store_true",
+                    help="c1-c3: never keep the state resident in shared memory (QIEO_FLAG_STREAMED)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-phases", action="store_true",
@@ -352,7 +357,7 @@ def run_gpu(a):
     np_, ng, G = c["np"], c["ng"], c["gens"]
     genes_per_step = np_ * ng * G
     stream = torch.cuda.Stream()
-    flags = Q.QIEO_FLAG_STATE_I8 if a.state_i8 else 0
+    flags = (Q.QIEO_FLAG_STATE_I8 if a.state_i8 else 0) | (Q.QIEO_FLAG_STREAMED if a.streamed else 0)
     inst = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
                       stream=stream.cuda_stream, flags=flags)
     shape = inst.shape()
@@ -433,13 +438,17 @@ def run_gpu(a):
         roof["t_hbm_us"] = t_hbm * 1e6
         roof["t_int_us"] = t_int * 1e6
     roof["state_in_l2"] = l2_resident
-    roof["traffic"] = None if a.state_i8 else profile_traffic("generation_kernel", a.workload)
+    kname = ("resident_run_kernel" if shape.resident else "run_kernel" if shape.persistent
+             else "generation_kernel")
+    roof["traffic"] = None if a.state_i8 else profile_traffic(kname, a.workload)
     if roof["traffic"]:
         roof["frac_dram_measured"] = roof["traffic"] / launch_s / 1e9 / hbm_peak
-    roof["kernel"] = ("run_kernel (one cooperative launch per run)" if shape.persistent
+    roof["kernel"] = ("resident_run_kernel (one cooperative launch per run, state in shared memory)"
+                      if shape.resident else
+                      "run_kernel (one cooperative launch per run)" if shape.persistent
                       else "generation_kernel (one launch per generation)")
     roof["us_per_generation"] = launch_s * 1e6
-    if not a.no_phases and not shape.persistent:
+    if not a.no_phases and (shape.resident or not shape.persistent):
         roof["phases"] = generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch,
                                            hbm_peak, int_peak)
 
@@ -480,7 +489,8 @@ def run_gpu(a):
                            ("segments of decreasing size (<= %d tile-rows) from a queue"
                             % shape.rows_per_cta) if shape.rows_per_cta >= 64
                            else "equal static shares of <= %d tile-rows" % shape.rows_per_cta,
-                           "one cooperative launch per run" if shape.persistent
+                           "one cooperative launch per run with the state resident in shared memory"
+                           if shape.resident else "one cooperative launch per run" if shape.persistent
                            else "one launch per generation")),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -539,7 +549,8 @@ def generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch, hbm_peak, 
     return {"spread": window(*SPREAD_WINDOW), "saturated": window(*SATURATED_WINDOW),
             "per_25": [round(1e3 * float(np.mean(ms[i:i + step])), 2) for i in range(0, len(ms), step)],
             "sum_of_launches_us": 1e3 * float(np.sum(ms)),
-            "what": "CUDA events before every generation launch of one run (launches serialised)"}
+            "what": "device clock at each generation's start (resident form) or CUDA events before "
+                    "every generation launch of one run (launches serialised)"}
 
 
 def batch_oracle_sample(specs, G: int, target_s: float = 10.0):
@@ -593,10 +604,13 @@ def run_batched(a):
     probs = [WL.knapsack(sp.ng, sp.seed) for sp in specs]
     stream = torch.cuda.Stream()
 
+    member_flags = Q.QIEO_FLAG_PER_GENERATION if a.per_generation else 0
+
     def make(tune: bool):
         out, t = [], 0.0
         for sp, prob in zip(specs, probs):
-            inst = Q.Instance(prob, sp.np_, seed=sp.seed, inst=sp.seed, stream=stream.cuda_stream)
+            inst = Q.Instance(prob, sp.np_, seed=sp.seed, inst=sp.seed, stream=stream.cuda_stream,
+                              flags=member_flags)
             if tune:
                 t0 = time.perf_counter()
                 inst.autotune(4)
@@ -693,8 +707,11 @@ def run_batched(a):
     achieved = STATE_BYTES_PER_GENE * genes_per_gen / launch_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src,
-            "state_in_l2": state_bytes < L2_BYTES, "traffic": profile_traffic("batch_generation_kernel", "c4"),
-            "kernel": "batch_generation_kernel (one launch per generation for all members)",
+            "state_in_l2": state_bytes < L2_BYTES, "traffic": profile_traffic("batch_generation_kernel" if a.per_generation
+                                                       else "batch_run_kernel", "c4"),
+            "kernel": ("batch_generation_kernel (one launch per generation for all members)"
+                       if a.per_generation else
+                       "batch_run_kernel (one persistent launch per run for all members)"),
             "us_per_generation": launch_s * 1e6}
     value = world * n * a.steps / tb
     line = {
@@ -703,7 +720,9 @@ def run_batched(a):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": "c4: 256 instances, Ng log-uniform [50, 20000], Np uniform {32,64,128,256,512}, "
-                               "300 generations, seeds 1..256", "parallelism": "one batched launch per generation"
+                               "300 generations, seeds 1..256",
+                   "parallelism": ("one batched launch per generation" if a.per_generation
+                                   else "one persistent batched launch per run")
                                + ("; 256 instances per rank" if world > 1 else ""),
                    "state_bytes": state_bytes,
                    "l2": "flushed between steps (512 MB write)" if flush else "state larger than L2 (no flush)"},
@@ -712,7 +731,9 @@ def run_batched(a):
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "256 x qieo_create_instance from host arrays + qieo_create_batch + qieo_batch_run + "
                         "256 x qieo_get_best + destroy, per step"},
-        "gpu_launches": a.steps * (n + G + 1),
+        # per step: n resets, then G + 1 batched launches, or the first generation's launch, one
+        # persistent launch for the others and the final CIP
+        "gpu_launches": a.steps * (n + (G + 1 if a.per_generation else 3)),
         "clocks": clocks,
         "one_launch_per_instance": {"value": world * n * single_steps / ts, "unit": "solves/s",
                                     "gene_updates_per_s": world * genes * single_steps / ts},

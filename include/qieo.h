@@ -97,13 +97,19 @@ typedef struct {
                                          QIEO_FLAG_REGISTER_PREFETCH, QIEO_FLAG_COOPERATIVE,
                                          QIEO_FLAG_UNFUSED or QIEO_FLAG_FORCE_WIDE, and not in
                                          batches */
-#define QIEO_FLAG_TIME_GENERATIONS 0x400 /* record a CUDA event before every generation
-                                            launch of a run and after the last one, so that
-                                            qieo_get_generation_times can report each
-                                            generation's device time (one launch per
-                                            generation, no CUDA graph; the events keep
-                                            consecutive launches from overlapping, so each
-                                            time is the launch alone). Not with
+#define QIEO_FLAG_STREAMED      0x800 /* never keep the state resident in shared memory
+                                         (see qieo_launch_shape.resident): stream it from
+                                         device memory every generation */
+#define QIEO_FLAG_TIME_GENERATIONS 0x400 /* time every generation of a run for
+                                            qieo_get_generation_times. In the resident form
+                                            (qieo_launch_shape.resident) one thread reads the
+                                            device clock at the start of each generation
+                                            (after the grid barrier) and at the run's end;
+                                            otherwise a CUDA event is recorded before every
+                                            generation launch and after the last one (one
+                                            launch per generation, no CUDA graph; the events
+                                            keep consecutive launches from overlapping, so
+                                            each time is the launch alone). Not with
                                             elite_on_host, QIEO_FLAG_COOPERATIVE or
                                             QIEO_FLAG_UNFUSED */
 
@@ -199,6 +205,13 @@ typedef struct {
     int32_t persistent;      /* out: 1 when a run is one cooperative launch (see
                                 QIEO_FLAG_COOPERATIVE), 0 when it is one launch per
                                 generation */
+    int32_t resident;        /* out: 1 when a run keeps the state in shared memory: each
+                                block holds its share of the angle indices on chip from the
+                                start of a run to its end (one cooperative launch; chosen
+                                whenever the shares fit, e.g. up to about 20-30 MB of state on
+                                a GB300, unless QIEO_FLAG_STREAMED, QIEO_FLAG_COOPERATIVE,
+                                QIEO_FLAG_PER_GENERATION, QIEO_FLAG_TIME_GENERATIONS,
+                                QIEO_FLAG_CONVERGE, elite_on_host or byte state) */
 } qieo_launch_shape;
 
 qieo_status qieo_get_launch_shape(qieo_instance *inst, qieo_launch_shape *shape);
@@ -209,9 +222,9 @@ qieo_status qieo_set_launch_shape(qieo_instance *inst, const qieo_launch_shape *
 qieo_status qieo_get_kernel_time(qieo_instance *inst, double *ms, int64_t *launches);
 
 /* Device time of each generation of the last run of an instance created with
- * QIEO_FLAG_TIME_GENERATIONS: ms_out[i] = the time (ms, CUDA events on the instance's
- * stream) from the start of the launch of the run's generation i to the start of the next
- * launch (for the last generation: to its end), for i < min(n, generations of that run);
+ * QIEO_FLAG_TIME_GENERATIONS: ms_out[i] = the time (ms) from the start of the run's
+ * generation i to the start of the next one (for the last generation: to the end of the
+ * run's last generation, before its final rotation), for i < min(n, generations of that run);
  * *count = that number. Waits (bounded) for the run to finish. The times cover one fused
  * generation kernel each (CIP of the generation before, QIP, Evaluation, DetermineElite);
  * the run's final CIP launch is not included. QIEO_ERR_INVALID without the flag. */
@@ -237,7 +250,8 @@ qieo_status qieo_get_generation_times(qieo_instance *inst, int32_t n, float *ms_
  * qieo_rows_observe: QIP and Evaluation of generation t (absolute; it keys the draws) on the
  * block's current angle indices, without a rotation first; *best_fitness and *best_row
  * receive the block's lowest-index maximum of eq. (1) (best_row is a global chromosome
- * index). Waits (bounded) for the device. Either output may be NULL.
+ * index). qieo_get_state then reports t + 1 as the next generation. Waits (bounded) for
+ * the device. Either output may be NULL.
  *
  * qieo_rows_rotate: CIP of the block's rows after the generation last observed, toward the
  * elite alleles elite_bits (host memory, ng bytes, each 0 or 1; copied before the call
@@ -300,14 +314,20 @@ qieo_status qieo_checkpoint_load(qieo_instance *inst, const void *buffer, size_t
  * run, whose elite fitness is the same. Either pointer may be NULL. */
 qieo_status qieo_get_convergence(qieo_instance *inst, int32_t *stopped, int32_t *stable);
 
-/* A batch: many instances advanced together, one persistent kernel launch per generation
- * for all of them (batching of independent QIEO solves; the paper runs one problem at a
- * time). The instances keep their own state, records and generation
- * counters; qieo_batch_run(b, G) is equivalent to qieo_run(inst, G) on every member, bit for
- * bit. The work of a generation (every member's tiles of rows) is cut into segments
- * balanced over a grid of one block per resident slot; members are grouped by item-sum
- * form and rotation rule, one launch per group and generation. Members must live on one
- * device, must not use elite_on_host and must not be destroyed while the batch exists. */
+/* A batch: many instances advanced together (batching of independent QIEO solves; the
+ * paper runs one problem at a time). The instances keep their own state, records and
+ * generation counters; qieo_batch_run(b, G) is equivalent to qieo_run(inst, G) on every
+ * member, bit for bit. The work of a generation (every member's tiles of rows) is cut into
+ * segments balanced over a grid of one block per resident slot; members are grouped by
+ * item-sum form and rotation rule. By default a run is one persistent cooperative launch
+ * per group for all its generations: blocks take (generation, segment) items from one queue
+ * in order, and a segment of an instance's next generation waits (bounded) only for that
+ * instance's previous generation to close, not for the other members. When a member uses
+ * QIEO_FLAG_CONVERGE or QIEO_FLAG_PER_GENERATION, a run is instead one launch per group and
+ * generation (replayed from a CUDA graph when a run length repeats). A wait that runs out
+ * sets the member's error word (QIEO_ERR_TIMEOUT from its next checked call). Members must
+ * live on one device, must not use elite_on_host and must not be destroyed while the batch
+ * exists. */
 typedef struct qieo_batch qieo_batch;
 
 /* Creates a batch over instances[0 .. n-1] (n >= 1, distinct). The batch runs on the stream

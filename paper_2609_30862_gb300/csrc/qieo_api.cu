@@ -130,6 +130,9 @@ struct qieo_instance {
     int32_t lanes = 32, warps = 8, grid = 1, grid_override = 0, narrow = 0;
     size_t smem = 0;
     bool coop = false;             // the run fits one cooperative launch
+    bool resident_fits = false;    // each block's share of the state fits in shared memory
+    size_t res_smem = 0;           // dynamic shared memory of the resident form
+    int32_t res_share = 0;         // tile-rows of the largest share
 
     // CUDA graphs keyed by the number of generations of a run; a graph is captured the
     // second time a run length is seen (a one-off run is cheaper to launch directly)
@@ -153,6 +156,10 @@ struct qieo_instance {
     // launch of the last run's generation i, gen_ev[gen_ev_n] after its last launch
     std::vector<cudaEvent_t> gen_ev;
     int32_t gen_ev_n = 0;
+    // ... or, for a resident-form run, the device clock at each generation's start
+    unsigned long long *gen_ns = nullptr;
+    int32_t gen_ns_cap = 0;
+    bool gen_ns_last = false;
 
     // a row block of a population sharded by rows (qieo_create_row_block): its rows are
     // chromosomes row0 .. row0 + np - 1 of the whole population; ext_elite holds the
@@ -222,6 +229,14 @@ const void *gen_kernel_of(const qieo_instance *q, bool ring, bool seg_delta)
 const void *run_kernel_of(const qieo_instance *q, bool ring)
 {
     return reinterpret_cast<const void *>(kernel_of<PickRun>(q, ring));
+}
+
+// The resident-form run kernel (rule R1 forms its CIP deltas once per segment).
+typedef void (*ResidentFn)(qieo::GenParams, int32_t, int32_t);
+ResidentFn resident_fn(const qieo_instance *q)
+{
+    if (q->narrow) return q->rule ? &qieo::resident_run_kernel<true, 1, false> : &qieo::resident_run_kernel<true, 0, true>;
+    return q->rule ? &qieo::resident_run_kernel<false, 1, false> : &qieo::resident_run_kernel<false, 0, true>;
 }
 
 // Lets the device's default memory pool keep up to 1 GiB of released blocks, so that
@@ -297,10 +312,18 @@ qieo_status resident_blocks(int device, const void *fn, size_t smem, int *bps)
             return QIEO_OK;
         }
     }
-    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // The limit is a property of the kernel, shared by every instance that launches it: it
+    // is only ever raised (to the largest size asked for on the device), never lowered below
+    // what another instance launches with.
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &lim = limit[{device, fn}];
+    if (smem > lim) {
+        CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        lim = smem;
+    }
     int n = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, qieo::kThreads, smem));
-    std::lock_guard<std::mutex> lock(mu);
     cache[key] = n;
     *bps = n;
     return QIEO_OK;
@@ -354,6 +377,10 @@ qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int s
 // 364 us (per-pass deltas), 2 blocks worse (10.7 / 387 us with per-segment deltas).
 constexpr int kBlocksPerSm = 3;
 
+// Most dynamic shared memory a block of the resident form may take (of the 227 KB a block
+// can have; the kernel's static tables take the rest).
+constexpr size_t kResidentMaxSmem = 200 * 1024;
+
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
 // fills the launch fields of gp.
 qieo_status configure(qieo_instance *q)
@@ -398,6 +425,20 @@ qieo_status configure(qieo_instance *q)
     q->smem = ring + (size_t)seg_max * row_bytes;
     q->coop = bps_run > 0 && grid <= (int64_t)q->sm_count * bps_run;
     q->gp.ring = use_ring ? 1 : 0;
+
+    // Resident form: every block's share of the state (share tile-rows x tile vectors of
+    // 16 bytes) stays in its shared memory for a whole run; possible when all blocks of
+    // the grid fit on the device at once with that much shared memory each.
+    q->resident_fits = false;
+    q->res_share = (int32_t)share;
+    q->res_smem = (size_t)share * tile * sizeof(uint4) + (size_t)seg_max * row_bytes;
+    if (q->res_smem <= kResidentMaxSmem && !q->state8) {
+        int bps_res = 0;
+        qieo_status rst = resident_blocks(q->device, reinterpret_cast<const void *>(resident_fn(q)),
+                                          q->res_smem, &bps_res);
+        if (rst != QIEO_OK) return rst;
+        q->resident_fits = bps_res > 0 && grid <= (int64_t)q->sm_count * bps_res;
+    }
 
     qieo::GenParams &g = q->gp;
     g.items_narrow = q->items_narrow;
@@ -593,6 +634,7 @@ qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
             q->gen_ev.push_back(e);
         }
         q->gen_ev_n = 0;
+        q->gen_ns_last = false;
     }
     for (int32_t g = 0; g < G; ++g) {
         if (per_gen) CUDA_TRY(cudaEventRecord(q->gen_ev[(size_t)g], q->stream));
@@ -612,6 +654,15 @@ qieo_status enqueue_device_run(qieo_instance *q, int32_t G)
 // launch per generation (measured: 64 x 100 genes 2.86 vs 3.44 us per generation; at
 // 1,024 x 10,000 the two are within 1 %, at 4,096 x 100,000 the cooperative form is 2 %
 // slower). Not with the convergence test or byte state.
+// The resident form (see resident_run_kernel) is used whenever it fits, unless a flag asks
+// for one launch per generation, the streamed form or the cooperative streamed form.
+bool use_resident(const qieo_instance *q)
+{
+    if (!q->resident_fits || q->host_de || q->row_block || !q->key_ok || q->state8) return false;
+    return !(q->flags & (QIEO_FLAG_UNFUSED | QIEO_FLAG_PER_GENERATION | QIEO_FLAG_CONVERGE |
+                         QIEO_FLAG_COOPERATIVE | QIEO_FLAG_STREAMED));
+}
+
 bool use_cooperative(const qieo_instance *q)
 {
     if (!q->coop || q->host_de ||
@@ -622,14 +673,55 @@ bool use_cooperative(const qieo_instance *q)
            (int64_t)q->np * q->svec * 8 <= ((int64_t)1 << 22);
 }
 
+// One resident-form run of G generations (one cooperative launch) and the one-thread launch
+// that then advances the generation counter.
+cudaError_t launch_resident(const qieo_instance *q, int32_t G, unsigned long long *gen_ns)
+{
+    qieo::GenParams p = q->gp;
+    p.deferred = 1;
+    p.g = 0;
+    p.gen_ns = gen_ns;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q->grid);
+    cfg.blockDim = dim3(qieo::kThreads);
+    cfg.dynamicSmemBytes = q->res_smem;
+    cfg.stream = q->stream;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t ce = cudaLaunchKernelEx(&cfg, resident_fn(q), p, G, q->res_share);
+    if (ce != cudaSuccess) return ce;
+    cudaLaunchAttribute attr1[1];
+    cudaLaunchConfig_t one = launch_config(q, dim3(1), 0, attr1);
+    one.blockDim = dim3(32);
+    return cudaLaunchKernelEx(&one, qieo::end_run_kernel, p, G);
+}
+
 qieo_status run_cooperative(qieo_instance *q, int32_t G)
 {
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
+    const bool resident = use_resident(q);
     if (timing) CUDA_TRY(cudaEventRecord(q->ev0, q->stream));
     // the barrier counts G x grid arrivals in 32 bits: split longer runs (run(a) + run(b)
     // equals run(a + b))
     const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(G, ((int64_t)1 << 30) / std::max(1, q->grid)));
-    for (int32_t done = 0; done < G; done += chunk) CUDA_TRY(launch_run(q, std::min(chunk, G - done)));
+    const bool stamps = resident && (q->flags & QIEO_FLAG_TIME_GENERATIONS);
+    if (stamps && q->gen_ns_cap < G + 1) {
+        if (q->gen_ns) cudaFreeAsync(q->gen_ns, q->stream);
+        q->gen_ns = nullptr;
+        q->gen_ns_cap = 0;
+        CUDA_TRY(cudaMallocAsync(&q->gen_ns, (size_t)(G + 1) * sizeof(unsigned long long), q->stream));
+        q->gen_ns_cap = G + 1;
+    }
+    for (int32_t done = 0; done < G; done += chunk)
+        CUDA_TRY(resident ? launch_resident(q, std::min(chunk, G - done), stamps ? q->gen_ns + done : nullptr)
+                          : launch_run(q, std::min(chunk, G - done)));
+    if (stamps) {
+        q->gen_ev_n = G;
+        q->gen_ns_last = true;
+    }
     if (timing) {
         CUDA_TRY(cudaEventRecord(q->ev1, q->stream));
         qieo_status st = wait_stream(q->stream);
@@ -648,7 +740,7 @@ qieo_status run_device(qieo_instance *q, int32_t G)
         qieo_status st = ensure_events(q);
         if (st != QIEO_OK) return st;
     }
-    if (use_cooperative(q)) return run_cooperative(q, G);
+    if (use_resident(q) || use_cooperative(q)) return run_cooperative(q, G);
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
     if ((q->flags & (QIEO_FLAG_NO_GRAPH | QIEO_FLAG_TIME_GENERATIONS)) || (first_time && !q->graphs.count(G))) {
@@ -1107,6 +1199,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->hist_f && !q->fixed_history) cudaFreeAsync(q->hist_f, q->stream);
     if (q->segq) cudaFreeAsync(q->segq, q->stream);
     if (q->ext_elite) cudaFreeAsync(q->ext_elite, q->stream);
+    if (q->gen_ns) cudaFreeAsync(q->gen_ns, q->stream);
     if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
@@ -1346,7 +1439,8 @@ qieo_status qieo_get_launch_shape(qieo_instance *q, qieo_launch_shape *s)
     s->narrow = q->narrow;
     s->tiles = q->gp.ntile;
     s->rows_per_cta = q->gp.seg_rows_max;
-    s->persistent = use_cooperative(q) ? 1 : 0;
+    s->persistent = (use_resident(q) || use_cooperative(q)) ? 1 : 0;
+    s->resident = use_resident(q) ? 1 : 0;
     return QIEO_OK;
 }
 
@@ -1391,8 +1485,15 @@ qieo_status qieo_get_generation_times(qieo_instance *q, int32_t n, float *ms_out
     st = wait_stream(q->stream);
     if (st != QIEO_OK) return st;
     const int32_t m = std::min(n, q->gen_ev_n);
-    for (int32_t i = 0; i < m; ++i)
-        CUDA_TRY(cudaEventElapsedTime(ms_out + i, q->gen_ev[(size_t)i], q->gen_ev[(size_t)i + 1]));
+    if (q->gen_ns_last) {
+        std::vector<unsigned long long> ns((size_t)m + 1);
+        st = fetch(q, ns.data(), q->gen_ns, ns.size() * sizeof(unsigned long long));
+        if (st != QIEO_OK) return st;
+        for (int32_t i = 0; i < m; ++i) ms_out[i] = (float)((double)(ns[(size_t)i + 1] - ns[(size_t)i]) * 1e-6);
+    } else {
+        for (int32_t i = 0; i < m; ++i)
+            CUDA_TRY(cudaEventElapsedTime(ms_out + i, q->gen_ev[(size_t)i], q->gen_ev[(size_t)i + 1]));
+    }
     if (count) *count = m;
     return QIEO_OK;
 }
@@ -1452,11 +1553,15 @@ qieo_status qieo_rows_observe(qieo_instance *q, int32_t t, int64_t *best_fitness
     if (st != QIEO_OK) return st;
     st = wait_stream(q->stream);   // the pinned buffer may still feed an earlier copy
     if (st != QIEO_OK) return st;
+    const int32_t next = t + 1;
     std::memcpy(h, &t, sizeof t);
+    std::memcpy(h + 4, &next, sizeof next);
     CUDA_TRY(cudaMemcpyAsync(q->gp.gen, h, sizeof t, cudaMemcpyHostToDevice, q->stream));
     CUDA_TRY(cudaMemsetAsync(q->gp.keys + (t % 3), 0, sizeof(unsigned long long), q->stream));
     CUDA_TRY(cudaMemsetAsync(q->gp.qctr + (t % 3), 0, sizeof(unsigned int), q->stream));
     CUDA_TRY(launch_gen(q, 0, 1, 0));
+    // the generation counter then names the next generation, as after qieo_run
+    CUDA_TRY(cudaMemcpyAsync(q->gp.gen, h + 4, sizeof next, cudaMemcpyHostToDevice, q->stream));
     CUDA_TRY(cudaMemcpyAsync(h + 8, q->gp.keys + (t % 3), sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                              q->stream));
     st = wait_checked(q);
@@ -1680,10 +1785,12 @@ struct qieo_batch {
         int32_t grid = 1;
         size_t smem = 0;
         int32_t seg_rows_max = 1;
-        void *dev = nullptr;                        // params | segs | queue | inst_segs
+        void *dev = nullptr;                        // params | segs | queue | inst_segs | done
         std::vector<qieo::GenParams> host_params;   // what is on the device
         qieo::BatchArgs args{};
+        size_t done_bytes = 0;
     };
+    bool persistent = false;   // runs are one cooperative launch per group (batch_run_kernel)
     std::vector<qieo_instance *> members;
     std::vector<Group> groups;
     int device = 0;
@@ -1706,6 +1813,12 @@ template <bool N, int R, bool C>
 struct PickBatch {
     static void (*get())(qieo::BatchArgs) { return &qieo::batch_generation_kernel<N, R, C>; }
 };
+
+void (*batch_run_kernel_of(bool narrow, int rule))(qieo::BatchArgs, int32_t)
+{
+    if (narrow) return rule ? &qieo::batch_run_kernel<true, 1> : &qieo::batch_run_kernel<true, 0>;
+    return rule ? &qieo::batch_run_kernel<false, 1> : &qieo::batch_run_kernel<false, 0>;
+}
 
 void (*batch_kernel_of(bool narrow, int rule, bool cip))(qieo::BatchArgs)
 {
@@ -1795,23 +1908,31 @@ qieo_status build_group(qieo_batch *bt, qieo_batch::Group &g)
     const size_t row_bytes = g.narrow ? 8 : 16;
     auto fn = batch_kernel_of(g.narrow, g.rule, true);
     auto fn0 = batch_kernel_of(g.narrow, g.rule, false);
+    auto fr = batch_run_kernel_of(g.narrow, g.rule);
     const size_t smem_max = qieo::kRingBytes + (size_t)qieo::kMaxSegRows * row_bytes;
     for (auto f : {fn, fn0})
         CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(f),
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-    int bps = 0;
+    CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(fr),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    int bps = 0, bps_run = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, reinterpret_cast<const void *>(fn),
                                                            qieo::kThreads, smem_max));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_run, reinterpret_cast<const void *>(fr),
+                                                           qieo::kThreads, smem_max));
+    // the persistent form needs every block resident at once
+    if (bt->persistent) bps = std::min(bps, bps_run);
+    if (bt->persistent && bps < 1) bt->persistent = false;
     g.grid = std::max(1, bps) * std::max(1, q0->sm_count);
     std::vector<qieo::BatchSeg> segs;
     std::vector<int32_t> inst_segs;
     partition(g.members, g.grid, segs, inst_segs, g.seg_rows_max);
     g.smem = qieo::kRingBytes + (size_t)g.seg_rows_max * row_bytes;
     const size_t n = g.members.size();
-    size_t off[4], total = 0;
-    const size_t sizes[4] = {n * sizeof(qieo::GenParams), segs.size() * sizeof(qieo::BatchSeg),
-                             2 * sizeof(unsigned int), n * sizeof(int32_t)};
-    for (int i = 0; i < 4; ++i) {
+    size_t off[5], total = 0;
+    const size_t sizes[5] = {n * sizeof(qieo::GenParams), segs.size() * sizeof(qieo::BatchSeg),
+                             2 * sizeof(unsigned int), n * sizeof(int32_t), n * sizeof(unsigned int)};
+    for (int i = 0; i < 5; ++i) {
         off[i] = total;
         total = align_up(total + sizes[i], 256);
     }
@@ -1821,6 +1942,8 @@ qieo_status build_group(qieo_batch *bt, qieo_batch::Group &g)
     g.args.segs = (const qieo::BatchSeg *)(d + off[1]);
     g.args.queue = (unsigned int *)(d + off[2]);
     g.args.inst_segs = (const int32_t *)(d + off[3]);
+    g.args.done = (unsigned int *)(d + off[4]);
+    g.done_bytes = sizes[4];
     g.args.nsegs = (int32_t)segs.size();
     g.args.seg_rows_max = g.seg_rows_max;
     CUDA_TRY(cudaMemcpyAsync(d + off[1], segs.data(), sizes[1], cudaMemcpyHostToDevice, bt->stream));
@@ -1829,6 +1952,46 @@ qieo_status build_group(qieo_batch *bt, qieo_batch::Group &g)
     qieo_status st = upload_group(bt, g);
     if (st != QIEO_OK) return st;
     return wait_stream(bt->stream);
+}
+
+// A persistent-form run: per group, the run's first generation (no CIP) as one batched
+// launch, then the run-local close counters cleared and one cooperative launch for the
+// other G - 1 generations (split so that generations x segments stays within 32 bits), and
+// the final rotation.
+qieo_status enqueue_batch_persistent(qieo_batch *bt, int32_t G)
+{
+    for (auto &g : bt->groups) {
+        {
+            cudaLaunchConfig_t cfg0 = {};
+            cfg0.gridDim = dim3(g.grid);
+            cfg0.blockDim = dim3(qieo::kThreads);
+            cfg0.dynamicSmemBytes = g.smem;
+            cfg0.stream = bt->stream;
+            CUDA_TRY(cudaLaunchKernelEx(&cfg0, batch_kernel_of(g.narrow, g.rule, false), g.args));
+        }
+        const int32_t rest = G - 1;
+        const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(std::max(rest, 1),
+                                                                               ((int64_t)1 << 30) / std::max(1, g.args.nsegs)));
+        for (int32_t done = 0; done < rest; done += chunk) {
+            const int32_t n = std::min(chunk, rest - done);
+            CUDA_TRY(cudaMemsetAsync(g.args.done, 0, g.done_bytes, bt->stream));
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(g.grid);
+            cfg.blockDim = dim3(qieo::kThreads);
+            cfg.dynamicSmemBytes = g.smem;
+            cfg.stream = bt->stream;
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CUDA_TRY(cudaLaunchKernelEx(&cfg, batch_run_kernel_of(g.narrow, g.rule), g.args, n));
+        }
+        if (g.rule) qieo::batch_cip_kernel<1><<<g.grid, qieo::kThreads, 0, bt->stream>>>(g.args);
+        else qieo::batch_cip_kernel<0><<<g.grid, qieo::kThreads, 0, bt->stream>>>(g.args);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return QIEO_OK;
 }
 
 qieo_status enqueue_batch_run(qieo_batch *bt, int32_t G)
@@ -1895,6 +2058,11 @@ qieo_status qieo_create_batch(qieo_instance *const *instances, int32_t n, qieo_b
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming);
     if (ce != cudaSuccess) return bail(fail(QIEO_ERR_CUDA, "batch setup: %s", cudaGetErrorString(ce)));
+    // One persistent launch per run unless a member asks for one launch per generation or
+    // uses the convergence test.
+    bt->persistent = true;
+    for (qieo_instance *q : members)
+        if (q->flags & (QIEO_FLAG_CONVERGE | QIEO_FLAG_PER_GENERATION)) bt->persistent = false;
     for (qieo_instance *q : members) {
         auto it = std::find_if(bt->groups.begin(), bt->groups.end(), [&](const qieo_batch::Group &g) {
             return g.narrow == (q->narrow != 0) && g.rule == q->rule;
@@ -1949,7 +2117,10 @@ qieo_status qieo_batch_run(qieo_batch *bt, int32_t G)
         CUDA_TRY(cudaStreamWaitEvent(bt->stream, bt->ev_in, 0));
     }
     const bool first_time = bt->run_lengths_seen[G]++ == 0;
-    if (first_time && !bt->graphs.count(G)) {
+    if (bt->persistent) {
+        qieo_status st = enqueue_batch_persistent(bt, G);
+        if (st != QIEO_OK) return st;
+    } else if (first_time && !bt->graphs.count(G)) {
         qieo_status st = enqueue_batch_run(bt, G);
         if (st != QIEO_OK) return st;
     } else {

@@ -150,6 +150,8 @@ struct GenParams {
     int32_t nsegs;
     int32_t row0;                 // chromosome index of row 0 in the draws' counters (a row
                                   // block of a population sharded by rows; 0 otherwise)
+    unsigned long long *gen_ns;   // resident form: device clock (ns) at the start of each
+                                  // generation of the run and at its end, or NULL
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -390,10 +392,21 @@ __shared__ uint4 s_item_bytes[kThreads];   // per thread: w4a, w4b, v4a, v4b
 // shared load instead of forming them (see ring_segment for where it pays).
 __shared__ uint4 s_delta[kThreads];
 
-// kSegDelta: form the rule R1 delta words of the segment (s_delta).
-template <bool kNarrow, bool kCip, bool kSegDelta = false>
-__device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int tile, int v_in,
-                                          int tile_vecs, const uint8_t *elite_row)
+// The elite alleles of the thread's vector; kSegDelta: also the rule R1 delta words of the
+// segment (s_delta).
+template <bool kCip, bool kSegDelta = false>
+__device__ __forceinline__ void seg_elite(SegCtx &g, const uint8_t *elite_row)
+{
+    g.e8 = (kCip && g.active) ? (uint32_t)__ldcg(elite_row + g.vec) : 0u;
+    if (kCip && kSegDelta)   // read back by this thread only (rule R1 passes)
+        s_delta[threadIdx.x] = make_uint4(delta_pair(g.e8 & 3u, 3u), delta_pair((g.e8 >> 2) & 3u, 3u),
+                                          delta_pair((g.e8 >> 4) & 3u, 3u), delta_pair((g.e8 >> 6) & 3u, 3u));
+}
+
+// The thread's vector of a tile and its 8 items (registers, and the byte vectors in the
+// thread's slot of s_item_bytes).
+template <bool kNarrow>
+__device__ __forceinline__ void seg_items(const GenParams &p, SegCtx &g, int tile, int v_in, int tile_vecs)
 {
     g.vec = tile * tile_vecs + v_in;
     g.active = g.vec < p.svec;
@@ -420,11 +433,15 @@ __device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int til
         g.vi[0] = d.x; g.vi[1] = d.y; g.vi[2] = d.z; g.vi[3] = d.w;
         g.vi[4] = e.x; g.vi[5] = e.y; g.vi[6] = e.z; g.vi[7] = e.w;
     }
-    g.e8 = (kCip && g.active) ? (uint32_t)__ldcg(elite_row + g.vec) : 0u;
-    if (kCip && kSegDelta)   // read back by this thread only (rule R1 passes)
-        s_delta[threadIdx.x] = make_uint4(delta_pair(g.e8 & 3u, 3u), delta_pair((g.e8 >> 2) & 3u, 3u),
-                                          delta_pair((g.e8 >> 4) & 3u, 3u), delta_pair((g.e8 >> 6) & 3u, 3u));
     g.ctr0 = 2u * (uint32_t)g.vec;
+}
+
+template <bool kNarrow, bool kCip, bool kSegDelta = false>
+__device__ __forceinline__ void seg_setup(const GenParams &p, SegCtx &g, int tile, int v_in,
+                                          int tile_vecs, const uint8_t *elite_row)
+{
+    seg_items<kNarrow>(p, g, tile, v_in, tile_vecs);
+    seg_elite<kCip, kSegDelta>(g, elite_row);
 }
 
 // Philox key sources: the ten round keys of a single instance live in the kernel parameter
@@ -473,7 +490,8 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
 // pass in the whole warp, the alleles are the bits of the state itself, no Philox call is
 // needed, and the state is unchanged (fixed = true: the caller skips its store). The test
 // is skipped for 15 passes after it fails, which keeps its cost low while the population
-// is still spread out.
+// is still spread out. (An exponential backoff, 1, 3, 7 then 15 passes, measured slower:
+// c3's saturated generations 186 vs 177 us, c2's spread ones 15.8 vs 14.9 us.)
 template <bool kNarrow, int kRule, bool kCip, class Keys, bool kSegDelta = false>
 __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys, const SegCtx &g, uint4 s,
                                             uint32_t xo, int32_t c, int32_t t,
@@ -993,6 +1011,8 @@ __device__ __forceinline__ void grid_arrive(const GenParams &p)
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(p.ticket) : "memory");
 }
 
+// kSpin: poll without sleeping (the resident form, whose generations are short).
+template <bool kSpin = false>
 __device__ __forceinline__ bool grid_wait(const GenParams &p, unsigned int target)
 {
     __shared__ int s_ok;
@@ -1005,7 +1025,7 @@ __device__ __forceinline__ bool grid_wait(const GenParams &p, unsigned int targe
                 break;
             }
             if (ld_acquire(p.error) != 0 || global_ns() > deadline) break;
-            __nanosleep(32);
+            if (!kSpin) __nanosleep(32);
         }
         if (!ok) atomicOr(p.error, kErrBarrierTimeout);
         s_ok = ok;
@@ -1175,6 +1195,195 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_k
         e = __ldcg(p.elite_idx);
     }
     final_cip_body<kRule>(p, b, t0 + G - 1, e);
+}
+
+// ---------------------------------------------------------------------------------------
+// Resident form: a cooperative run whose blocks keep their share of the state in shared
+// memory for the whole run. A population whose state fits in the SMs' combined shared
+// memory (about 34 MB on a GB300, e.g. 1,024 x 10,000 genes = 20 MB) is read from device
+// memory once at the start of a run and written back once at its end; in between, a
+// generation reads and writes nothing but the allele plane, the row sums and the elite key
+// in device memory. Each block owns the same equal share of tile-rows in every generation
+// (no queue: the share is fixed because its state lives in the block), and the blocks meet
+// at the bounded grid barrier of the deferred close between generations.
+// ---------------------------------------------------------------------------------------
+
+// One segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation on the
+// resident state st (thread (r_sub, v_in) of row rr at st[rr * tile_vecs + v_in]).
+// g: the segment's items (seg_items, this tile) and elite alleles (seg_elite).
+template <bool kNarrow, int kRule, bool kCip, bool kSegDelta>
+__device__ __forceinline__ void resident_segment(const GenParams &p, const BlockShare &b, const SegCtx &g,
+                                                 int ra, int seg_rows, int32_t t, const uint8_t *x_prev,
+                                                 uint8_t *x_cur, const unsigned char *thr_bytes, uint4 *st,
+                                                 uint32_t *s_acc32, unsigned long long *s_acc64,
+                                                 int &countdown)
+{
+    const int rpp = b.rows_per_pass;
+    const int passes = (seg_rows + rpp - 1) / rpp;
+    const int ra_key = ra + p.row0;
+    uint4 *sp = st + (size_t)b.r_sub * b.tile_vecs + b.v_in;
+    const int sstep = rpp * b.tile_vecs;
+    uint8_t *xptr = x_cur + ((size_t)ra + b.r_sub) * p.xstride + g.vec;
+    const uint8_t *xoptr = x_prev + ((size_t)ra + b.r_sub) * p.xstride + g.vec;
+    const size_t xstep = (size_t)rpp * p.xstride;
+    int rr = b.r_sub;
+    for (int pass = 0; pass < passes; ++pass) {
+        const bool ok = rr < seg_rows;
+        const bool live = g.active && ok;
+        uint4 sv = live ? *sp : make_uint4(0, 0, 0, 0);
+        const uint32_t xo = (kRule == 1 && kCip && live) ? (uint32_t)*xoptr : 0u;
+        uint32_t xbits, accn;
+        int64_t acw, acv;
+        bool fixed;
+        sv = qubit_pass<kNarrow, kRule, kCip, ParamKeys, kSegDelta>(p, ParamKeys{p}, g, sv, xo, ra_key + rr, t,
+                                                                    thr_bytes, fixed, countdown, xbits, accn,
+                                                                    acw, acv);
+        if (live) {
+            if (!fixed) *sp = sv;
+            *xptr = (uint8_t)xbits;
+        }
+        add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
+        sp += sstep;
+        xptr += xstep;
+        xoptr += xstep;
+        rr += rpp;
+    }
+    flush_segment<kNarrow>(p, t, ra, seg_rows, s_acc32, s_acc64);
+}
+
+// Copies the block's share of the state between device memory and the resident copy
+// (to_smem: at the start of a run; otherwise at its end), optionally applying the CIP of
+// generation t toward elite row `elite` on the way out (the run's final rotation).
+template <int kRule, bool kToSmem>
+__device__ __forceinline__ void resident_copy(const GenParams &p, const BlockShare &b, uint4 *st,
+                                              int32_t t, const uint8_t *elite)
+{
+    const int64_t n = (b.u_end - b.u_begin) * b.tile_vecs;
+    const int sh = __ffs(b.tile_vecs) - 1;
+    const uint8_t *xl = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint32_t k8 = (uint32_t)(8 * p.K) * 0x00010001u;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+        const int64_t u = b.u_begin + (i >> sh);
+        const int tile = (int)(u / p.np);
+        const int64_t row = u - (int64_t)tile * p.np;
+        const int vec = tile * b.tile_vecs + (int)(i & (b.tile_vecs - 1));
+        if (vec >= p.svec) continue;
+        const size_t gi = (size_t)row * p.svec + vec;
+        if constexpr (kToSmem) {
+            st[i] = p.state[gi];
+        } else {
+            const uint32_t e8 = elite[vec];
+            const uint32_t m8 = kRule == 1 ? (e8 ^ (uint32_t)xl[(size_t)row * p.xstride + vec]) : 0xffu;
+            p.state[gi] = rotate_vec(st[i], e8, m8, k8);
+        }
+    }
+}
+
+// Records of generation t in a resident run (block 0, all threads): the best-so-far record
+// is kept by thread 0 in registers for the whole run (no other block writes it), so writing
+// a generation's records costs no read of device memory unless the best row changes.
+__device__ __forceinline__ void record_resident(const GenParams &p, int32_t t, int32_t e, int64_t f,
+                                                int64_t &best_f, int64_t &best_g)
+{
+    __shared__ int32_t s_improved;
+    if (threadIdx.x == 0) {
+        p.hist_e[t] = e;
+        p.hist_f[t] = f;
+        *p.elite_idx = e;
+        const int improved = (best_g < 0 || f > best_f) ? 1 : 0;
+        if (improved) {
+            best_f = f;
+            best_g = t;
+            p.best[0] = f;
+            p.best[1] = t;
+            p.best[2] = e;
+        }
+        s_improved = improved;
+    }
+    __syncthreads();
+    if (s_improved) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(
+            p.xbits + (size_t)(t & 1) * p.xplane + (size_t)e * p.xstride);
+        uint4 *dst = reinterpret_cast<uint4 *>(p.best_row);
+        for (int i = threadIdx.x; i < p.xstride / 16; i += kThreads) dst[i] = __ldcg(src + i);
+    }
+}
+
+// Dynamic shared memory: [resident state: share_max tile-rows x tile_vecs uint4][row sums].
+template <bool kNarrow, int kRule, bool kSegDelta>
+__global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) resident_run_kernel(const GenParams p, int32_t G,
+                                                                                  int32_t share_max)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    __shared__ int s_e;
+    __shared__ long long s_f;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    load_thresholds(p, s_thr);
+    grid_dependency_wait();
+    const BlockShare b = block_share(p);
+    uint4 *st = reinterpret_cast<uint4 *>(smem_raw);
+    unsigned char *acc = smem_raw + (size_t)share_max * b.tile_vecs * sizeof(uint4);
+    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(acc);
+    unsigned long long *s_acc64 = reinterpret_cast<unsigned long long *>(acc);
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    const int32_t t0 = *p.gen;
+    resident_copy<kRule, true>(p, b, st, t0, nullptr);
+    clear_row_sums<kNarrow>(p.seg_rows_max, s_acc32, s_acc64);   // (its barrier orders the copy)
+    int countdown = 0;
+    int32_t e = 0;
+    int64_t best_f = 0, best_g = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        best_f = __ldcg(p.best);
+        best_g = __ldcg(p.best + 1);
+    }
+    const bool stamp = p.gen_ns != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) p.gen_ns[0] = global_ns();
+    for (int32_t g = 0; g <= G; ++g) {
+        const int32_t t = t0 + g;
+        int64_t f = 0;
+        if (g > 0) {
+            if (!grid_wait<true>(p, (unsigned int)g * gridDim.x)) return;
+            if (stamp) p.gen_ns[g] = global_ns();
+            if (threadIdx.x == 0) {
+                int32_t ee;
+                int64_t ff;
+                elite_from_key(p, t - 1, ee, ff);
+                s_e = ee;
+                s_f = ff;
+            }
+            __syncthreads();
+            e = s_e;
+            f = s_f;
+            if (blockIdx.x == 0) record_resident(p, t - 1, e, f, best_f, best_g);
+        }
+        if (g == G) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *key_slot(p, t + 1) = 0ull;
+        const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+        uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+        const uint8_t *elite_row = x_prev + (size_t)e * p.xstride;
+        for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
+            const int tile = (int)(u0 / p.np);
+            const int ra = (int)(u0 - (int64_t)tile * p.np);
+            const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
+            uint4 *seg_st = st + (size_t)(u0 - b.u_begin) * b.tile_vecs;
+            SegCtx sg;
+            seg_items<kNarrow>(p, sg, tile, b.v_in, b.tile_vecs);
+            if (g == 0) {
+                resident_segment<kNarrow, kRule, false, kSegDelta>(p, b, sg, ra, seg_rows, t, x_prev, x_cur,
+                                                                   thr_bytes, seg_st, s_acc32, s_acc64, countdown);
+            } else {
+                seg_elite<true, kSegDelta>(sg, elite_row);
+                resident_segment<kNarrow, kRule, true, kSegDelta>(p, b, sg, ra, seg_rows, t, x_prev, x_cur,
+                                                                  thr_bytes, seg_st, s_acc32, s_acc64, countdown);
+            }
+            u0 += seg_rows;
+        }
+        grid_arrive(p);
+    }
+    // the run's final CIP on the way back to device memory
+    const int32_t t_last = t0 + G - 1;
+    resident_copy<kRule, false>(p, b, st, t_last,
+                                p.xbits + (size_t)(t_last & 1) * p.xplane + (size_t)e * p.xstride);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1581,6 +1790,8 @@ struct BatchArgs {
     const int32_t *inst_segs;     // [n] segments per instance
     unsigned int *queue;          // [2] next segment to take, blocks finished (both 0
                                   // between launches: the last block clears them)
+    unsigned int *done;           // [n] persistent form: generations of the run each
+                                  // instance has closed (0 at the start of a run)
     int32_t nsegs;
     int32_t seg_rows_max;
 };
@@ -1662,6 +1873,100 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_generation_ke
     allow_dependent_launch();
     // The last block to finish clears the queue for the next launch (which reads it only
     // after this grid has completed).
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 1, 1u) == gridDim.x - 1u) {
+            a.queue[0] = 0u;
+            a.queue[1] = 0u;
+        }
+    }
+}
+
+// Persistent form of a batched run: generations 2 .. G of the run (the first, which applies
+// no CIP, is one batch_generation_kernel launch before it) in one cooperative launch. The
+// work items are (step g, segment) in one queue over the launch, step-major with each step's
+// segments largest first; a block takes the next item with one atomic. Before computing a
+// segment of step g >= 1 of instance i the block waits (bounded, like the grid barrier of
+// run_kernel) until instance i has closed its generation of step g - 1, which the block that
+// finished that generation's last segment announces in done[i]. There is no grid-wide
+// barrier: while the last segments of one instance's generation run, blocks already work on
+// other instances' next generation. Items are taken in queue order and every block of the
+// grid is resident (cooperative launch), so the earliest unfinished item never waits on a
+// later one. Members with the convergence test use the per-generation form.
+template <bool kNarrow, int kRule>
+__global__ void __launch_bounds__(kThreads, kNarrow ? 4 : 2) batch_run_kernel(const BatchArgs a, int32_t G)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    __shared__ int s_last, s_ok;
+    __shared__ uint32_t s_q;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemParts m = carve_smem<true>(smem_raw);
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    uint4 *slots = m.ring + threadIdx.x;
+    grid_dependency_wait();
+    clear_row_sums<kNarrow>(a.seg_rows_max, m.acc32, m.acc64);
+    int countdown = 0;
+    int32_t table_K = -1;
+    const uint32_t total = (uint32_t)G * (uint32_t)a.nsegs;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const uint32_t q = s_q;
+        if (q >= total) break;
+        const int32_t step = (int32_t)(q / (uint32_t)a.nsegs);
+        const BatchSeg sg = a.segs[q - (uint32_t)step * (uint32_t)a.nsegs];
+        const GenParams &p = a.params[sg.inst];
+        if (p.K != table_K) {               // table of this instance's D (row sums are clear)
+            table_K = p.K;
+            for (int i = threadIdx.x; i < 2 * p.K + 1; i += kThreads) s_thr[i] = p.thr[i];
+        }
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (step > 0) {                 // the instance's previous generation must be closed
+                const int32_t *dw = reinterpret_cast<const int32_t *>(a.done + sg.inst);
+                const uint64_t deadline = global_ns() + p.wait_ns;
+                ok = 0;
+                for (uint32_t it = 0; it < (1u << 30); ++it) {
+                    if (ld_acquire(dw) >= step) {
+                        ok = 1;
+                        break;
+                    }
+                    if (ld_acquire(p.error) != 0 || global_ns() > deadline) break;
+                }
+                if (!ok) atomicOr(p.error, kErrBarrierTimeout);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) continue;                // reported through the instance's error word
+        const int32_t t = __ldcg(p.gen);
+        const int32_t e_prev = __ldcg(p.elite_idx);
+        const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+        uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+        const BlockShare b = tile_geometry(p.lanes, p.warps);
+        ring_segment<kNarrow, kRule, true, InlineKeys, false, false, true>(
+            p, InlineKeys{p.rk0[0], p.rk1[0]}, b, sg.tile, sg.ra, sg.rows, t, x_prev, x_cur,
+            x_prev + (size_t)e_prev * p.xstride, thr_bytes, slots, m.acc32, m.acc64, countdown);
+        // the block that finishes the generation's last segment closes it and announces it
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned int prev = atom_add_acq_rel(p.ticket, 1u);
+            s_last = (prev == (unsigned int)a.inst_segs[sg.inst] - 1u) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            close_generation(p, t);
+            if (threadIdx.x == 0) {
+                *p.gen = t + 1;
+                *p.ticket = 0u;
+                *p.bar_gen = t + 1;
+                __threadfence();
+                st_release(reinterpret_cast<int32_t *>(a.done + sg.inst), step + 1);
+            }
+            __syncthreads();
+        }
+    }
+    // The last block to finish clears the queue for the next run.
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(a.queue + 1, 1u) == gridDim.x - 1u) {

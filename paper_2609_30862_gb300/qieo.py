@@ -36,6 +36,7 @@ QIEO_CONVERGE_WINDOW = 20
 QIEO_FLAG_STATE_I8 = 0x100
 QIEO_FLAG_PER_GENERATION = 0x200
 QIEO_FLAG_TIME_GENERATIONS = 0x400
+QIEO_FLAG_STREAMED = 0x800
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
@@ -82,7 +83,7 @@ class qieo_params(C.Structure):
 class qieo_launch_shape(C.Structure):
     _fields_ = [("lanes_per_row", C.c_int32), ("warps_per_row", C.c_int32),
                 ("grid_ctas", C.c_int32), ("narrow", C.c_int32), ("tiles", C.c_int32),
-                ("rows_per_cta", C.c_int32), ("persistent", C.c_int32)]
+                ("rows_per_cta", C.c_int32), ("persistent", C.c_int32), ("resident", C.c_int32)]
 
 
 class qieo_server_config(C.Structure):

@@ -61,6 +61,24 @@ def test_batch_matches_each_instance_alone():
         inst.close()
 
 
+def test_batch_per_generation_form():
+    """A member with QIEO_FLAG_PER_GENERATION makes the batch run one launch per generation
+    (graph replay for repeated lengths) instead of one persistent launch; same results."""
+    made = []
+    for i, s_ in enumerate(SPECS[:7]):
+        ng, np_, rule, D, lam, wide = s_
+        prob = W.knapsack(ng, 100 + i) if not wide else make(s_, i)[0]
+        inst = Q.Instance(prob, np_, seed=i + 1, inst=i, D=D, lam=lam, rule=rule,
+                          flags=Q.QIEO_FLAG_PER_GENERATION if i == 3 else 0)
+        made.append((prob, inst))
+    with Q.Batch([m[1] for m in made]) as b:
+        for g in (6, 6, 4):
+            b.run(g)
+    for i, (s_, (prob, inst)) in enumerate(zip(SPECS[:7], made)):
+        check_against_oracle(inst, prob, s_[1], 16, i + 1, i, s_[3], s_[4], s_[2])
+        inst.close()
+
+
 def test_batch_and_single_runs_interleave():
     """Members keep their own generation counters: single runs and batch runs mix."""
     made = [make(s, i) for i, s in enumerate(SPECS[:6])]

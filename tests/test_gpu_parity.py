@@ -76,14 +76,17 @@ def test_device_philox_matches_oracle():
         assert np.array_equal(got, O.philox4x32_10(row[:4], row[4:]))
 
 
-@pytest.mark.parametrize("flags", [0, Q.QIEO_FLAG_PER_GENERATION])
+@pytest.mark.parametrize("flags", [0, Q.QIEO_FLAG_STREAMED, Q.QIEO_FLAG_PER_GENERATION])
 def test_c1_full_run(flags):
     """Ng = 100, Np = 64, 500 generations, Philox seed 1: the small named workload, as one
-    cooperative launch (the default at this size) and as one launch per generation."""
+    cooperative launch with the state resident in shared memory (the default at this
+    size), as one cooperative launch streaming the state, and as one launch per
+    generation."""
     c = W.WORKLOADS["c1"]
     shape = compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
                     inst=c["inst"], flags=flags)
-    assert shape.persistent == (0 if flags else 1)
+    assert shape.persistent == (0 if flags == Q.QIEO_FLAG_PER_GENERATION else 1)
+    assert shape.resident == (1 if flags == 0 else 0)
 
 
 def test_c1_rule_r2():
@@ -110,6 +113,26 @@ def test_cooperative_launch(rule):
             flags=Q.QIEO_FLAG_COOPERATIVE)
     compare(W.knapsack(2500, 15), 60, [7, 7], seed=15, rule=rule,
             flags=Q.QIEO_FLAG_COOPERATIVE | Q.QIEO_FLAG_REGISTER_PREFETCH)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+@pytest.mark.parametrize("flags,shape", [(0, None), (Q.QIEO_FLAG_FORCE_WIDE, None), (0, (32, 2, 0)),
+                                         (0, (4, 1, 7)), (0, (32, 8, 40)), (0, (1, 1, 64)),
+                                         (Q.QIEO_FLAG_TIME_GENERATIONS, None)])
+def test_resident_form(rule, flags, shape):
+    """The state kept in shared memory for a whole run (one cooperative launch): across run
+    boundaries, with wide item sums, with several rows per pass, shares that span two tiles,
+    one lane per row tile (256 rows per pass), and with per-generation device timestamps."""
+    prob = W.knapsack(5000, 17)
+    got = compare(prob, 90, [9, 9, 5], seed=17, rule=rule, flags=flags, shape=shape)
+    assert got.resident == 1 and got.persistent == 1
+
+
+def test_resident_form_wide_items_and_large_lambda():
+    rng = np.random.default_rng(4)
+    prob = W.custom_problem(rng.integers(0, 3000, 900), rng.integers(0, 3000, 900), 3000 * 900 // 3)
+    got = compare(prob, 70, [13, 7], seed=4, lam=7, rule=1)
+    assert got.resident == 1 and got.narrow == 0
 
 
 @pytest.mark.parametrize("rule", [0, 1])
@@ -247,12 +270,16 @@ def test_reset_and_zero_generations():
     compare(prob, 16, [17], seed=1)
 
 
-def test_c2_full_size():
+@pytest.mark.parametrize("flags", [0, Q.QIEO_FLAG_STREAMED])
+def test_c2_full_size(flags):
     """Ng = 10,000, Np = 1,024, 1,000 generations: bit-exact against the OpenMP build of
-    the oracle (identical to the serial one by construction and by test)."""
+    the oracle (identical to the serial one by construction and by test), with the state
+    resident in shared memory (the default: 20 MB fits the SMs' shared memory) and
+    streamed from device memory every generation."""
     c = W.WORKLOADS["c2"]
-    compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
-            inst=c["inst"], kind="omp")
+    shape = compare(W.knapsack(c["ng"], c["item_seed"]), c["np"], [c["gens"]], seed=c["seed"],
+                    inst=c["inst"], kind="omp", flags=flags)
+    assert shape.resident == (1 if flags == 0 else 0)
 
 
 def test_c3_full_run_properties():
