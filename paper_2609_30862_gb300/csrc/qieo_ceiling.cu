@@ -7,10 +7,10 @@
 // multiplies of Philox run on a half-rate pipe at a fraction of the simple-integer rate, and
 // the compiler's instruction mix decides how the rest share the issue slots. This file
 // measures that ceiling on the device itself: the same per-gene arithmetic the drawn pass
-// of the generation kernel does (the same helpers: rotate_pair, philox4x32_10_rk with the
-// round keys in the parameter block, the shared-memory threshold table), with the state
-// held in registers instead of streamed from memory, no per-row reduction and no stores
-// but one word per thread at the end. A second kernel runs Philox4x32-10 alone.
+// of the generation kernel does (the same helpers: rotate_pair_signed, philox4x32_10_rk
+// with the round keys in the parameter block, the shared-memory threshold table), with the
+// state held in registers instead of streamed from memory, no per-row reduction and no
+// stores but one word per thread at the end. A second kernel runs Philox4x32-10 alone.
 //
 // Both kernels use the generation kernel's launch shape (256 threads, three blocks per SM,
 // one block per SM-slot) and draw with the same counters (gene vector, chromosome,
@@ -66,9 +66,9 @@ qieo_status ceil_fail(qieo_status st, const char *fmt, ...)
     } while (0)
 
 // The drawn pass's per-gene arithmetic over `passes` rows of one 8-gene vector per thread:
-// CIP toward a fixed elite pattern (rule R1 deltas formed once, as the generation kernel
-// forms them once per segment), two Philox4x32-10 calls keyed (2 vec + i, row, t), eight
-// table lookups and compares, the allele byte and the packed (v << 16 | w) item sums.
+// CIP toward a fixed elite pattern (rule R1 signed steps formed once, as the generation
+// kernel forms them once per segment), two Philox4x32-10 calls keyed (2 vec + i, row, t),
+// eight table lookups and compares, the allele byte and the packed (v << 16 | w) item sums.
 __global__ void __launch_bounds__(kThreads, kBlocksPerSm) drawn_ceiling_kernel(const CeilingParams p)
 {
     __shared__ uint32_t s_thr[2 * kK + 1];
@@ -83,8 +83,10 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) drawn_ceiling_kernel(c
         wv[i] = ((w + 5u) << 16) | w;
     }
     const uint32_t e8 = (vec * 37u + 11u) & 0xffu;
-    const uint32_t d0 = qieo::delta_pair(e8 & 3u, 3u), d1 = qieo::delta_pair((e8 >> 2) & 3u, 3u);
-    const uint32_t d2 = qieo::delta_pair((e8 >> 4) & 3u, 3u), d3 = qieo::delta_pair((e8 >> 6) & 3u, 3u);
+    const uint32_t d0 = qieo::signed_step(qieo::delta_pair(e8 & 3u, 3u));
+    const uint32_t d1 = qieo::signed_step(qieo::delta_pair((e8 >> 2) & 3u, 3u));
+    const uint32_t d2 = qieo::signed_step(qieo::delta_pair((e8 >> 4) & 3u, 3u));
+    const uint32_t d3 = qieo::signed_step(qieo::delta_pair((e8 >> 6) & 3u, 3u));
     const uint32_t off_top = 8u * kK;
     const uint32_t k8 = off_top * 0x00010001u;
     uint4 s = make_uint4(4u * kK * 0x00010001u, 4u * kK * 0x00010001u, 4u * kK * 0x00010001u,
@@ -93,10 +95,10 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) drawn_ceiling_kernel(c
     const uint32_t row0 = blockIdx.x * 7u;
     uint32_t chk = 0u;
     for (int pass = 0; pass < p.passes; ++pass) {
-        s.x = qieo::rotate_pair(s.x, d0, k8);
-        s.y = qieo::rotate_pair(s.y, d1, k8);
-        s.z = qieo::rotate_pair(s.z, d2, k8);
-        s.w = qieo::rotate_pair(s.w, d3, k8);
+        s.x = qieo::rotate_pair_signed(s.x, d0, k8);
+        s.y = qieo::rotate_pair_signed(s.y, d1, k8);
+        s.z = qieo::rotate_pair_signed(s.z, d2, k8);
+        s.w = qieo::rotate_pair_signed(s.w, d3, k8);
         const uint32_t c = row0 + (uint32_t)pass;
         const qieo::Draw4 r0 = qieo::philox4x32_10_rk(ctr0, c, (uint32_t)p.t, 0u, p.rk0, p.rk1);
         const qieo::Draw4 r1 = qieo::philox4x32_10_rk(ctr0 + 1u, c, (uint32_t)p.t, 0u, p.rk0, p.rk1);

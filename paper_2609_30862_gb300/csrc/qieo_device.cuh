@@ -79,6 +79,20 @@ __device__ __forceinline__ uint32_t rotate_pair(uint32_t s, uint32_t d, uint32_t
     return __vminu2(__vmaxu2(s + d, 0x00040004u) - 0x00040004u, k8);
 }
 
+// The same step with the delta given as a signed per-halfword step sd = d - 4 in {-4, 0, 4}
+// (16-bit two's complement halves): 4n' = min(max(4n + sd, 0), 8K) with a per-halfword add
+// (no carry between the halves) and a signed per-halfword maximum, three operations instead
+// of four. 4n + sd lies in [-4, 8K + 4], inside the signed 16-bit range for 8K <= 8000.
+__device__ __forceinline__ uint32_t signed_step(uint32_t d)
+{
+    return __vsub2(d, 0x00040004u);
+}
+
+__device__ __forceinline__ uint32_t rotate_pair_signed(uint32_t s, uint32_t sd, uint32_t k8)
+{
+    return __vminu2(__vmaxs2(__vadd2(s, sd), 0u), k8);
+}
+
 __device__ __forceinline__ uint4 rotate_vec(uint4 s, uint32_t e8, uint32_t m8, uint32_t k8)
 {
     s.x = rotate_pair(s.x, delta_pair(e8 & 3u, m8 & 3u), k8);

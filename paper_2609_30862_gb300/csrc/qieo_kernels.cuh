@@ -388,8 +388,9 @@ struct SegCtx {
 __shared__ uint4 s_item_bytes[kThreads];   // per thread: w4a, w4b, v4a, v4b
 // Rule R1 moves every qubit toward the elite's allele, so the CIP deltas of a vector depend
 // only on the elite's 8 alleles: kernels built with kSegDelta form them once per segment
-// (four delta_pair words) into this per-thread slot, and a pass reads them with one 16-byte
-// shared load instead of forming them (see ring_segment for where it pays).
+// (four delta_pair words, as signed steps for rotate_pair_signed) into this per-thread
+// slot, and a pass reads them with one 16-byte shared load instead of forming them (see
+// ring_segment for where it pays).
 __shared__ uint4 s_delta[kThreads];
 
 // The elite alleles of the thread's vector; kSegDelta: also the rule R1 delta words of the
@@ -399,8 +400,10 @@ __device__ __forceinline__ void seg_elite(SegCtx &g, const uint8_t *elite_row)
 {
     g.e8 = (kCip && g.active) ? (uint32_t)__ldcg(elite_row + g.vec) : 0u;
     if (kCip && kSegDelta)   // read back by this thread only (rule R1 passes)
-        s_delta[threadIdx.x] = make_uint4(delta_pair(g.e8 & 3u, 3u), delta_pair((g.e8 >> 2) & 3u, 3u),
-                                          delta_pair((g.e8 >> 4) & 3u, 3u), delta_pair((g.e8 >> 6) & 3u, 3u));
+        s_delta[threadIdx.x] = make_uint4(signed_step(delta_pair(g.e8 & 3u, 3u)),
+                                          signed_step(delta_pair((g.e8 >> 2) & 3u, 3u)),
+                                          signed_step(delta_pair((g.e8 >> 4) & 3u, 3u)),
+                                          signed_step(delta_pair((g.e8 >> 6) & 3u, 3u)));
 }
 
 // The thread's vector of a tile and its 8 items (registers, and the byte vectors in the
@@ -540,12 +543,12 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
     }
 
     if (kCip) {
-        if (kRule == 0 && kSegDelta) {  // R1: the segment's delta words
+        if (kRule == 0 && kSegDelta) {  // R1: the segment's signed steps
             const uint4 d = s_delta[threadIdx.x];
-            s.x = rotate_pair(s.x, d.x, k8);
-            s.y = rotate_pair(s.y, d.y, k8);
-            s.z = rotate_pair(s.z, d.z, k8);
-            s.w = rotate_pair(s.w, d.w, k8);
+            s.x = rotate_pair_signed(s.x, d.x, k8);
+            s.y = rotate_pair_signed(s.y, d.y, k8);
+            s.z = rotate_pair_signed(s.z, d.z, k8);
+            s.w = rotate_pair_signed(s.w, d.w, k8);
         } else {
             s = rotate_vec(s, g.e8, m8, k8);
         }
