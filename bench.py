@@ -111,13 +111,14 @@ def load_peaks() -> tuple[dict, str]:
 
 
 def profile_traffic(kernel: str, workload: str):
-    """Per-launch DRAM traffic from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    """DRAM traffic per generation (read + write bytes; per launch for the kernels launched
+    once per generation) from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(r"traffic_bytes_per_generation:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not m or not h or h.group(1) != kernel_source_hash():
         return None
@@ -441,6 +442,8 @@ def run_gpu(a):
     kname = ("resident_run_kernel" if shape.resident else "run_kernel" if shape.persistent
              else "generation_kernel")
     roof["traffic"] = None if a.state_i8 else profile_traffic(kname, a.workload)
+    roof["traffic_per"] = ("generation (one launch per generation)" if not shape.persistent
+                           else "generation (the run's launch divided by its generations)")
     if roof["traffic"]:
         roof["frac_dram_measured"] = roof["traffic"] / launch_s / 1e9 / hbm_peak
     roof["kernel"] = ("resident_run_kernel (one cooperative launch per run, state in shared memory)"
@@ -712,7 +715,10 @@ def run_batched(a):
             "kernel": ("batch_generation_kernel (one launch per generation for all members)"
                        if a.per_generation else
                        "batch_run_kernel (one persistent launch per run for all members)"),
-            "us_per_generation": launch_s * 1e6}
+            "us_per_generation": launch_s * 1e6,
+            "traffic_per": "generation (the persistent launch divided by its generations)"}
+    if roof["traffic"]:
+        roof["frac_dram_measured"] = roof["traffic"] / launch_s / 1e9 / hbm_peak
     value = world * n * a.steps / tb
     line = {
         "metric": "solves/s (256 instances x 300 generations)", "value": value, "unit": "solves/s",
