@@ -701,22 +701,39 @@ def run_batched(a):
     h2d = sum(((sp.ng + 7) // 8) * 8 * 4 * 3 + 4 * 51 for sp in specs)
     d2h = sum(((sp.ng + 7) // 8 + 15) // 16 * 16 + 24 for sp in specs)
 
-    # Roofline of batch_generation_kernel: a batched run is G launches plus one final CIP
-    # launch over all members; per launch the algorithmic bytes are 4 B x every member's
-    # genes (state read + write), timed as the run / G.
+    # Roofline of the batched kernels: per generation the algorithmic work is every member's
+    # genes -- 4 B of state each, read and written, and the drawn pass's integer work --
+    # timed as the run / G; the bound is the slower of the two measured ceilings (HBM copy
+    # bandwidth, the integer ceiling of the same per-gene arithmetic).
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     launch_s = run_s / (a.steps * G)
+    ceiling = Q.qieo_measure_integer_ceiling(5)
+    int_peak = ceiling.drawn_genes_per_s
+    t_hbm = STATE_BYTES_PER_GENE * genes_per_gen / (hbm_peak * 1e9)
+    t_int = genes_per_gen / int_peak
     achieved = STATE_BYTES_PER_GENE * genes_per_gen / launch_s / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src,
-            "state_in_l2": state_bytes < L2_BYTES, "traffic": profile_traffic("batch_generation_kernel" if a.per_generation
-                                                       else "batch_run_kernel", "c4"),
-            "kernel": ("batch_generation_kernel (one launch per generation for all members)"
-                       if a.per_generation else
-                       "batch_run_kernel (one persistent launch per run for all members)"),
-            "us_per_generation": launch_s * 1e6,
-            "traffic_per": "generation (the persistent launch divided by its generations)"}
+    if t_hbm >= t_int:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": "%s hbm_gbs" % peak_src}
+    else:
+        ach = genes_per_gen / launch_s / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": int_peak / 1e9, "unit": "Ggene-updates/s",
+                "frac": ach / (int_peak / 1e9),
+                "peak_source": "measured: qieo_measure_integer_ceiling (the drawn pass's per-gene "
+                               "integer work, state in registers, %d blocks, best of %d)" % (
+                                   ceiling.grid_ctas, ceiling.reps)}
+    roof.update({"frac_hbm_4B_formula": achieved / hbm_peak, "hbm_peak_gbs": hbm_peak,
+                 "int_ceiling_gene_updates_per_s": int_peak, "t_hbm_us": t_hbm * 1e6,
+                 "t_int_us": t_int * 1e6,
+                 "state_in_l2": state_bytes < L2_BYTES,
+                 "traffic": profile_traffic("batch_generation_kernel" if a.per_generation
+                                            else "batch_run_kernel", "c4"),
+                 "kernel": ("batch_generation_kernel (one launch per generation for all members)"
+                            if a.per_generation else
+                            "batch_run_kernel (one persistent launch per run for all members)"),
+                 "us_per_generation": launch_s * 1e6,
+                 "traffic_per": "generation (the persistent launch divided by its generations)"})
     if roof["traffic"]:
         roof["frac_dram_measured"] = roof["traffic"] / launch_s / 1e9 / hbm_peak
     value = world * n * a.steps / tb
