@@ -100,6 +100,13 @@ typedef struct {
 #define QIEO_FLAG_STREAMED      0x800 /* never keep the state resident in shared memory
                                          (see qieo_launch_shape.resident): stream it from
                                          device memory every generation */
+#define QIEO_FLAG_SIXTEEN       0x1000 /* one-launch-per-generation runs process 16 genes per
+                                          thread and pass instead of 8 (rule R1, items of at
+                                          most 127, 16-bit state, the default tile; otherwise
+                                          ignored); identical results. Faster while every
+                                          qubit still draws, slower once many saturate
+                                          (4,096 x 100,000 genes: 406 vs 422 us per spread
+                                          generation, 241 vs 184 us per collapsed one) */
 #define QIEO_FLAG_TIME_GENERATIONS 0x400 /* time every generation of a run for
                                             qieo_get_generation_times. In the resident form
                                             (qieo_launch_shape.resident) one thread reads the

@@ -134,6 +134,19 @@ struct qieo_instance {
     size_t res_smem = 0;           // dynamic shared memory of the resident form
     int32_t res_share = 0;         // tile-rows of the largest share
 
+    // sixteen genes per thread and pass (QIEO_FLAG_SIXTEEN): the geometry of
+    // generation_kernel2 (tiles of 512 vectors), its grid, shared memory and segment queue;
+    // a launch takes gp and replaces these fields
+    bool sixteen = false;
+    int32_t max_item = 0;          // largest weight or value
+    int32_t ntile2 = 0, seg_rows_max2 = 0, nsegs2 = 0;
+    int64_t units2 = 0;
+    const int4 *segq2_view = nullptr;
+    int32_t grid2 = 0;
+    size_t smem2 = 0;
+    int4 *segq2 = nullptr;
+    int32_t segq2_cap = 0;
+
     // CUDA graphs keyed by the number of generations of a run; a graph is captured the
     // second time a run length is seen (a one-off run is cheaper to launch directly)
     std::map<int32_t, cudaGraphExec_t> graphs;
@@ -341,10 +354,11 @@ qieo_status resident_blocks(int device, const void *fn, size_t smem, int *bps)
 constexpr int64_t kQueueMinRows = 4;
 constexpr int64_t kQueueMinShare = 64;
 
-qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring)
+qieo_status build_queue_into(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring, int4 *&buf,
+                             int32_t &cap, const int4 *&segq_out, int32_t &nsegs_out)
 {
-    q->gp.segq = nullptr;
-    q->gp.nsegs = 0;
+    segq_out = nullptr;
+    nsegs_out = 0;
     if (!use_ring || !q->owns_block || units < kQueueMinShare * (int64_t)grid) return QIEO_OK;
     std::vector<int4> segs;
     for (int64_t u = 0; u < units;) {
@@ -355,19 +369,23 @@ qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int s
         segs.push_back(make_int4((int)tile, (int)ra, (int)rows, 0));
         u += rows;
     }
-    if ((int64_t)segs.size() > q->segq_cap) {
-        if (q->segq) cudaFreeAsync(q->segq, q->stream);
-        q->segq = nullptr;
-        q->segq_cap = 0;
+    if ((int64_t)segs.size() > cap) {
+        if (buf) cudaFreeAsync(buf, q->stream);
+        buf = nullptr;
+        cap = 0;
         keep_pool_memory(q->device);
-        CUDA_TRY(cudaMallocAsync(&q->segq, segs.size() * sizeof(int4), q->stream));
-        q->segq_cap = (int32_t)segs.size();
+        CUDA_TRY(cudaMallocAsync(&buf, segs.size() * sizeof(int4), q->stream));
+        cap = (int32_t)segs.size();
     }
-    CUDA_TRY(cudaMemcpyAsync(q->segq, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice,
-                             q->stream));
-    q->gp.segq = q->segq;
-    q->gp.nsegs = (int32_t)segs.size();
+    CUDA_TRY(cudaMemcpyAsync(buf, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice, q->stream));
+    segq_out = buf;
+    nsegs_out = (int32_t)segs.size();
     return QIEO_OK;
+}
+
+qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring)
+{
+    return build_queue_into(q, units, grid, seg_max, use_ring, q->segq, q->segq_cap, q->gp.segq, q->gp.nsegs);
 }
 
 // Persistent blocks per SM of the single-instance kernels. The schedulers favour older
@@ -380,6 +398,8 @@ constexpr int kBlocksPerSm = 3;
 // Most dynamic shared memory a block of the resident form may take (of the 227 KB a block
 // can have; the kernel's static tables take the rest).
 constexpr size_t kResidentMaxSmem = 200 * 1024;
+
+qieo_status configure_sixteen(qieo_instance *q);
 
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
 // fills the launch fields of gp.
@@ -452,7 +472,7 @@ qieo_status configure(qieo_instance *q)
     if (qst != QIEO_OK) return qst;
     q->seg_delta = g.nsegs > 0 && q->rule == 0;   // long queued segments: deltas per segment
     drop_graphs(q);
-    return QIEO_OK;
+    return configure_sixteen(q);
 }
 
 void default_tile(qieo_instance *q)
@@ -487,6 +507,21 @@ cudaLaunchConfig_t launch_config(const qieo_instance *q, dim3 grid, size_t smem,
 // per launch).
 cudaError_t launch_gen(const qieo_instance *q, int apply_cip, int do_de, int32_t deferred_g = -1)
 {
+    if (q->sixteen && deferred_g >= 0) {   // 16 genes per thread and pass (deferred close)
+        qieo::GenParams p = q->gp;
+        p.ntile = q->ntile2;
+        p.units = q->units2;
+        p.seg_rows_max = q->seg_rows_max2;
+        p.segq = q->segq2_view;
+        p.nsegs = q->nsegs2;
+        p.apply_cip = apply_cip;
+        p.do_de = do_de;
+        p.deferred = 1;
+        p.g = deferred_g;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = launch_config(q, dim3(q->grid2), q->smem2, attr);
+        return cudaLaunchKernelEx(&cfg, qieo::generation_kernel2, p);
+    }
     qieo::GenParams p = q->gp;
     p.apply_cip = apply_cip;
     p.do_de = do_de;
@@ -661,6 +696,45 @@ bool use_resident(const qieo_instance *q)
     if (!q->resident_fits || q->host_de || q->row_block || !q->key_ok || q->state8) return false;
     return !(q->flags & (QIEO_FLAG_UNFUSED | QIEO_FLAG_PER_GENERATION | QIEO_FLAG_CONVERGE |
                          QIEO_FLAG_COOPERATIVE | QIEO_FLAG_STREAMED));
+}
+
+bool use_cooperative(const qieo_instance *q);
+
+// Sixteen genes per thread and pass (generation_kernel2), when asked for and the run takes
+// the deferred one-launch-per-generation form: rule R1, packed items of at most 127, 16-bit
+// state, the default tile (32 lanes x 8 warps), no convergence test. Its tiles are 512
+// vectors; gp2 carries their geometry and segment queue, gp keeps the 8-gene one for every
+// other launch (batches, cooperative and resident forms, the final CIP).
+qieo_status configure_sixteen(qieo_instance *q)
+{
+    q->sixteen = false;
+    if (!(q->flags & QIEO_FLAG_SIXTEEN) || !q->narrow || q->max_item > 127 || q->rule != 0 || q->state8 ||
+        !q->gp.ring || !q->key_ok || q->host_de || (q->flags & (QIEO_FLAG_CONVERGE | QIEO_FLAG_UNFUSED)) ||
+        q->lanes != 32 || q->warps != 8 || q->row_block || !q->owns_block || use_resident(q) ||
+        use_cooperative(q))
+        return QIEO_OK;
+    constexpr int kTileVecs = 2 * qieo::kThreads;
+    const int ntile = (q->svec + kTileVecs - 1) / kTileVecs;
+    if (ntile > 4095) return QIEO_OK;
+    const int64_t units = (int64_t)ntile * q->np;
+    const size_t ring = (size_t)qieo::kRing2Stages * 2 * qieo::kThreads * sizeof(uint4);
+    const size_t smem0 = ring + (size_t)qieo::kMaxSegRows * 8;
+    int bps = 0;
+    qieo_status st = resident_blocks(q->device, reinterpret_cast<const void *>(qieo::generation_kernel2), smem0, &bps);
+    if (st != QIEO_OK) return st;
+    if (bps < 1) return QIEO_OK;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)q->sm_count * std::min(bps, 2), units));
+    const int64_t share = (units + grid - 1) / grid;
+    const int seg_max = (int)std::max<int64_t>(1, std::min<int64_t>(qieo::kMaxSegRows, share));
+    q->ntile2 = ntile;
+    q->units2 = units;
+    q->seg_rows_max2 = seg_max;
+    st = build_queue_into(q, units, grid, seg_max, true, q->segq2, q->segq2_cap, q->segq2_view, q->nsegs2);
+    if (st != QIEO_OK) return st;
+    q->grid2 = grid;
+    q->smem2 = ring + (size_t)seg_max * 8;
+    q->sixteen = true;
+    return QIEO_OK;
 }
 
 bool use_cooperative(const qieo_instance *q)
@@ -1033,6 +1107,7 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
     q->seed = pa->seed;
     q->inst_id = pa->instance_id;
     q->narrow_items = max_w <= 255 && max_v <= 255 && min_v >= 0;
+    q->max_item = std::max(max_w, max_v);
     q->sum_w = sum_w;
     q->sum_v = sum_v;
     q->sum_absv = sum_absv;
@@ -1198,6 +1273,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->hist_e && !q->fixed_history) cudaFreeAsync(q->hist_e, q->stream);
     if (q->hist_f && !q->fixed_history) cudaFreeAsync(q->hist_f, q->stream);
     if (q->segq) cudaFreeAsync(q->segq, q->stream);
+    if (q->segq2) cudaFreeAsync(q->segq2, q->stream);
     if (q->ext_elite) cudaFreeAsync(q->ext_elite, q->stream);
     if (q->gen_ns) cudaFreeAsync(q->gen_ns, q->stream);
     if (q->h_fit) cudaFreeHost(q->h_fit);

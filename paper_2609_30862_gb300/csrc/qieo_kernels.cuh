@@ -1201,6 +1201,193 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? (kRing ? 4 : 3) : 2) run_k
 }
 
 // ---------------------------------------------------------------------------------------
+// Sixteen genes per thread and pass: two adjacent 8-gene vectors of a row (32 contiguous
+// bytes of state). The per-gene arithmetic is that of qubit_pass; the per-pass work around
+// it -- the copy ring's issue and wait, the countdown, the row-sum reduction, the pointer
+// steps -- is shared by sixteen genes instead of eight. Rule R1 with the segment's signed
+// steps, packed item sums with items <= 127 (32 lanes x 16 genes x 127 < 2^16), 16-bit
+// state; a tile-row is 256 threads x 2 vectors, one row per pass.
+// ---------------------------------------------------------------------------------------
+constexpr int kRing2Stages = 8;
+__shared__ uint4 s_item_bytes2[kThreads];   // the second vector's byte vectors
+__shared__ uint4 s_delta2[kThreads];        // the second vector's signed steps
+
+struct SegCtx2 {
+    uint32_t wv[16];              // packed items (v << 16 | w) of the 16 genes
+    uint32_t e0, e1;              // elite alleles of the two vectors
+    uint32_t ctr0;                // Philox counter word 0 of the first 4 genes
+    int vec;                      // the first vector (even)
+    bool act0, act1;              // vec < svec, vec + 1 < svec
+};
+
+template <bool kCip>
+__device__ __forceinline__ void seg_setup2(const GenParams &p, SegCtx2 &g, int tile, const uint8_t *elite_row)
+{
+    g.vec = tile * (2 * kThreads) + 2 * (int)threadIdx.x;
+    g.act0 = g.vec < p.svec;
+    g.act1 = g.vec + 1 < p.svec;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    uint4 a = z, c = z, d = z, a1 = z, c1 = z, d1 = z;
+    if (g.act0) {
+        a = __ldg(p.items_narrow + 2 * (size_t)g.vec);
+        c = __ldg(p.items_narrow + 2 * (size_t)g.vec + 1);
+        d = __ldg(p.items_narrow + 2 * (size_t)p.svec + g.vec);
+    }
+    if (g.act1) {
+        a1 = __ldg(p.items_narrow + 2 * (size_t)g.vec + 2);
+        c1 = __ldg(p.items_narrow + 2 * (size_t)g.vec + 3);
+        d1 = __ldg(p.items_narrow + 2 * (size_t)p.svec + g.vec + 1);
+    }
+    g.wv[0] = a.x; g.wv[1] = a.y; g.wv[2] = a.z; g.wv[3] = a.w;
+    g.wv[4] = c.x; g.wv[5] = c.y; g.wv[6] = c.z; g.wv[7] = c.w;
+    g.wv[8] = a1.x; g.wv[9] = a1.y; g.wv[10] = a1.z; g.wv[11] = a1.w;
+    g.wv[12] = c1.x; g.wv[13] = c1.y; g.wv[14] = c1.z; g.wv[15] = c1.w;
+    s_item_bytes[threadIdx.x] = d;      // read back by this thread only
+    s_item_bytes2[threadIdx.x] = d1;
+    g.e0 = (kCip && g.act0) ? (uint32_t)__ldcg(elite_row + g.vec) : 0u;
+    g.e1 = (kCip && g.act1) ? (uint32_t)__ldcg(elite_row + g.vec + 1) : 0u;
+    if (kCip) {
+        s_delta[threadIdx.x] = make_uint4(signed_step(delta_pair(g.e0 & 3u, 3u)),
+                                          signed_step(delta_pair((g.e0 >> 2) & 3u, 3u)),
+                                          signed_step(delta_pair((g.e0 >> 4) & 3u, 3u)),
+                                          signed_step(delta_pair((g.e0 >> 6) & 3u, 3u)));
+        s_delta2[threadIdx.x] = make_uint4(signed_step(delta_pair(g.e1 & 3u, 3u)),
+                                           signed_step(delta_pair((g.e1 >> 2) & 3u, 3u)),
+                                           signed_step(delta_pair((g.e1 >> 4) & 3u, 3u)),
+                                           signed_step(delta_pair((g.e1 >> 6) & 3u, 3u)));
+    }
+    g.ctr0 = 2u * (uint32_t)g.vec;
+}
+
+// The saturation test of one vector: sat, and its alleles as the byte pair (xa, xb) and
+// the byte xs (see qubit_pass).
+__device__ __forceinline__ bool saturated_vec(uint4 s, uint32_t off_top, int bp, uint32_t &xa, uint32_t &xb,
+                                              uint32_t &xs)
+{
+    const uint32_t b0 = (s.x >> bp) & 0x00010001u, b1 = (s.y >> bp) & 0x00010001u;
+    const uint32_t b2 = (s.z >> bp) & 0x00010001u, b3 = (s.w >> bp) & 0x00010001u;
+    xa = b0 | (b1 << 8);
+    xb = b2 | (b3 << 8);
+    xs = (allele_nibble_hi(xa) >> 24) | ((allele_nibble_hi(xb) >> 20) & 0xf0u);
+    return s.x == b0 * off_top && s.y == b1 * off_top && s.z == b2 * off_top && s.w == b3 * off_top;
+}
+
+// One pass of 16 genes: CIP(t-1) (rule R1), QIP(t), the packed item sums; xbits holds the
+// 16 alleles (the first vector's in bits 0-7). The fixed-allele test covers both vectors.
+template <bool kCip>
+__device__ __forceinline__ void qubit_pass2(const GenParams &p, const SegCtx2 &g, uint4 &s0, uint4 &s1,
+                                            int32_t c, int32_t t, const unsigned char *thr_bytes,
+                                            bool &fixed, int &countdown, uint32_t &xbits, uint32_t &accn)
+{
+    const uint32_t off_top = (uint32_t)(8 * p.K);
+    const uint32_t k8 = off_top * 0x00010001u;
+    accn = 0u;
+    fixed = false;
+    if (countdown == 0) {
+        const int bp = __ffs((int)off_top) - 1;
+        uint32_t xa0, xb0, xs0, xa1, xb1, xs1;
+        const bool sat = saturated_vec(s0, off_top, bp, xa0, xb0, xs0) & saturated_vec(s1, off_top, bp, xa1, xb1, xs1);
+        const bool ok = sat && (!kCip || (xs0 == g.e0 && xs1 == g.e1));
+        if (__all_sync(0xffffffffu, ok)) {
+            fixed = true;
+            xbits = xs0 | (xs1 << 8);
+            const uint4 ib = s_item_bytes[threadIdx.x], ib2 = s_item_bytes2[threadIdx.x];
+            const uint32_t sw = __dp4a(xa0, ib.x, __dp4a(xb0, ib.y, __dp4a(xa1, ib2.x, __dp4a(xb1, ib2.y, 0u))));
+            const uint32_t sv = __dp4a(xa0, ib.z, __dp4a(xb0, ib.w, __dp4a(xa1, ib2.z, __dp4a(xb1, ib2.w, 0u))));
+            accn = sw | (sv << 16);
+            return;
+        }
+        countdown = 15;
+    } else {
+        --countdown;
+    }
+    if (kCip) {
+        const uint4 d = s_delta[threadIdx.x], d2 = s_delta2[threadIdx.x];
+        s0.x = rotate_pair_signed(s0.x, d.x, k8);
+        s0.y = rotate_pair_signed(s0.y, d.y, k8);
+        s0.z = rotate_pair_signed(s0.z, d.z, k8);
+        s0.w = rotate_pair_signed(s0.w, d.w, k8);
+        s1.x = rotate_pair_signed(s1.x, d2.x, k8);
+        s1.y = rotate_pair_signed(s1.y, d2.y, k8);
+        s1.z = rotate_pair_signed(s1.z, d2.z, k8);
+        s1.w = rotate_pair_signed(s1.w, d2.w, k8);
+    }
+    const uint32_t sp[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    const Draw4 r0 = philox4x32_10_rk(g.ctr0, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+    const Draw4 r1 = philox4x32_10_rk(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+    const Draw4 r2 = philox4x32_10_rk(g.ctr0 + 2u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+    const Draw4 r3 = philox4x32_10_rk(g.ctr0 + 3u, (uint32_t)c, (uint32_t)t, 0u, p.rk0, p.rk1);
+    const uint32_t u[16] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d,
+                            r2.a, r2.b, r2.c, r2.d, r3.a, r3.b, r3.c, r3.d};
+    xbits = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
+        const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+        if ((u[i] < thr) || (off == off_top)) {
+            xbits |= 1u << i;
+            accn += g.wv[i];
+        }
+    }
+}
+
+// One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation, 16
+// genes per thread and pass, the state streamed through a per-thread cp.async ring of
+// kRing2Stages slots of 32 bytes (ring: this block's ring; slot s, half h of thread i at
+// ring[(2 s + h) * kThreads + i]).
+template <bool kCip>
+__device__ __forceinline__ void ring_segment2(const GenParams &p, int tile, int ra, int seg_rows, int32_t t,
+                                              uint8_t *x_cur, const uint8_t *elite_row,
+                                              const unsigned char *thr_bytes, uint4 *ring, uint32_t *s_acc32,
+                                              int &countdown)
+{
+    SegCtx2 g;
+    seg_setup2<kCip>(p, g, tile, elite_row);
+    const int ra_key = ra + p.row0;
+    const bool leader = (threadIdx.x & 31) == 0;
+    uint4 *slots = ring + threadIdx.x;
+    uint4 *sptr = p.state + (size_t)ra * p.svec + g.vec;
+    const size_t sstep = (size_t)p.svec;
+    uint8_t *xptr = x_cur + (size_t)ra * p.xstride + g.vec;
+    const size_t xstep = (size_t)p.xstride;
+    const uint4 *ld_ptr = sptr;
+    uint4 *st_ptr = sptr;
+    uint8_t *xst_ptr = xptr;
+    auto issue = [&](uint32_t stage, bool v) {
+        uint4 *dst = slots + (size_t)stage * 2 * kThreads;
+        const bool v0 = v && g.act0, v1 = v && g.act1;
+        cp_async16(dst, v0 ? (const void *)ld_ptr : (const void *)p.state, v0 ? 16u : 0u);
+        cp_async16(dst + kThreads, v1 ? (const void *)(ld_ptr + 1) : (const void *)p.state, v1 ? 16u : 0u);
+        cp_async_commit();
+        ld_ptr += sstep;
+    };
+#pragma unroll
+    for (int k = 0; k < kRing2Stages - 1; ++k) issue((uint32_t)k, k < seg_rows);
+    const int lim = seg_rows - (kRing2Stages - 1);
+    for (int pass = 0; pass < seg_rows; ++pass) {
+        issue((uint32_t)(pass + kRing2Stages - 1) & (kRing2Stages - 1), pass < lim);
+        cp_async_wait<kRing2Stages - 1>();
+        const uint32_t slot = (uint32_t)pass & (kRing2Stages - 1);
+        uint4 s0 = slots[(size_t)slot * 2 * kThreads];
+        uint4 s1 = slots[(size_t)slot * 2 * kThreads + kThreads];
+        uint32_t xbits, accn;
+        bool fixed;
+        qubit_pass2<kCip>(p, g, s0, s1, ra_key + pass, t, thr_bytes, fixed, countdown, xbits, accn);
+        if (!fixed) {                   // a fixed pass leaves the state as it is
+            if (g.act0) st_ptr[0] = s0;
+            if (g.act1) st_ptr[1] = s1;
+        }
+        if (g.act1) *reinterpret_cast<uint16_t *>(xst_ptr) = (uint16_t)xbits;
+        else if (g.act0) *xst_ptr = (uint8_t)xbits;
+        add_row_sums<true>(32, leader, true, pass, accn, 0, 0, s_acc32, nullptr);
+        st_ptr += sstep;
+        xst_ptr += xstep;
+    }
+    cp_async_wait<0>();
+    flush_segment<true>(p, t, ra, seg_rows, s_acc32, nullptr);
+}
+
+// ---------------------------------------------------------------------------------------
 // Resident form: a cooperative run whose blocks keep their share of the state in shared
 // memory for the whole run. A population whose state fits in the SMs' combined shared
 // memory (about 34 MB on a GB300, e.g. 1,024 x 10,000 genes = 20 MB) is read from device
@@ -1654,6 +1841,100 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
             p.conv[2] = kStopped;
         }
     }
+}
+
+// generation_kernel2: the deferred-close generation launch with 16 genes per thread and
+// pass (ring_segment2; rule R1, packed items <= 127, 16-bit state). p describes tiles of 512
+// vectors (ntile, units, the segment queue); dynamic shared memory: the ring
+// (kRing2Stages x 2 x kThreads x 16 B), then the row sums of a segment.
+template <bool kCip>
+__device__ __forceinline__ void generation2_body(const GenParams &p, int32_t t, int32_t e_prev,
+                                                 unsigned char *smem, const uint32_t *s_thr)
+{
+    __shared__ int32_t s_qi;
+    uint4 *ring = reinterpret_cast<uint4 *>(smem);
+    uint32_t *s_acc32 = reinterpret_cast<uint32_t *>(smem + (size_t)kRing2Stages * 2 * kThreads * 16);
+    const unsigned char *thr_bytes = reinterpret_cast<const unsigned char *>(s_thr);
+    const uint8_t *x_prev = p.xbits + (size_t)((t + 1) & 1) * p.xplane;
+    uint8_t *x_cur = p.xbits + (size_t)(t & 1) * p.xplane;
+    const uint8_t *elite_row = x_prev + (size_t)e_prev * p.xstride;
+    int countdown = 0;
+    clear_row_sums<true>(p.seg_rows_max, s_acc32, nullptr);
+    if (p.nsegs > 0) {
+        unsigned int *ctr = p.qctr + (t % 3);
+        for (;;) {
+            if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
+            __syncthreads();
+            const int32_t qi = s_qi;
+            if (qi >= p.nsegs) break;
+            const int4 sg = __ldg(p.segq + qi);
+            ring_segment2<kCip>(p, sg.x, sg.y, sg.z, t, x_cur, elite_row, thr_bytes, ring, s_acc32, countdown);
+        }
+    } else {
+        const BlockShare b = block_share(p);
+        for (int64_t u0 = b.u_begin; u0 < b.u_end;) {
+            const int tile = (int)(u0 / p.np);
+            const int ra = (int)(u0 - (int64_t)tile * p.np);
+            const int seg_rows = (int)min(min((int64_t)(p.np - ra), b.u_end - u0), (int64_t)p.seg_rows_max);
+            u0 += seg_rows;
+            ring_segment2<kCip>(p, tile, ra, seg_rows, t, x_cur, elite_row, thr_bytes, ring, s_acc32, countdown);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) generation_kernel2(const GenParams p)
+{
+    __shared__ uint32_t s_thr[kMaxThr];
+    __shared__ int s_stop, s_t, s_e;
+    __shared__ long long s_f;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    load_thresholds(p, s_thr);
+    grid_dependency_wait();
+    if (threadIdx.x == 0) {
+        const int32_t t = *p.gen + p.g;
+        int stop = deferred_skip(p, t) ? kStopped : kRunning;
+        int32_t e = 0;
+        int64_t f = 0;
+        if (stop == kRunning && p.apply_cip) {
+            elite_from_key(p, t - 1, e, f);
+            if (p.converge) {
+                const int32_t prev = t - 1 > 0 ? p.conv[(t - 2) & 1] : 0;
+                const int32_t run = (prev > 0 && f == p.hist_f[t - 2]) ? prev + 1 : 1;
+                if (run >= kConvergeWindow) stop = kStopPending;
+            }
+        }
+        s_t = t;
+        s_stop = stop;
+        s_e = e;
+        s_f = f;
+    }
+    __syncthreads();
+    const int32_t stop = s_stop, t = s_t, e_prev = s_e;
+    const int64_t f_prev = s_f;
+    if (stop == kStopped) return;
+    if (blockIdx.x == 0) {
+        if (p.apply_cip) {
+            record_generation(p, t - 1, e_prev, f_prev);
+            if (stop == kStopPending && threadIdx.x == 0) {
+                p.conv[3] = t - 1;
+                __threadfence();
+                st_release(p.conv + 2, kStopped);
+            }
+        }
+        if (threadIdx.x == 0) {
+            *key_slot(p, t + 1) = 0ull;
+            p.qctr[(t + 1) % 3] = 0u;
+        }
+    }
+    if (stop == kStopPending) {
+        // the CIP of the converged generation (grid-stride over the whole state)
+        if (p.state8) rotate_all<0, true>(p, t - 1, e_prev);
+        else rotate_all<0, false>(p, t - 1, e_prev);
+        return;
+    }
+    if (p.apply_cip) generation2_body<true>(p, t, e_prev, smem_raw, s_thr);
+    else generation2_body<false>(p, t, e_prev, smem_raw, s_thr);
+    allow_dependent_launch();
 }
 
 // ---------------------------------------------------------------------------------------

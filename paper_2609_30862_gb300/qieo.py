@@ -37,6 +37,7 @@ QIEO_FLAG_STATE_I8 = 0x100
 QIEO_FLAG_PER_GENERATION = 0x200
 QIEO_FLAG_TIME_GENERATIONS = 0x400
 QIEO_FLAG_STREAMED = 0x800
+QIEO_FLAG_SIXTEEN = 0x1000
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (

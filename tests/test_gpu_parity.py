@@ -558,3 +558,43 @@ def test_segment_queue_with_convergence_stop():
         assert np.array_equal(e, ref.hist_e) and np.array_equal(f, ref.hist_f)
         bits, bf, bg, bc = I.best()
         assert (bf, bg, bc) == tuple(int(v) for v in ref.best)
+
+
+@pytest.mark.parametrize("ng,np_", [(1, 3), (9, 5), (16, 7), (17, 33), (4095, 9), (4096, 12), (4097, 40),
+                                    (9001, 64), (2000, 700)])
+def test_sixteen_genes_per_pass(ng, np_):
+    """QIEO_FLAG_SIXTEEN (two 8-gene vectors per thread and pass) equals the oracle: ragged
+    gene counts (odd vector counts leave a thread one active vector, short rows leave
+    threads none), static shares and split runs."""
+    prob = W.knapsack(ng, ng + 3 * np_)
+    flags = Q.QIEO_FLAG_SIXTEEN | Q.QIEO_FLAG_PER_GENERATION
+    compare(prob, np_, [7, 6], seed=ng, inst=np_, flags=flags)
+
+
+def test_sixteen_genes_per_pass_queued():
+    """The queued form: 9,000 genes (three 512-vector tiles per row) x 7,000 rows give each
+    of the 304 blocks a share of at least 64 tile-rows, so the blocks take segments from the
+    queue."""
+    prob = W.knapsack(9000, 77)
+    shape = compare(prob, 7000, [12, 8], seed=77, inst=2, kind="omp",
+                    flags=Q.QIEO_FLAG_SIXTEEN | Q.QIEO_FLAG_PER_GENERATION)
+    assert shape.persistent == 0
+
+
+def test_sixteen_genes_per_pass_from_saturated_state():
+    prob = W.knapsack(5000, 64)
+    k0 = saturated_start(5000, 256, 65, n_odd=9, flips=40)
+    from oracle import oracle as O
+    st = O.State(256, 5000)
+    st.k[:] = k0
+    O.run(prob, 256, 30, seed=5, state=st)
+    with Q.Instance(prob, 256, seed=5, flags=Q.QIEO_FLAG_SIXTEEN | Q.QIEO_FLAG_PER_GENERATION) as I:
+        load_state(I, k0)
+        I.run(30)
+        k, t = I.state()
+        assert t == 30 and np.array_equal(k, st.k)
+        e, f = I.history(0, 30)
+        assert np.array_equal(e, st.hist_e) and np.array_equal(f, st.hist_f)
+        assert np.array_equal(I.alleles(), st.x)
+        bits, bf, bg, bc = I.best()
+        assert (bf, bg, bc) == tuple(int(v) for v in st.best)
