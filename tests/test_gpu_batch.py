@@ -206,3 +206,29 @@ def test_batch_from_saturated_states():
         bits, bf, bg, bc = inst.best()
         assert (bf, bg, bc) == tuple(int(v) for v in st.best)
         inst.close()
+
+
+def test_persistent_batch_wait_that_runs_out_is_reported():
+    """In the persistent form a segment of a member's next generation waits, bounded, for
+    that member's previous generation. With a 1 ns bound the waits of that member run out:
+    the run still ends (no trap, no hang), the member reports QIEO_ERR_TIMEOUT, the other
+    members are unaffected, and after qieo_reset the member runs correctly again."""
+    probs = [W.knapsack(3000, 41), W.knapsack(2500, 42)]
+    a = Q.Instance(probs[0], 120, seed=41)
+    b = Q.Instance(probs[1], 90, seed=42)
+    try:
+        a.set_wait_timeout(1)
+        with Q.Batch([a, b]) as bt:
+            bt.run(6)
+        with pytest.raises(Q.QieoError) as e:
+            a.synchronize()
+        assert e.value.status == Q.QIEO_ERR_TIMEOUT
+        check_against_oracle(b, probs[1], 90, 6, 42, 0)
+        a.set_wait_timeout(10 * 10**9)
+        a.reset()
+        with Q.Batch([a]) as bt:
+            bt.run(6)
+        check_against_oracle(a, probs[0], 120, 6, 41, 0)
+    finally:
+        a.close()
+        b.close()
