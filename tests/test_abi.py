@@ -82,6 +82,29 @@ def test_defaults_and_errors_without_gpu(lib):
     with pytest.raises(Q.QieoError) as e:
         Q.qieo_run(None, 1)
     assert e.value.status == Q.QIEO_ERR_INVALID
+    # the entry points added for measurement and for sharded populations check their
+    # arguments on the host before any device call
+    for reps in (0, 1001):
+        with pytest.raises(Q.QieoError) as e:
+            Q.qieo_measure_integer_ceiling(reps)
+        assert e.value.status == Q.QIEO_ERR_INVALID and "reps" in str(e.value)
+    for call in (lambda: Q.qieo_get_generation_times(None, 4), lambda: Q.qieo_rows_observe(None, 0),
+                 lambda: Q.qieo_rows_rotate(None, [0, 1]), lambda: Q.qieo_get_allele_row(None, 0, 4)):
+        with pytest.raises(Q.QieoError) as e:
+            call()
+        assert e.value.status == Q.QIEO_ERR_INVALID
+    for bad in (dict(row0=-1), dict(row0=0, elite_on_host=1), dict(row0=0, flags=Q.QIEO_FLAG_CONVERGE),
+                dict(row0=0, flags=Q.QIEO_FLAG_UNFUSED)):
+        kw = dict(bad)
+        row0 = kw.pop("row0")
+        with pytest.raises(Q.QieoError) as e:
+            Q.qieo_create_row_block([1, 2], [3, 4], 2, _params(p, **kw), row0)
+        assert e.value.status == Q.QIEO_ERR_INVALID
+    for bad in (dict(flags=Q.QIEO_FLAG_TIME_GENERATIONS, elite_on_host=1),
+                dict(flags=Q.QIEO_FLAG_TIME_GENERATIONS | Q.QIEO_FLAG_UNFUSED)):
+        with pytest.raises(Q.QieoError) as e:
+            Q.qieo_create_instance([1, 2], [3, 4], 2, _params(p, **bad))
+        assert e.value.status == Q.QIEO_ERR_INVALID and "TIME_GENERATIONS" in str(e.value)
 
 
 def _params(p, **kw):
