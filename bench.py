@@ -62,6 +62,9 @@ def parse():
                     help="c1-c3: store the angle indices as bytes (QIEO_FLAG_STATE_I8)")
     ap.add_argument("--streamed", action="store_true",
                     help="c1-c3: never keep the state resident in shared memory (QIEO_FLAG_STREAMED)")
+    ap.add_argument("--no-fixed-words", action="store_true",
+                    help="c1-c3: keep no fixed-vector words, so every generation runs the dense "
+                         "pass (QIEO_FLAG_NO_FIXED_WORDS)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-phases", action="store_true",
@@ -358,7 +361,8 @@ def run_gpu(a):
     np_, ng, G = c["np"], c["ng"], c["gens"]
     genes_per_step = np_ * ng * G
     stream = torch.cuda.Stream()
-    flags = (Q.QIEO_FLAG_STATE_I8 if a.state_i8 else 0) | (Q.QIEO_FLAG_STREAMED if a.streamed else 0)
+    flags = ((Q.QIEO_FLAG_STATE_I8 if a.state_i8 else 0) | (Q.QIEO_FLAG_STREAMED if a.streamed else 0) |
+             (Q.QIEO_FLAG_NO_FIXED_WORDS if a.no_fixed_words else 0))
     inst = Q.Instance(prob, np_, seed=c["seed"], inst=c["inst"] + rank,
                       stream=stream.cuda_stream, flags=flags)
     shape = inst.shape()
@@ -432,6 +436,12 @@ def run_gpu(a):
                                "integer work, state in registers, %d blocks, best of %d)" % (
                                    ceiling.grid_ctas, ceiling.reps)}
     roof["frac_hbm_4B_formula"] = hbm_achieved / hbm_peak
+    roof["fixed_words"] = bool(shape.fixed_words)
+    if shape.fixed_words:
+        roof["note"] = ("fixed-vector words: generations in which most vectors are fixed skip their "
+                        "draws and state traffic exactly (identical results), so the 4 B and full-draw "
+                        "per gene-update formula behind frac can exceed 1; phases.work_adjusted is "
+                        "the roofline of the work each generation needed")
     roof["hbm_peak_gbs"] = hbm_peak
     if int_peak:
         roof["int_ceiling_gene_updates_per_s"] = int_peak
@@ -532,6 +542,7 @@ def generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch, hbm_peak, 
         inst.reset()
         inst.run(G)
         ms = inst.generation_times(G)
+        drawn = inst.drawn_vectors(0, G) if inst.shape().fixed_words else None
         inst.close()
     genes = np_ * ng
 
@@ -549,11 +560,37 @@ def generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch, hbm_peak, 
         return out
 
     step = 25
-    return {"spread": window(*SPREAD_WINDOW), "saturated": window(*SATURATED_WINDOW),
-            "per_25": [round(1e3 * float(np.mean(ms[i:i + step])), 2) for i in range(0, len(ms), step)],
-            "sum_of_launches_us": 1e3 * float(np.sum(ms)),
-            "what": "device clock at each generation's start (resident form) or CUDA events before "
-                    "every generation launch of one run (launches serialised)"}
+    out = {"spread": window(*SPREAD_WINDOW), "saturated": window(*SATURATED_WINDOW),
+           "per_25": [round(1e3 * float(np.mean(ms[i:i + step])), 2) for i in range(0, len(ms), step)],
+           "sum_of_launches_us": 1e3 * float(np.sum(ms)),
+           "what": "device clock at each generation's start (resident form) or CUDA events before "
+                   "every generation launch of one run (launches serialised)"}
+    if drawn is not None and int_peak:
+        out["work_adjusted"] = work_adjusted(ms, drawn, np_ * ((ng + 7) // 8), hbm_peak, int_peak)
+    return out
+
+
+def work_adjusted(ms, drawn, nvec, hbm_peak, int_peak):
+    """The roofline of the work each generation actually needed. A vector that drew (the
+    qieo_get_drawn_vectors count) needs its 8 draws at the measured integer ceiling and its
+    32 B of state (read and written); one that did not needs its fixed-vector word read and
+    its alleles written (3 B). Per generation the bound is the slower of the two; the
+    fraction is the sum of the bounds over the sum of the measured times."""
+    import numpy as np
+    d = np.asarray(drawn, dtype=np.float64)
+    t_int = 8.0 * d / int_peak
+    t_hbm = (32.0 * d + 3.0 * (nvec - d)) / (hbm_peak * 1e9)
+    bound = np.maximum(t_int, t_hbm)
+    meas = np.asarray(ms, dtype=np.float64) * 1e-3
+    return {"frac": float(bound.sum() / meas.sum()),
+            "bound_us": 1e6 * float(bound.sum()), "measured_us": 1e6 * float(meas.sum()),
+            "drawn_fraction": float(d.sum() / (nvec * len(d))),
+            "drawn_per_25": [round(float(d[i:i + 25].mean()) / nvec, 4) for i in range(0, len(d), 25)],
+            "frac_per_25": [round(float(bound[i:i + 25].sum() / meas[i:i + 25].sum()), 3)
+                            for i in range(0, len(d), 25)],
+            "what": "per generation: max(8 draws per vector that drew at the measured integer "
+                    "ceiling, (32 B per vector that drew + 3 B per one that did not) at the "
+                    "measured HBM bandwidth), summed, over the measured generation times"}
 
 
 def batch_oracle_sample(specs, G: int, target_s: float = 10.0):

@@ -107,6 +107,13 @@ typedef struct {
                                           qubit still draws, slower once many saturate
                                           (4,096 x 100,000 genes: 406 vs 422 us per spread
                                           generation, 241 vs 184 us per collapsed one) */
+#define QIEO_FLAG_NO_FIXED_WORDS 0x2000 /* keep no fixed-vector words: every generation of
+                                          the one-launch-per-generation form runs the dense
+                                          pass over all qubits (see qieo_launch_shape.
+                                          fixed_words) */
+#define QIEO_FLAG_SPARSE_ALWAYS 0x4000 /* with fixed-vector words, take the sparse form in
+                                          every generation, however few vectors are fixed
+                                          (identical results; for tests and measurement) */
 #define QIEO_FLAG_TIME_GENERATIONS 0x400 /* time every generation of a run for
                                             qieo_get_generation_times. In the resident form
                                             (qieo_launch_shape.resident) one thread reads the
@@ -193,6 +200,15 @@ qieo_status qieo_get_allele_row(qieo_instance *inst, int32_t c, uint8_t *x_out);
 qieo_status qieo_get_elite_history(qieo_instance *inst, int32_t first, int32_t n,
                                    int32_t *idx_out, int64_t *fit_out);
 
+/* Work of generations first .. first+n-1 (all < t) of an instance that keeps fixed-vector
+ * words (qieo_launch_shape.fixed_words): out[i] = the 8-gene vectors of generation first+i
+ * that drew (ran QIP with a Philox draw per qubit, after their CIP); the rest were fixed, so
+ * their alleles were known without a draw (the fixed-allele pass of the dense form, the
+ * stable vectors of the sparse form). np * ceil(ng / 8) means every vector drew; generations
+ * run in a batch, or restored by a checkpoint load, report that value (they are not counted).
+ * QIEO_ERR_INVALID for an instance without the words, out NULL or a range outside [0, t). */
+qieo_status qieo_get_drawn_vectors(qieo_instance *inst, int32_t first, int32_t n, int64_t *out);
+
 /* The observation thresholds T[0 .. 2K] the device uses (2K+1 uint64). */
 qieo_status qieo_get_threshold_table(qieo_instance *inst, uint64_t *t_out);
 
@@ -219,6 +235,16 @@ typedef struct {
                                 a GB300, unless QIEO_FLAG_STREAMED, QIEO_FLAG_COOPERATIVE,
                                 QIEO_FLAG_PER_GENERATION, QIEO_FLAG_TIME_GENERATIONS,
                                 QIEO_FLAG_CONVERGE, elite_on_host or byte state) */
+    int32_t fixed_words;     /* out: 1 when the instance keeps a fixed-vector word per 8 genes
+                                (16 bits: all eight qubits at theta = 0 or pi/2, and their
+                                sides), so that a generation in which most vectors are fixed
+                                takes the sparse form: only the vectors that are not fixed, or
+                                that the previous elite turns away from their bound, run CIP,
+                                QIP and Evaluation in full; the rest contribute their sides.
+                                Kept by the one-launch-per-generation runs with the packed
+                                elite key, rule R1, items in [0, 255], 16-bit state and the
+                                default tile, unless QIEO_FLAG_NO_FIXED_WORDS,
+                                QIEO_FLAG_SIXTEEN or QIEO_FLAG_CONVERGE */
 } qieo_launch_shape;
 
 qieo_status qieo_get_launch_shape(qieo_instance *inst, qieo_launch_shape *shape);

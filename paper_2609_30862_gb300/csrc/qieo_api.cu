@@ -121,6 +121,8 @@ struct qieo_instance {
     bool seg_delta = false;          // generation kernel forms the R1 deltas once per segment
     int32_t *hist_e = nullptr;
     int64_t *hist_f = nullptr;
+    unsigned long long *hist_d = nullptr;   // vectors that did not draw, per generation (in
+                                            // hist_f's block)
     int32_t hist_cap = 0;
 
     // host mirror of the generation counter (number of generations run since reset)
@@ -180,6 +182,12 @@ struct qieo_instance {
     bool row_block = false;
     uint8_t *ext_elite = nullptr;
     int32_t rows_t = -1;
+
+    // fixed-vector words (qieo_launch_shape.fixed_words): one allocation holding the three
+    // per-generation counters (first 256 bytes) and the words; fword_bytes = 0 when the
+    // instance keeps none
+    void *fword_mem = nullptr;
+    size_t fword_bytes = 0;
 };
 
 namespace {
@@ -220,6 +228,7 @@ struct PickRun {
 PickGen<true, 0, true>::type gen_fn(const qieo_instance *q, bool ring, bool seg_delta)
 {
     if (seg_delta && ring && q->rule == 0) {
+        if (q->gp.fword) return &qieo::generation_kernel<true, 0, true, false, true, true>;
         if (q->state8) return &qieo::generation_kernel<true, 0, true, true, true>;
         return q->narrow ? &qieo::generation_kernel<true, 0, true, false, true>
                          : &qieo::generation_kernel<false, 0, true, false, true>;
@@ -351,20 +360,25 @@ qieo_status resident_blocks(int device, const void *fn, size_t smem, int *bps)
 // gains (measured: 1,024 x 10,000 genes, 8 rows per block, 10.1 -> 12.2 us per generation
 // with a queue; 4,096 x 100,000, 330 rows per block, 396 -> 367 us). Instances placed in
 // a server arena run in batches only and keep none.
+//
+// Instances that keep fixed-vector words always take the queue (their generation kernel
+// has no other form) and cut it at multiples of 8 rows (f_align; seg_max is then a
+// multiple of 8), so that every segment starts on a group of F words.
 constexpr int64_t kQueueMinRows = 4;
 constexpr int64_t kQueueMinShare = 64;
 
 qieo_status build_queue_into(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring, int4 *&buf,
-                             int32_t &cap, const int4 *&segq_out, int32_t &nsegs_out)
+                             int32_t &cap, const int4 *&segq_out, int32_t &nsegs_out, bool f_align = false)
 {
     segq_out = nullptr;
     nsegs_out = 0;
-    if (!use_ring || !q->owns_block || units < kQueueMinShare * (int64_t)grid) return QIEO_OK;
+    if (!use_ring || !q->owns_block || (!f_align && units < kQueueMinShare * (int64_t)grid)) return QIEO_OK;
     std::vector<int4> segs;
     for (int64_t u = 0; u < units;) {
         const int64_t tile = u / q->np, ra = u - tile * q->np;
         const int64_t rem = units - u;
         int64_t rows = std::max<int64_t>(kQueueMinRows, (rem + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid));
+        if (f_align) rows = (rows + 7) / 8 * 8;
         rows = std::min<int64_t>(rows, std::min<int64_t>((int64_t)seg_max, (int64_t)q->np - ra));
         segs.push_back(make_int4((int)tile, (int)ra, (int)rows, 0));
         u += rows;
@@ -383,9 +397,11 @@ qieo_status build_queue_into(qieo_instance *q, int64_t units, int grid, int seg_
     return QIEO_OK;
 }
 
-qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring)
+qieo_status build_segment_queue(qieo_instance *q, int64_t units, int grid, int seg_max, bool use_ring,
+                                bool f_align = false)
 {
-    return build_queue_into(q, units, grid, seg_max, use_ring, q->segq, q->segq_cap, q->gp.segq, q->gp.nsegs);
+    return build_queue_into(q, units, grid, seg_max, use_ring, q->segq, q->segq_cap, q->gp.segq, q->gp.nsegs,
+                            f_align);
 }
 
 // Persistent blocks per SM of the single-instance kernels. The schedulers favour older
@@ -400,6 +416,73 @@ constexpr int kBlocksPerSm = 3;
 constexpr size_t kResidentMaxSmem = 200 * 1024;
 
 qieo_status configure_sixteen(qieo_instance *q);
+bool use_resident(const qieo_instance *q);
+bool use_cooperative(const qieo_instance *q);
+
+// Fixed-vector words: kept from the generation after the first whose estimate of fixed
+// vectors reaches kFwordOnFraction of the population's vectors; a generation takes the
+// sparse form once at least kSparseMinFraction were fixed after the one before.
+constexpr double kFwordOnFraction = 0.40;
+constexpr double kSparseMinFraction = 0.50;
+constexpr int kFwordMaxSegRows = 256;      // a row of a segment fits 8 bits of a list entry
+
+// Whether the instance keeps fixed-vector words: the runs that take the one-launch-per-
+// generation deferred form with the generation kernel that maintains them.
+bool wants_fword(const qieo_instance *q, bool use_ring)
+{
+    return !(q->flags & (QIEO_FLAG_NO_FIXED_WORDS | QIEO_FLAG_SIXTEEN | QIEO_FLAG_CONVERGE | QIEO_FLAG_UNFUSED |
+                         QIEO_FLAG_COOPERATIVE)) &&
+           use_ring && q->narrow && !q->state8 && q->rule == 0 && q->key_ok && !q->host_de && q->lanes == 32 &&
+           q->warps == 8 && q->owns_block && !q->row_block && !use_resident(q) && !use_cooperative(q);
+}
+
+// Allocates (all words 0: no vector known to be fixed) or releases the words and fills the
+// fields of gp. Words kept from an earlier call of the same geometry stay valid.
+qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
+{
+    qieo::GenParams &g = q->gp;
+    // [counters: 256 B][the words][row totals: np x 8 B][row changes: np x 16 B]
+    const int32_t np8 = (q->np + 7) / 8;
+    const size_t words = align_up((size_t)ntile * (size_t)np8 * qieo::kThreads * 8 * sizeof(uint16_t), 256);
+    const size_t prev = align_up((size_t)q->np * 8, 256);
+    const size_t bytes = want ? 256 + words + prev + (size_t)q->np * 16 : 0;
+    if (bytes != q->fword_bytes) {
+        if (q->fword_mem) cudaFreeAsync(q->fword_mem, q->stream);
+        q->fword_mem = nullptr;
+        q->fword_bytes = 0;
+        if (bytes) {
+            keep_pool_memory(q->device);
+            cudaError_t ce = cudaMallocAsync(&q->fword_mem, bytes, q->stream);
+            if (ce != cudaSuccess) {
+                g.fword = nullptr;
+                g.fcnt = nullptr;
+                return fail(ce == cudaErrorMemoryAllocation ? QIEO_ERR_OOM : QIEO_ERR_CUDA,
+                            "fixed-vector words (%zu bytes): %s", bytes, cudaGetErrorString(ce));
+            }
+            q->fword_bytes = bytes;
+            CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, bytes, q->stream));
+        }
+    }
+    char *base = static_cast<char *>(q->fword_mem);
+    g.fcnt = bytes ? reinterpret_cast<unsigned long long *>(base) : nullptr;
+    g.fword = bytes ? reinterpret_cast<uint16_t *>(base + 256) : nullptr;
+    g.fprev = bytes ? reinterpret_cast<unsigned long long *>(base + 256 + words) : nullptr;
+    g.fdacc = bytes ? reinterpret_cast<unsigned long long *>(base + 256 + words + prev) : nullptr;
+    g.np8 = np8;
+    const double vecs = (double)q->np * (double)q->svec;
+    const double need = std::ceil(kSparseMinFraction * vecs), on = std::ceil(kFwordOnFraction * vecs);
+    const bool always = (q->flags & QIEO_FLAG_SPARSE_ALWAYS) != 0;
+    g.sparse_min = always ? 0ull : (unsigned long long)need;
+    g.f_on_min = always ? 0ull : (unsigned long long)on;
+    return QIEO_OK;
+}
+
+// Every fixed-vector word to 0 (after the state changed outside the kernels that keep them).
+qieo_status clear_fword(qieo_instance *q, cudaStream_t s)
+{
+    if (q->fword_bytes) CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, q->fword_bytes, s));
+    return QIEO_OK;
+}
 
 // Picks the sum mode and the persistent grid for the current tile (lanes x warps) and
 // fills the launch fields of gp.
@@ -427,12 +510,16 @@ qieo_status configure(qieo_instance *q)
     // Blocks resident at once, for the larger of the shared-memory sizes used and either
     // generation-kernel variant, capped at kBlocksPerSm.
     const size_t smem0 = ring + (size_t)qieo::kMaxSegRows * row_bytes;
-    int bps_gen = 0, bps_sd = 0, bps_run = 0;
+    int bps_gen = 0, bps_sd = 0, bps_run = 0, bps_f = kBlocksPerSm;
     qieo_status ost = resident_blocks(q->device, gen_kernel_of(q, use_ring, false), smem0, &bps_gen);
     if (ost == QIEO_OK) ost = resident_blocks(q->device, gen_kernel_of(q, use_ring, true), smem0, &bps_sd);
     if (ost == QIEO_OK) ost = resident_blocks(q->device, run_kernel_of(q, use_ring), smem0, &bps_run);
+    if (ost == QIEO_OK && use_ring && q->narrow && q->rule == 0 && !q->state8)
+        ost = resident_blocks(q->device,
+                              reinterpret_cast<const void *>(&qieo::generation_kernel<true, 0, true, false, true, true>),
+                              ring + (size_t)kFwordMaxSegRows * row_bytes, &bps_f);
     if (ost != QIEO_OK) return ost;
-    const int bps = std::min(kBlocksPerSm, std::min(bps_gen, std::min(bps_sd, bps_run)));
+    const int bps = std::min(std::min(kBlocksPerSm, bps_f), std::min(bps_gen, std::min(bps_sd, bps_run)));
     const int64_t resident = (int64_t)q->sm_count * std::max(1, bps);
     int grid = q->grid_override;
     if (grid <= 0) {
@@ -440,7 +527,7 @@ qieo_status configure(qieo_instance *q)
         grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, by_work));
     }
     const int64_t share = (units + grid - 1) / grid;
-    const int seg_max = (int)std::max<int64_t>(1, std::min<int64_t>(qieo::kMaxSegRows, share));
+    int seg_max = (int)std::max<int64_t>(1, std::min<int64_t>(qieo::kMaxSegRows, share));
     q->grid = grid;
     q->smem = ring + (size_t)seg_max * row_bytes;
     q->coop = bps_run > 0 && grid <= (int64_t)q->sm_count * bps_run;
@@ -460,6 +547,13 @@ qieo_status configure(qieo_instance *q)
         q->resident_fits = bps_res > 0 && grid <= (int64_t)q->sm_count * bps_res;
     }
 
+    // fixed-vector words: segments of at most 256 rows, cut at multiples of 8
+    const bool want_f = wants_fword(q, use_ring);
+    if (want_f) {
+        seg_max = std::min(kFwordMaxSegRows, std::max(8, seg_max & ~7));
+        q->smem = ring + (size_t)seg_max * row_bytes;
+    }
+
     qieo::GenParams &g = q->gp;
     g.items_narrow = q->items_narrow;
     g.ntile = ntile;
@@ -468,7 +562,9 @@ qieo_status configure(qieo_instance *q)
     g.warps = q->warps;
     g.seg_rows_max = seg_max;
     g.key_mode = q->key_ok ? 1 : 0;
-    qieo_status qst = build_segment_queue(q, units, grid, seg_max, use_ring);
+    qieo_status qst = build_segment_queue(q, units, grid, seg_max, use_ring, want_f);
+    if (qst != QIEO_OK) return qst;
+    qst = configure_fword(q, want_f && g.nsegs > 0, ntile);
     if (qst != QIEO_OK) return qst;
     q->seg_delta = g.nsegs > 0 && q->rule == 0;   // long queued segments: deltas per segment
     drop_graphs(q);
@@ -633,24 +729,32 @@ qieo_status ensure_history(qieo_instance *q, int32_t need)
     int64_t *f = nullptr;
     keep_pool_memory(q->device);
     CUDA_TRY(cudaMallocAsync(&e, (size_t)cap * sizeof(int32_t), q->stream));
-    cudaError_t err = cudaMallocAsync(&f, (size_t)cap * sizeof(int64_t), q->stream);
+    // the fitness history, then the counts of vectors that did not draw
+    // (qieo_get_drawn_vectors)
+    cudaError_t err = cudaMallocAsync(&f, (size_t)cap * 2 * sizeof(int64_t), q->stream);
     if (err != cudaSuccess) {
         cudaFreeAsync(e, q->stream);
         return fail(QIEO_ERR_OOM, "history buffer: %s", cudaGetErrorString(err));
     }
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(f + cap);
+    CUDA_TRY(cudaMemsetAsync(d, 0, (size_t)cap * sizeof(unsigned long long), q->stream));
     if (q->hist_cap > 0) {
         CUDA_TRY(cudaMemcpyAsync(e, q->hist_e, (size_t)q->hist_cap * sizeof(int32_t),
                                  cudaMemcpyDeviceToDevice, q->stream));
         CUDA_TRY(cudaMemcpyAsync(f, q->hist_f, (size_t)q->hist_cap * sizeof(int64_t),
+                                 cudaMemcpyDeviceToDevice, q->stream));
+        CUDA_TRY(cudaMemcpyAsync(d, q->hist_d, (size_t)q->hist_cap * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToDevice, q->stream));
         cudaFreeAsync(q->hist_e, q->stream);
         cudaFreeAsync(q->hist_f, q->stream);
     }
     q->hist_e = e;
     q->hist_f = f;
+    q->hist_d = d;
     q->hist_cap = cap;
     q->gp.hist_e = e;
     q->gp.hist_f = f;
+    q->gp.hist_d = d;
     drop_graphs(q);
     return QIEO_OK;
 }
@@ -1276,6 +1380,7 @@ qieo_status qieo_destroy_instance(qieo_instance *q)
     if (q->segq2) cudaFreeAsync(q->segq2, q->stream);
     if (q->ext_elite) cudaFreeAsync(q->ext_elite, q->stream);
     if (q->gen_ns) cudaFreeAsync(q->gen_ns, q->stream);
+    if (q->fword_mem) cudaFreeAsync(q->fword_mem, q->stream);
     if (q->h_fit) cudaFreeHost(q->h_fit);
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
@@ -1301,6 +1406,8 @@ qieo_status qieo_reset(qieo_instance *q)
     qieo::init_kernel<<<blocks, qieo::kThreads, 0, q->stream>>>(q->gp, words, xbytes,
                                                                (size_t)q->np * 2);
     CUDA_TRY(cudaGetLastError());
+    if (q->hist_d)
+        CUDA_TRY(cudaMemsetAsync(q->hist_d, 0, (size_t)q->hist_cap * sizeof(unsigned long long), q->stream));
     q->t = 0;
     q->rows_t = -1;
     if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
@@ -1489,6 +1596,25 @@ qieo_status qieo_get_elite_history(qieo_instance *q, int32_t first, int32_t n, i
     return QIEO_OK;
 }
 
+qieo_status qieo_get_drawn_vectors(qieo_instance *q, int32_t first, int32_t n, int64_t *out)
+{
+    qieo_status st = check_inst(q);
+    if (st != QIEO_OK) return st;
+    if (!out && n > 0) return fail(QIEO_ERR_INVALID, "out is NULL");
+    if (!q->gp.fword || !q->hist_d)
+        return fail(QIEO_ERR_INVALID, "the instance keeps no fixed-vector words (qieo_launch_shape.fixed_words)");
+    if (first < 0 || n < 0 || (int64_t)first + n > q->t)
+        return fail(QIEO_ERR_INVALID, "generation range [%d, %d) outside [0, %d)", first, first + n, q->t);
+    if (n == 0) return QIEO_OK;
+    st = set_device(q);
+    if (st != QIEO_OK) return st;
+    st = fetch(q, out, q->hist_d + first, (size_t)n * sizeof(int64_t));   // the vectors skipped
+    if (st != QIEO_OK) return st;
+    const int64_t all = (int64_t)q->np * q->svec;
+    for (int32_t i = 0; i < n; ++i) out[i] = all - out[i];
+    return QIEO_OK;
+}
+
 qieo_status qieo_get_threshold_table(qieo_instance *q, uint64_t *t_out)
 {
     qieo_status st = check_inst(q);
@@ -1517,6 +1643,7 @@ qieo_status qieo_get_launch_shape(qieo_instance *q, qieo_launch_shape *s)
     s->rows_per_cta = q->gp.seg_rows_max;
     s->persistent = (use_resident(q) || use_cooperative(q)) ? 1 : 0;
     s->resident = use_resident(q) ? 1 : 0;
+    s->fixed_words = q->gp.fword ? 1 : 0;
     return QIEO_OK;
 }
 
@@ -1604,6 +1731,11 @@ qieo_status qieo_create_row_block(const qieo_problem *problem, const qieo_params
     }
     q->row_block = true;
     q->gp.row0 = row0;
+    st = configure(q);   // a row block keeps no fixed-vector words
+    if (st != QIEO_OK) {
+        qieo_destroy_instance(q);
+        return st;
+    }
     cudaError_t ce = cudaMallocAsync(&q->ext_elite, (size_t)q->xstride, q->stream);
     if (ce != cudaSuccess) {
         qieo_destroy_instance(q);
@@ -1809,6 +1941,7 @@ qieo_status qieo_checkpoint_load(qieo_instance *q, const void *buffer, size_t by
     if (st == QIEO_OK) st = upload(q, q->hist_f, p, (size_t)h.t * sizeof(int64_t));
     p += (size_t)h.t * sizeof(int64_t);
     if (st == QIEO_OK) st = upload(q, q->gp.state, p, h.state_bytes);
+    if (st == QIEO_OK) st = clear_fword(q, q->stream);   // the words of the reset state
     if (st == QIEO_OK) st = upload(q, q->gp.conv, h.conv, sizeof h.conv);
     if (st == QIEO_OK) st = upload(q, q->gp.best, h.best, sizeof h.best);
     if (st == QIEO_OK) st = upload(q, q->gp.elite_idx, &h.elite_idx, sizeof h.elite_idx);
@@ -2221,6 +2354,10 @@ qieo_status qieo_batch_run(qieo_batch *bt, int32_t G)
             exec = it->second;
         }
         CUDA_TRY(cudaGraphLaunch(exec, bt->stream));
+    }
+    for (qieo_instance *q : bt->members) {   // the batched kernels do not keep F
+        qieo_status st = clear_fword(q, bt->stream);
+        if (st != QIEO_OK) return st;
     }
     if (!bt->other_streams.empty()) {
         CUDA_TRY(cudaEventRecord(bt->ev_out, bt->stream));

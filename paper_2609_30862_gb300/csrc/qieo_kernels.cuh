@@ -152,6 +152,24 @@ struct GenParams {
                                   // block of a population sharded by rows; 0 otherwise)
     unsigned long long *gen_ns;   // resident form: device clock (ns) at the start of each
                                   // generation of the run and at its end, or NULL
+    uint16_t *fword;              // fixed-vector words F of the stored state (see f_index),
+                                  // or NULL when the instance keeps none
+    unsigned long long *fcnt;     // [7] vectors whose F is nonzero after generation t, in
+                                  // slot t % 3 (an estimate while the words are not kept);
+                                  // [3]: 1 once the words are kept; [4 + t % 3]: vectors
+                                  // that did not draw in generation t
+    unsigned long long *hist_d;   // [capacity] vectors that did not draw, per generation
+                                  // (copied from fcnt once the generation is complete), or
+                                  // NULL
+    unsigned long long *fprev;    // [np] packed row totals (SV << 26 | SW) of the last
+                                  // generation, kept by the kernel that keeps F
+    unsigned long long *fdacc;    // [2 np] signed changes of a sparse generation's row
+                                  // totals (w, v), reset by the block that finishes the row
+    int32_t np8;                  // rows of a tile in F, in groups of 8: ceil(np / 8)
+    unsigned long long sparse_min;   // a generation takes the sparse form when at least
+                                     // this many vectors were fixed after the one before
+    unsigned long long f_on_min;     // the words are kept from the first generation after
+                                     // one whose estimate of fixed vectors reached this
     uint32_t rk0[10], rk1[10];    // Philox round keys of (seed, instance)
 };
 
@@ -484,6 +502,28 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
     return sw | (sv << 16);
 }
 
+// Fixed-vector words. F of a vector of the stored state is 0x100 | (its 8 alleles, bit i =
+// gene i) when all eight qubits sit at theta = 0 or pi/2 (n = 0 or 2K: each allele is then
+// the side of its bound whatever the draw), and 0 otherwise; 0 is also always a safe value
+// ("not known to be fixed"), so F may be cleared at any time. Instances that keep F store
+// it per tile of 256 vectors in groups of 8 rows, the words of one vector's group adjacent:
+// (tile, row, v_in) at ((tile * np8 + row / 8) * 256 + v_in) * 8 + row % 8, so a thread
+// reads or writes the words of 8 rows of its vector as one 16-byte access.
+__device__ __forceinline__ size_t f_index(const GenParams &p, int tile, int row, int v_in)
+{
+    return (((size_t)tile * (size_t)p.np8 + (size_t)(row >> 3)) * kThreads + (size_t)v_in) * 8 +
+           (size_t)(row & 7);
+}
+
+// Alleles of four genes (bit i = gene i of the nibble) -> bytes (x0, x2, x1, x3), the order
+// narrow_sums takes: the multiplier's terms 1, 2^15, 2^6, 2^21 move bit 0 to bit 0, bit 1 to
+// 16, bit 2 to 8 and bit 3 to 24, and the sixteen partial products all land on different
+// bits, so nothing carries.
+__device__ __forceinline__ uint32_t allele_bytes(uint32_t nib)
+{
+    return (nib * 0x00208041u) & 0x01010101u;
+}
+
 // One vector of one row: CIP(t-1), QIP(t), the row's partial sums. Returns the new state
 // and the packed or wide sums through accn / acw, acv (before the segment reduction).
 //
@@ -495,12 +535,17 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
 // is skipped for 15 passes after it fails, which keeps its cost low while the population
 // is still spread out. (An exponential backoff, 1, 3, 7 then 15 passes, measured slower:
 // c3's saturated generations 186 vs 177 us, c2's spread ones 15.8 vs 14.9 us.)
+//
+// zor (when not NULL) receives the OR of the eight threshold words the pass compared
+// against: 0 exactly when every qubit of the vector sits at theta = 0 or pi/2 after the
+// rotation (T[0] = 0 and T[2K] = 2^32 have zero low words, every T[n] in between has not).
 template <bool kNarrow, int kRule, bool kCip, class Keys, bool kSegDelta = false>
 __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys, const SegCtx &g, uint4 s,
                                             uint32_t xo, int32_t c, int32_t t,
                                             const unsigned char *thr_bytes, bool &fixed,
                                             int &countdown, uint32_t &xbits, uint32_t &accn,
-                                            int64_t &acw, int64_t &acv)
+                                            int64_t &acw, int64_t &acv, uint32_t *zor = nullptr,
+                                            uint32_t *nsat = nullptr)
 {
     const uint32_t off_top = (uint32_t)(8 * p.K);
     const uint32_t k8 = off_top * 0x00010001u;
@@ -521,9 +566,11 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
         const uint32_t xa = b0 | (b1 << 8), xb = b2 | (b3 << 8);
         const uint32_t xs = (allele_nibble_hi(xa) >> 24) | ((allele_nibble_hi(xb) >> 20) & 0xf0u);
         const bool ok = sat && (!kCip || ((g.e8 ^ xs) & m8) == 0u);
+        if (nsat && sat && g.active) ++*nsat;
         if (__all_sync(0xffffffffu, ok)) {
             fixed = true;
             xbits = xs;
+            if (zor) *zor = 0u;
             if (kNarrow) {
                 accn = narrow_sums(xa, xb);
             } else {
@@ -558,10 +605,12 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
     const Draw4 r1 = keys(g.ctr0 + 1u, (uint32_t)c, (uint32_t)t);
     const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
     xbits = 0u;
+    uint32_t z = 0u;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const uint32_t off = (i & 1) ? (sp[i >> 1] >> 16) : (sp[i >> 1] & 0xffffu);
         const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+        z |= thr;
         if ((u[i] < thr) || (off == off_top)) {
             xbits |= 1u << i;
             if (kNarrow) {
@@ -572,6 +621,7 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
             }
         }
     }
+    if (zor) *zor = z;
     return s;
 }
 
@@ -594,15 +644,66 @@ __device__ __forceinline__ void add_row_sums(int lanes, bool leader, bool ok, in
     }
 }
 
+// The kernel that keeps F also keeps every row's totals (fprev): a dense generation adds
+// the tile-rows' sums as combine_row<true> does and the block that finishes a row stores
+// its totals; a sparse generation adds only the signed changes of the vectors it drew
+// again (fdacc, before the row's count with a fence in between), and the block that
+// finishes the row adds them to the totals of the generation before.
+__device__ __forceinline__ void combine_row_keep(const GenParams &p, int32_t c, uint64_t sw, uint64_t sv,
+                                                 int32_t t)
+{
+    const unsigned long long add = (1ull << 52) | (sv << 26) | sw;
+    const unsigned long long old = atomicAdd(p.acc + c, add);
+    if ((int32_t)(old >> 52) == p.ntile - 1) {
+        const unsigned long long full = old + add;
+        p.acc[c] = 0ull;
+        p.fprev[c] = full & ((1ull << 52) - 1ull);
+        finish_row(p, c, (int64_t)(full & 0x3ffffffull), (int64_t)((full >> 26) & 0x3ffffffull), t);
+    }
+}
+
+__device__ __forceinline__ void combine_row_delta(const GenParams &p, int32_t c, int32_t dw, int32_t dv,
+                                                  int32_t t)
+{
+    if ((dw | dv) != 0) {
+        atomicAdd(p.fdacc + 2 * (size_t)c, (unsigned long long)(long long)dw);
+        atomicAdd(p.fdacc + 2 * (size_t)c + 1, (unsigned long long)(long long)dv);
+        __threadfence();
+    }
+    const unsigned long long old = atomicAdd(p.acc + c, 1ull << 52);
+    if ((int32_t)(old >> 52) == p.ntile - 1) {
+        __threadfence();
+        const long long w = (long long)__ldcg(p.fdacc + 2 * (size_t)c);
+        const long long v = (long long)__ldcg(p.fdacc + 2 * (size_t)c + 1);
+        p.acc[c] = 0ull;
+        p.fdacc[2 * (size_t)c] = 0ull;
+        p.fdacc[2 * (size_t)c + 1] = 0ull;
+        const unsigned long long prev = p.fprev[c];
+        const int64_t SW = (int64_t)(prev & 0x3ffffffull) + w, SV = (int64_t)((prev >> 26) & 0x3ffffffull) + v;
+        p.fprev[c] = ((unsigned long long)SV << 26) | (unsigned long long)SW;
+        finish_row(p, c, SW, SV, t);
+    }
+}
+
 // Adds the block's tile-row sums of a segment to the rows (one atomic per tile-row) and
-// clears the shared accumulators. Called by the whole block.
-template <bool kNarrow>
+// clears the shared accumulators. Called by the whole block. kMode 1: the packed sums
+// with the row totals kept (combine_row_keep); kMode 2: signed 32-bit changes
+// (combine_row_delta).
+template <bool kNarrow, int kMode = 0>
 __device__ __forceinline__ void flush_segment(const GenParams &p, int32_t t, int ra, int seg_rows,
                                               uint32_t *s_acc32, unsigned long long *s_acc64)
 {
     __syncthreads();
     for (int i = threadIdx.x; i < seg_rows; i += kThreads) {
-        if (kNarrow) {
+        if (kMode == 2) {
+            combine_row_delta(p, ra + i, (int32_t)s_acc32[2 * i], (int32_t)s_acc32[2 * i + 1], t);
+            s_acc32[2 * i] = 0u;
+            s_acc32[2 * i + 1] = 0u;
+        } else if (kMode == 1) {
+            combine_row_keep(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1], t);
+            s_acc32[2 * i] = 0u;
+            s_acc32[2 * i + 1] = 0u;
+        } else if (kNarrow) {
             combine_row<true>(p, ra + i, s_acc32[2 * i], s_acc32[2 * i + 1], t);
             s_acc32[2 * i] = 0u;
             s_acc32[2 * i + 1] = 0u;
@@ -756,6 +857,16 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
+// Appends one 16-bit F word to the 8-word group q (a shift register: the first word of the
+// group ends in the low half of q.x after eight appends).
+__device__ __forceinline__ void f_push(uint4 &q, uint32_t w)
+{
+    q.x = __funnelshift_r(q.x, q.y, 16);
+    q.y = __funnelshift_r(q.y, q.z, 16);
+    q.z = __funnelshift_r(q.z, q.w, 16);
+    q.w = (q.w >> 16) | (w << 16);
+}
+
 // One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation. kS8:
 // the state is stored as bytes (copied 8 bytes per pass, widened to 16-bit lanes).
 // kSegDelta: rule R1 deltas formed once per segment into s_delta. The host selects it with
@@ -764,15 +875,24 @@ __device__ __forceinline__ void cp_async_wait()
 // segments are many and short, forms the deltas every pass (4,618 vs 4,338 solves/s on c4).
 // kUnroll2: the pass loop unrolled twice (the batched kernel: c4 4,692 vs 4,593 solves/s;
 // no gain for the single-instance kernels, c2 9.90 vs 9.70 us per generation).
+//
+// kF: the instance keeps fixed-vector words (tiles of 256 vectors, one row per pass, segments
+// starting at a multiple of 8 rows): the pass's F is formed from its threshold words and
+// alleles, the words of 8 rows are stored together, and nfix counts the nonzero ones.
+// Both count in nskip the vectors that did not draw (the fixed-allele passes).
+// kSample (an instance whose words are not kept yet): nfix counts 16 for every vector the
+// fixed-allele test finds at the bounds (the test runs on about one pass in 16 while the
+// population is spread), an estimate that decides when to start keeping them.
 template <bool kNarrow, int kRule, bool kCip, class Keys, bool kS8 = false, bool kSegDelta = false,
-          bool kUnroll2 = false>
+          bool kUnroll2 = false, bool kF = false, bool kSample = false>
 __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &keys, const BlockShare &b,
                                              int tile, int ra, int seg_rows, int32_t t,
                                              const uint8_t *x_prev, uint8_t *x_cur,
                                              const uint8_t *elite_row,
                                              const unsigned char *thr_bytes, uint4 *slots,
                                              uint32_t *s_acc32, unsigned long long *s_acc64,
-                                             int &countdown)
+                                             int &countdown, uint32_t *nfix = nullptr,
+                                             uint32_t *nskip = nullptr)
 {
     const int rpp = b.rows_per_pass;
     const int passes = (seg_rows + rpp - 1) / rpp;
@@ -795,6 +915,11 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     uint8_t *xst_ptr = xptr;
     const uint8_t *xo_ptr = xoptr;
     int rr = b.r_sub;
+    // kF: words of the current group of 8 rows (oldest in the low half of fq.x) and where
+    // the group goes
+    uint4 fq = make_uint4(0u, 0u, 0u, 0u);
+    uint4 *fptr = nullptr;
+    if constexpr (kF) fptr = reinterpret_cast<uint4 *>(p.fword + f_index(p, tile, ra, b.v_in));
     auto issue = [&](uint32_t stage, bool v) {
         if constexpr (kS8)
             cp_async8(slots + (size_t)stage * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
@@ -829,11 +954,16 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         else sv = slots[(size_t)slot * kThreads];
 
         const bool ok = rr < seg_rows;
-        uint32_t xbits, accn;
+        uint32_t xbits, accn, zor = 1u, nsat = 0u;
         int64_t acw, acv;
         bool fixed;
         sv = qubit_pass<kNarrow, kRule, kCip, Keys, kSegDelta>(p, keys, g, sv, xo, ra_key + rr, t, thr_bytes,
-                                                               fixed, countdown, xbits, accn, acw, acv);
+                                                               fixed, countdown, xbits, accn, acw, acv,
+                                                               kF ? &zor : nullptr, kSample ? &nsat : nullptr);
+        if constexpr (kSample) *nfix += 16u * nsat;
+        if constexpr (kF || kSample) {
+            if (fixed && g.active && ok) ++*nskip;
+        }
         if (g.active && ok) {
             if (!fixed) {               // a fixed pass leaves the state as it is
                 if constexpr (kS8) *st_ptr = pack8(sv);
@@ -841,13 +971,249 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
             }
             *xst_ptr = (uint8_t)xbits;
         }
+        if constexpr (kF) {
+            const uint32_t fw = (g.active && ok && zor == 0u) ? (0x100u | xbits) : 0u;
+            *nfix += fw != 0u ? 1u : 0u;
+            f_push(fq, fw);
+            if ((rr & 7) == 7) {
+                if (g.active) *fptr = fq;
+                fptr += kThreads;       // the next group: 256 vectors x 8 words on
+            }
+        }
         add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
         st_ptr += sstep;
         xst_ptr += xstep;
         rr += rpp;
     }
+    if constexpr (kF) {                 // the last group of a tile's rows: pad with zeros
+        if ((seg_rows & 7) != 0) {
+            for (int k = seg_rows & 7; k < 8; ++k) f_push(fq, 0u);
+            if (g.active) *fptr = fq;
+        }
+    }
     cp_async_wait<0>();
-    flush_segment<kNarrow>(p, t, ra, seg_rows, s_acc32, s_acc64);
+    flush_segment<kNarrow, (kF || kSample) ? 1 : 0>(p, t, ra, seg_rows, s_acc32, s_acc64);
+}
+
+// ---------------------------------------------------------------------------------------
+// Sparse form of a tile segment (instances that keep F: rule R1, packed sums, 16-bit state,
+// tiles of 256 vectors; generations that rotate, i.e. not a run's first). Once most of the
+// population has collapsed, most vectors are stable: every qubit at a bound on the side of
+// the previous elite's allele, so CIP leaves it, the observation cannot differ from the
+// side, the state needs no read or write, and the vector's alleles, hence its share of the
+// row sums, are those of the generation before. Which vectors are unstable follows the
+// columns (a gene where the elite left the consensus is unstable in nearly every row), so a
+// warp whose lane kept its column would still run the full pass for almost every row.
+// Instead each warp:
+//   1. reads F of 8 rows of its 32 vectors at a time (one 16-byte load a lane) and writes a
+//      stable vector's alleles (its side bits); nothing else: the row totals of the
+//      generation before (fprev) already hold its share;
+//   2. lists the unstable (row, vector) pairs in its slice of a shared-memory ring;
+//   3. streams the listed vectors' state, and the word of the previous alleles, through
+//      per-thread cp.async rings, 32 per step, and runs the full pass on each (the vector's
+//      items and CIP steps are read from the slots of the lane that owns its column): CIP,
+//      QIP, the state, the alleles and, when it changed, F; its sums enter the row as the
+//      signed change against the previous alleles (two shared atomics), which
+//      combine_row_delta adds to the row's totals.
+// Listing runs ahead of the copies, so the ring's 7 rows of look-ahead become 7 steps of
+// 32 listed vectors. All sums are exact integers, so the results equal the dense form's.
+// Segments start at a multiple of 8 rows and hold at most 256 (the row fits 8 bits of a
+// list entry: row << 6 | lane << 1 | F nonzero).
+// ---------------------------------------------------------------------------------------
+constexpr int kListCap = 512;               // entries of a warp's list (a power of two)
+__shared__ uint16_t s_list[kThreads / 32][kListCap];
+__shared__ uint32_t s_xo[kRingStages][kThreads];   // per-thread ring of previous-allele words
+
+// Packed narrow sums (sum v << 16 | sum w) of 8 genes from their alleles (bit i = gene i)
+// and the vector's item byte vectors.
+__device__ __forceinline__ uint32_t narrow_sums_bits(uint32_t x8, uint4 ib)
+{
+    const uint32_t xa = allele_bytes(x8 & 15u), xb = allele_bytes((x8 >> 4) & 15u);
+    const uint32_t sw = __dp4a(xa, ib.x, __dp4a(xb, ib.y, 0u));
+    const uint32_t sv = __dp4a(xa, ib.z, __dp4a(xb, ib.w, 0u));
+    return sw | (sv << 16);
+}
+
+// 4-byte global->shared copy; src_bytes = 0 writes zeros (nothing is read).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int ra, int seg_rows, int32_t t,
+                                               const uint8_t *x_prev, uint8_t *x_cur, const uint8_t *elite_row,
+                                               const unsigned char *thr_bytes, uint4 *slots,
+                                               uint32_t *s_acc32, uint16_t *list, uint32_t &nfix,
+                                               uint32_t &nskip)
+{
+    constexpr uint32_t kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int wbase = threadIdx.x & ~31;        // slot (and tile vector) of the warp's lane 0
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t off_top = (uint32_t)(8 * p.K);
+    const uint32_t k8 = off_top * 0x00010001u;
+    const uint32_t ra_key = (uint32_t)(ra + p.row0);
+    const size_t svec = (size_t)p.svec, xstride = (size_t)p.xstride;
+
+    // F of the next groups of 8 rows in flight (one group's work is too short to cover a
+    // load's latency); the first loads go out before the segment's other loads
+    const bool active = (uint32_t)tile * kThreads + threadIdx.x < (uint32_t)p.svec;
+    const uint4 *fsrc = reinterpret_cast<const uint4 *>(p.fword + f_index(p, tile, ra, threadIdx.x));
+    const int nchunk = (seg_rows + 7) >> 3;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    auto fload = [&](int k) -> uint4 {
+        return (active && k < nchunk) ? __ldcg(fsrc + (size_t)k * kThreads) : zero4;
+    };
+    uint4 fb0 = fload(0), fb1 = fload(1), fb2 = fload(2), fb3 = fload(3), fb4 = fload(4), fb5 = fload(5);
+
+    SegCtx g;
+    seg_setup<true, true, true>(p, g, tile, threadIdx.x, kThreads, elite_row);
+    __syncwarp();                               // lanes read the other lanes' slots
+    const uint32_t vec0 = (uint32_t)tile * kThreads + (uint32_t)wbase;
+    uint4 *const sbase = p.state + (size_t)ra * svec + vec0;       // row ra, the warp's vector 0
+    uint8_t *const xbase = x_cur + (size_t)ra * xstride + vec0;
+    const uint8_t *const xobase = x_prev + (size_t)ra * xstride + vec0;
+    // a pair word's halves are 0 exactly where the row is stable: F = 0x100 | the elite's
+    // alleles of this vector
+    const uint32_t tgt = (0x100u | g.e8) * 0x00010001u;
+    int chunk = 0;
+    uint32_t head = 0;                          // entries listed so far (warp-uniform)
+
+    // Step 1 and 2 for the next 8 rows (bit j of the masks = row r0 + j).
+    auto produce = [&]() {
+        const uint4 f = fb0;
+        fb0 = fb1;
+        fb1 = fb2;
+        fb2 = fb3;
+        fb3 = fb4;
+        fb4 = fb5;
+        fb5 = fload(chunk + 6);
+        const int r0 = chunk << 3;
+        ++chunk;
+        const uint32_t d[4] = {f.x ^ tgt, f.y ^ tgt, f.z ^ tgt, f.w ^ tgt};
+        const int nvalid = g.active ? min(8, seg_rows - r0) : 0;
+        uint32_t sm = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t h = (j & 1) ? (d[j >> 1] >> 16) : (d[j >> 1] & 0xffffu);
+            sm |= (h == 0u && j < nvalid ? 1u : 0u) << j;
+        }
+        const uint32_t vm = nvalid >= 8 ? 0xffu : ((1u << nvalid) - 1u);
+        const uint32_t um = vm & ~sm;
+        nfix += (uint32_t)__popc(sm);
+        nskip += (uint32_t)__popc(sm);
+        uint8_t *xp = xbase + (size_t)r0 * xstride + lane;
+        const uint8_t side = (uint8_t)g.e8;     // a stable vector's alleles
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if ((sm >> j) & 1u) *xp = side;
+            xp += xstride;
+        }
+        if (__any_sync(kFull, um != 0u)) {
+            const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t w = (j & 1) ? (fw[j >> 1] >> 16) : (fw[j >> 1] & 0xffffu);
+                const bool u = (um >> j) & 1u;
+                const uint32_t bal = __ballot_sync(kFull, u);
+                if (u)
+                    list[(head + (uint32_t)__popc(bal & lt)) & (kListCap - 1)] =
+                        (uint16_t)(((uint32_t)(r0 + j) << 6) | ((uint32_t)lane << 1) | (w != 0u ? 1u : 0u));
+                head += (uint32_t)__popc(bal);
+            }
+        }
+    };
+
+    // Copies of step j (entries 32 j .. 32 j + 31) into ring slot j % 8: the state and the
+    // aligned word holding the previous alleles; the step must be listed in full (or the
+    // listing finished).
+    auto issue = [&](uint32_t j) {
+        const uint32_t i = j * 32u + (uint32_t)lane;
+        const bool has = i < head;
+        const void *src = p.state;
+        const void *xsrc = p.state;
+        if (has) {
+            const uint32_t e = list[i & (kListCap - 1)];
+            const size_t row = e >> 6, col = (e >> 1) & 31u;
+            src = sbase + row * svec + col;
+            xsrc = reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(xobase + row * xstride + col) &
+                                                  ~(uintptr_t)3);
+        }
+        const uint32_t slot = j & (kRingStages - 1);
+        cp_async16(slots + (size_t)slot * kThreads, src, has ? 16u : 0u);
+        cp_async4(&s_xo[slot][threadIdx.x], xsrc, has ? 4u : 0u);
+        cp_async_commit();
+    };
+
+    // Step 3 for step j.
+    auto compute = [&](uint32_t j) {
+        const uint32_t i = j * 32u + (uint32_t)lane;
+        if (i >= head) return;
+        const uint32_t e = list[i & (kListCap - 1)];
+        const uint32_t row = e >> 6;
+        const uint32_t col = (e >> 1) & 31u;
+        const int cv = wbase + (int)col;
+        const uint32_t ctr = 2u * (vec0 + col);
+        const uint32_t slot = j & (kRingStages - 1);
+        uint4 s = slots[(size_t)slot * kThreads];
+        const uint32_t xo = (s_xo[slot][threadIdx.x] >> (8u * ((vec0 + col) & 3u))) & 0xffu;
+        const uint4 d = s_delta[cv];
+        s.x = rotate_pair_signed(s.x, d.x, k8);
+        s.y = rotate_pair_signed(s.y, d.y, k8);
+        s.z = rotate_pair_signed(s.z, d.z, k8);
+        s.w = rotate_pair_signed(s.w, d.w, k8);
+        const Draw4 r0 = philox4x32_10_rk(ctr, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r1 = philox4x32_10_rk(ctr + 1u, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
+        const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
+        uint32_t xbits = 0u, z = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t off = (k & 1) ? (sp[k >> 1] >> 16) : (sp[k >> 1] & 0xffffu);
+            const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+            z |= thr;
+            if ((u[k] < thr) || (off == off_top)) xbits |= 1u << k;
+        }
+        if (xbits != xo) {
+            const uint4 ib = s_item_bytes[cv];
+            const uint32_t a = narrow_sums_bits(xbits, ib), b = narrow_sums_bits(xo, ib);
+            atomicAdd(s_acc32 + 2 * row, (a & 0xffffu) - (b & 0xffffu));
+            atomicAdd(s_acc32 + 2 * row + 1, (a >> 16) - (b >> 16));
+        }
+        sbase[(size_t)row * svec + col] = s;
+        xbase[(size_t)row * xstride + col] = (uint8_t)xbits;
+        const uint32_t fwn = z == 0u ? (0x100u | xbits) : 0u;
+        if (fwn != 0u || (e & 1u)) p.fword[f_index(p, tile, ra + (int)row, cv)] = (uint16_t)fwn;
+        nfix += fwn != 0u ? 1u : 0u;
+    };
+
+    // Listing runs ahead of the copies in bursts: the steps up to jc + 7 are listed before
+    // the copies of jc + 7 are issued, and a burst stops once they are, so the live entries
+    // (from step jc on) stay below 32 (jc + 8) + 256 <= 32 jc + 512, the list's size. The
+    // loop between bursts issues and computes without listing.
+    while (chunk < nchunk && head < 8u * 32u) produce();
+    __syncwarp();
+#pragma unroll 1
+    for (uint32_t j = 0; j < kRingStages - 1; ++j) issue(j);
+    uint32_t jc = 0;
+#pragma unroll 1
+    for (;;) {
+        while (chunk < nchunk && head < (jc + 8u) * 32u) produce();
+        __syncwarp();
+        const bool done = chunk >= nchunk;
+        const uint32_t avail = done ? (head + 31u) / 32u : head / 32u;
+        if (jc >= avail) break;
+        const uint32_t jend = done ? avail : avail - (kRingStages - 1);
+#pragma unroll 1
+        for (; jc < jend; ++jc) {
+            issue(jc + kRingStages - 1);
+            cp_async_wait<kRingStages - 1>();
+            compute(jc);
+        }
+    }
+    cp_async_wait<0>();
+    flush_segment<true, 2>(p, t, ra, seg_rows, s_acc32, nullptr);
 }
 
 template <bool kNarrow>
@@ -891,7 +1257,15 @@ __device__ __forceinline__ void generation_body_ring(const GenParams &p, const B
 // empty while the others finish; taken from a queue in order of decreasing size, the
 // segments keep every block busy until the work runs out. Any split gives the same
 // results: each tile-row's sums are exact integers added once per segment.
-template <bool kNarrow, int kRule, bool kCip, bool kS8 = false, bool kSegDelta = false>
+//
+// kF (instances that can keep F). While fcnt[3] is 0 the words are not kept: they are all 0
+// (cleared with the state and never written since), the dense form runs as without them and
+// estimates the fixed vectors from the fixed-allele test's samples. Once that estimate
+// reaches f_on_min the words are kept from then on (fcnt[3] = 1, set by block 0 of the
+// first such generation): the dense form writes every vector's F, and a generation takes the
+// sparse form (sparse_segment) when at least sparse_min vectors were fixed after the one
+// before. Each warp adds its count (exact, or the estimate) to fcnt[t % 3].
+template <bool kNarrow, int kRule, bool kCip, bool kS8 = false, bool kSegDelta = false, bool kF = false>
 __device__ __forceinline__ void generation_body_queue(const GenParams &p, const BlockShare &b,
                                                       int32_t t, int32_t e_prev, uint4 *ring,
                                                       const uint32_t *s_thr, uint32_t *s_acc32,
@@ -905,18 +1279,69 @@ __device__ __forceinline__ void generation_body_queue(const GenParams &p, const 
     uint4 *slots = ring + threadIdx.x;
     unsigned int *ctr = p.qctr + (t % 3);
     int countdown = 0;
+    uint32_t nfix = 0u, nskip = 0u;
+    bool keep = false, sparse = false;
+    __shared__ unsigned long long s_cnt[2];
+    if constexpr (kF) {
+        const unsigned long long prev = __ldcg(p.fcnt + (t + 2) % 3);
+        keep = __ldcg(p.fcnt + 3) != 0ull || prev >= p.f_on_min;
+        sparse = kCip && keep && prev >= p.sparse_min;
+        if (keep && blockIdx.x == 0 && threadIdx.x == 0) p.fcnt[3] = 1ull;
+        if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0ull;   // read after the loop's barriers
+    }
     clear_row_sums<kNarrow>(p.seg_rows_max, s_acc32, s_acc64);
+    // Sparse generations: thread 0 takes the next segment's index while the block works on
+    // the current one (the atomic's round trip is off the block's path; a sparse
+    // segment's work is short) and publishes it after the segment's last barrier, with one
+    // more barrier before every thread reads it. Dense ones take it when they need it
+    // (holding a second segment would coarsen the end of the guided schedule).
+    if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
+    __syncthreads();
+    int32_t qi = s_qi;
     for (;;) {
-        // every thread reads the index before the segment's first barrier, after which
-        // thread 0 may overwrite it
-        if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
-        __syncthreads();
-        const int32_t qi = s_qi;
         if (qi >= p.nsegs) break;
+        int32_t next = 0;
+        if (sparse && threadIdx.x == 0) next = (int32_t)atomicAdd(ctr, 1u);
         const int4 sg = __ldg(p.segq + qi);
-        ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta>(p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t,
-                                                                      x_prev, x_cur, elite_row, thr_bytes, slots,
-                                                                      s_acc32, s_acc64, countdown);
+        if constexpr (kF) {
+            if (sparse)
+                sparse_segment(p, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots, s_acc32,
+                               s_list[threadIdx.x >> 5], nfix, nskip);
+            else if (keep)
+                ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta, false, true>(
+                    p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots, s_acc32,
+                    s_acc64, countdown, &nfix, &nskip);
+            else
+                ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta, false, false, true>(
+                    p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots, s_acc32,
+                    s_acc64, countdown, &nfix, &nskip);
+        } else {
+            ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta>(p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t,
+                                                                          x_prev, x_cur, elite_row, thr_bytes,
+                                                                          slots, s_acc32, s_acc64, countdown);
+        }
+        if (sparse) {
+            if (threadIdx.x == 0) s_qi = next;
+            __syncthreads();
+        } else {
+            // every thread has read the index before the segment's first barrier
+            if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
+            __syncthreads();
+        }
+        qi = s_qi;
+    }
+    if constexpr (kF) {
+        // one atomic per block for each count
+        const uint32_t n = __reduce_add_sync(0xffffffffu, nfix), d = __reduce_add_sync(0xffffffffu, nskip);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_cnt[0], (unsigned long long)n);
+            atomicAdd(&s_cnt[1], (unsigned long long)d);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_cnt[0] != 0ull) atomicAdd(p.fcnt + t % 3, s_cnt[0]);
+            if (s_cnt[1] != 0ull) atomicAdd(p.fcnt + 4 + t % 3, s_cnt[1]);
+        }
     }
 }
 
@@ -1059,15 +1484,16 @@ __device__ __forceinline__ SmemParts carve_smem(unsigned char *raw)
 }
 
 // queued: take the segments from the instance's queue (deferred forms with a queue).
-template <bool kNarrow, int kRule, bool kCip, bool kRing, bool kS8 = false, bool kSegDelta = false>
+template <bool kNarrow, int kRule, bool kCip, bool kRing, bool kS8 = false, bool kSegDelta = false,
+          bool kF = false>
 __device__ __forceinline__ void one_generation(const GenParams &p, const BlockShare &b, int32_t t,
                                                int32_t e_prev, SmemParts &m, const uint32_t *s_thr,
                                                bool queued = false)
 {
     if constexpr (kRing) {
         if (queued && p.nsegs > 0)
-            generation_body_queue<kNarrow, kRule, kCip, kS8, kSegDelta>(p, b, t, e_prev, m.ring, s_thr,
-                                                                        m.acc32, m.acc64);
+            generation_body_queue<kNarrow, kRule, kCip, kS8, kSegDelta, kF>(p, b, t, e_prev, m.ring, s_thr,
+                                                                            m.acc32, m.acc64);
         else
             generation_body_ring<kNarrow, kRule, kCip, kS8, kSegDelta>(p, b, t, e_prev, m.ring, s_thr,
                                                                        m.acc32, m.acc64);
@@ -1595,7 +2021,10 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) resident_run_kernel
 // Three blocks per SM (the host's grid), so up to 85 registers a thread: the compiler takes
 // 76 for the narrow ring form, which measured c3 348 vs 361 us per generation against the
 // 64 that four blocks would allow.
-template <bool kNarrow, int kRule, bool kRing, bool kS8 = false, bool kSegDelta = false>
+//
+// kF: the variant for instances that keep F (rule R1, packed sums, 16-bit state, the ring,
+// per-segment deltas, deferred close with a segment queue); the host runs it only so.
+template <bool kNarrow, int kRule, bool kRing, bool kS8 = false, bool kSegDelta = false, bool kF = false>
 __global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) generation_kernel(const GenParams p)
 {
     __shared__ uint32_t s_thr[kMaxThr];
@@ -1641,14 +2070,21 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) generation_kernel(c
             if (threadIdx.x == 0) {
                 *key_slot(p, t + 1) = 0ull;
                 p.qctr[(t + 1) % 3] = 0u;
+                if (kF) {
+                    p.fcnt[(t + 1) % 3] = 0ull;
+                    p.fcnt[4 + (t + 1) % 3] = 0ull;
+                    if (t >= 1 && p.hist_d) p.hist_d[t - 1] = p.fcnt[4 + (t + 2) % 3];
+                }
             }
         }
         if (stop == kStopPending) {
             final_cip_body<kRule, kS8>(p, b, t - 1, e_prev);   // the CIP of the converged generation
             return;
         }
-        if (p.apply_cip) one_generation<kNarrow, kRule, true, kRing, kS8, kSegDelta>(p, b, t, e_prev, m, s_thr, true);
-        else one_generation<kNarrow, kRule, false, kRing, kS8, kSegDelta>(p, b, t, e_prev, m, s_thr, true);
+        if (p.apply_cip)
+            one_generation<kNarrow, kRule, true, kRing, kS8, kSegDelta, kF>(p, b, t, e_prev, m, s_thr, true);
+        else
+            one_generation<kNarrow, kRule, false, kRing, kS8, kSegDelta, kF>(p, b, t, e_prev, m, s_thr, true);
         allow_dependent_launch();
         return;
     }
@@ -1812,6 +2248,7 @@ __global__ void __launch_bounds__(kThreads) cip_kernel(const GenParams p)
         if (s_stop) return;
         const int32_t t_last = s_t, e = s_e;
         if (blockIdx.x == 0) {
+            if (threadIdx.x == 0 && p.fword && p.hist_d) p.hist_d[t_last] = p.fcnt[4 + t_last % 3];
             const int32_t run = record_generation(p, t_last, e, s_f);
             if (run >= kConvergeWindow && threadIdx.x == 0) {
                 p.conv[3] = t_last;
@@ -2316,6 +2753,17 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
     for (size_t i = i0; i < (size_t)p.np; i += stride) {
         p.fitness[i] = 0;
         p.cnt[i] = 0u;
+    }
+    if (p.fword) {   // no qubit at a bound: every fixed-vector word 0
+        uint4 *f = reinterpret_cast<uint4 *>(p.fword);
+        const size_t n = (size_t)p.ntile * (size_t)p.np8 * kThreads;
+        for (size_t i = i0; i < n; i += stride) f[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (size_t i = i0; i < (size_t)p.np; i += stride) {
+            p.fprev[i] = 0ull;
+            p.fdacc[2 * i] = p.fdacc[2 * i + 1] = 0ull;
+        }
+        if (i0 == 0)
+            for (int i = 0; i < 7; ++i) p.fcnt[i] = 0ull;
     }
     if (i0 == 0) {
         *p.gen = 0;

@@ -38,6 +38,8 @@ QIEO_FLAG_PER_GENERATION = 0x200
 QIEO_FLAG_TIME_GENERATIONS = 0x400
 QIEO_FLAG_STREAMED = 0x800
 QIEO_FLAG_SIXTEEN = 0x1000
+QIEO_FLAG_NO_FIXED_WORDS = 0x2000
+QIEO_FLAG_SPARSE_ALWAYS = 0x4000
 
 # Every symbol include/qieo.h declares.
 EXPORTS = (
@@ -47,6 +49,7 @@ EXPORTS = (
     "qieo_get_alleles", "qieo_get_allele_row", "qieo_get_elite_history", "qieo_get_threshold_table",
     "qieo_get_launch_shape", "qieo_set_launch_shape", "qieo_get_kernel_time",
     "qieo_get_phase_times", "qieo_get_generation_times", "qieo_measure_integer_ceiling",
+    "qieo_get_drawn_vectors",
     "qieo_create_row_block", "qieo_rows_observe", "qieo_rows_rotate",
     "qieo_get_convergence", "qieo_checkpoint_size",
     "qieo_checkpoint_save", "qieo_checkpoint_load", "qieo_philox",
@@ -84,7 +87,8 @@ class qieo_params(C.Structure):
 class qieo_launch_shape(C.Structure):
     _fields_ = [("lanes_per_row", C.c_int32), ("warps_per_row", C.c_int32),
                 ("grid_ctas", C.c_int32), ("narrow", C.c_int32), ("tiles", C.c_int32),
-                ("rows_per_cta", C.c_int32), ("persistent", C.c_int32), ("resident", C.c_int32)]
+                ("rows_per_cta", C.c_int32), ("persistent", C.c_int32), ("resident", C.c_int32),
+                ("fixed_words", C.c_int32)]
 
 
 class qieo_server_config(C.Structure):
@@ -147,6 +151,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "qieo_get_kernel_time": ([P, P, P], C.c_int),
         "qieo_get_phase_times": ([P, P, P], C.c_int),
         "qieo_get_generation_times": ([P, i32, P, P], C.c_int),
+        "qieo_get_drawn_vectors": ([P, i32, i32, P], C.c_int),
         "qieo_measure_integer_ceiling": ([i32, P], C.c_int),
         "qieo_create_row_block": ([P, P, i32, P], C.c_int),
         "qieo_rows_observe": ([P, i32, P, P], C.c_int),
@@ -337,6 +342,12 @@ def qieo_get_kernel_time(h):
     ms, n = C.c_double(), C.c_int64()
     _check(load().qieo_get_kernel_time(h, C.byref(ms), C.byref(n)))
     return float(ms.value), int(n.value)
+
+
+def qieo_get_drawn_vectors(h, first: int, n: int) -> np.ndarray:
+    out = np.zeros(max(int(n), 0), dtype=np.int64)
+    _check(load().qieo_get_drawn_vectors(h, int(first), int(n), _ptr(out)))
+    return out
 
 
 def qieo_get_generation_times(h, n: int) -> np.ndarray:
@@ -599,6 +610,9 @@ class Instance:
 
     def generation_times(self, n: int) -> np.ndarray:
         return qieo_get_generation_times(self.h, n)
+
+    def drawn_vectors(self, first: int, n: int) -> np.ndarray:
+        return qieo_get_drawn_vectors(self.h, first, n)
 
     def phase_times(self):
         return qieo_get_phase_times(self.h)

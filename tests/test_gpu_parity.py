@@ -185,11 +185,14 @@ def test_async_ring_and_register_streaming_agree(rule):
 
 def test_long_shares_split_into_segments():
     """Two blocks over 6000 rows x 2 tiles: each block's share crosses a tile boundary and
-    exceeds the 1536 tile-rows its shared memory sums at once."""
+    exceeds the 1536 tile-rows its shared memory sums at once. With fixed-vector words the
+    queue's segments are at most 256 rows."""
     prob = W.knapsack(2050, 18)
-    shape = compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2))
-    assert shape.tiles == 2 and shape.rows_per_cta == 1536
+    shape = compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2), flags=Q.QIEO_FLAG_NO_FIXED_WORDS)
+    assert shape.tiles == 2 and shape.rows_per_cta == 1536 and shape.fixed_words == 0
     compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2), flags=Q.QIEO_FLAG_REGISTER_PREFETCH)
+    shape = compare(prob, 6000, [2, 1], seed=18, shape=(32, 8, 2))
+    assert shape.tiles == 2 and shape.rows_per_cta == 256 and shape.fixed_words == 1
 
 
 def test_wide_items_and_penalty():
