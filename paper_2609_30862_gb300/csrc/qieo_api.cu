@@ -188,6 +188,9 @@ struct qieo_instance {
     // instance keeps none
     void *fword_mem = nullptr;
     size_t fword_bytes = 0;
+    size_t fword_state_bytes = 0;      // the counters, words and row totals (cleared together);
+                                       // the tile sums after them stay
+    std::vector<uint32_t> tile_sums;   // per tile of 256 vectors: sum of weights, of values
 };
 
 namespace {
@@ -433,6 +436,7 @@ bool wants_fword(const qieo_instance *q, bool use_ring)
     return !(q->flags & (QIEO_FLAG_NO_FIXED_WORDS | QIEO_FLAG_SIXTEEN | QIEO_FLAG_CONVERGE | QIEO_FLAG_UNFUSED |
                          QIEO_FLAG_COOPERATIVE)) &&
            use_ring && q->narrow && !q->state8 && q->rule == 0 && q->key_ok && !q->host_de && q->lanes == 32 &&
+           q->sum_w < ((int64_t)1 << 25) && q->sum_v < ((int64_t)1 << 25) && !q->tile_sums.empty() &&
            q->warps == 8 && q->owns_block && !q->row_block && !use_resident(q) && !use_cooperative(q);
 }
 
@@ -441,15 +445,16 @@ bool wants_fword(const qieo_instance *q, bool use_ring)
 qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
 {
     qieo::GenParams &g = q->gp;
-    // [counters: 256 B][the words][row totals: np x 8 B][row changes: np x 16 B]
-    const int32_t np8 = (q->np + 7) / 8;
-    const size_t words = align_up((size_t)ntile * (size_t)np8 * qieo::kThreads * 8 * sizeof(uint16_t), 256);
+    // [counters: 256 B][the words: np x fstride][row totals: np x 8 B][tile item sums]
+    const int32_t fstride = ntile * qieo::kThreads;
+    const size_t words = align_up((size_t)q->np * (size_t)fstride * sizeof(uint16_t), 256);
     const size_t prev = align_up((size_t)q->np * 8, 256);
-    const size_t bytes = want ? 256 + words + prev + (size_t)q->np * 16 : 0;
+    const size_t bytes = want ? 256 + words + prev + (size_t)ntile * 8 : 0;
     if (bytes != q->fword_bytes) {
         if (q->fword_mem) cudaFreeAsync(q->fword_mem, q->stream);
         q->fword_mem = nullptr;
         q->fword_bytes = 0;
+        q->fword_state_bytes = 0;
         if (bytes) {
             keep_pool_memory(q->device);
             cudaError_t ce = cudaMallocAsync(&q->fword_mem, bytes, q->stream);
@@ -460,15 +465,21 @@ qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
                             "fixed-vector words (%zu bytes): %s", bytes, cudaGetErrorString(ce));
             }
             q->fword_bytes = bytes;
+            q->fword_state_bytes = 256 + words + prev;
             CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, bytes, q->stream));
+            if ((int)q->tile_sums.size() != 2 * ntile) return fail(QIEO_ERR_INVALID, "internal: tile sums");
+            CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(q->fword_mem) + 256 + words + prev, q->tile_sums.data(),
+                                     (size_t)ntile * 8, cudaMemcpyHostToDevice, q->stream));
         }
     }
     char *base = static_cast<char *>(q->fword_mem);
     g.fcnt = bytes ? reinterpret_cast<unsigned long long *>(base) : nullptr;
     g.fword = bytes ? reinterpret_cast<uint16_t *>(base + 256) : nullptr;
     g.fprev = bytes ? reinterpret_cast<unsigned long long *>(base + 256 + words) : nullptr;
-    g.fdacc = bytes ? reinterpret_cast<unsigned long long *>(base + 256 + words + prev) : nullptr;
-    g.np8 = np8;
+    g.ftile = bytes ? reinterpret_cast<const uint32_t *>(base + 256 + words + prev) : nullptr;
+    g.fsum_w = q->sum_w;
+    g.fsum_v = q->sum_v;
+    g.fstride = fstride;
     const double vecs = (double)q->np * (double)q->svec;
     const double need = std::ceil(kSparseMinFraction * vecs), on = std::ceil(kFwordOnFraction * vecs);
     const bool always = (q->flags & QIEO_FLAG_SPARSE_ALWAYS) != 0;
@@ -477,10 +488,11 @@ qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
     return QIEO_OK;
 }
 
-// Every fixed-vector word to 0 (after the state changed outside the kernels that keep them).
+// Every fixed-vector word to 0 (after the state changed outside the kernels that keep them),
+// with the counters and row totals; the tile sums stay.
 qieo_status clear_fword(qieo_instance *q, cudaStream_t s)
 {
-    if (q->fword_bytes) CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, q->fword_bytes, s));
+    if (q->fword_state_bytes) CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, q->fword_state_bytes, s));
     return QIEO_OK;
 }
 
@@ -1303,6 +1315,14 @@ qieo_status create_instance_impl(const qieo_problem *pr, const qieo_params *pa,
         }
         wide[(size_t)j] = (uint32_t)pr->weights[j];
         wide[ngp + (size_t)j] = (uint32_t)pr->values[j];
+    }
+    if (q->narrow_items) {   // per tile of 256 vectors (2,048 genes): the biases of sparse row changes
+        const int32_t nt = (q->svec + qieo::kThreads - 1) / qieo::kThreads;
+        q->tile_sums.assign((size_t)2 * nt, 0u);
+        for (int32_t j = 0; j < q->ng; ++j) {
+            q->tile_sums[(size_t)2 * (j / (8 * qieo::kThreads))] += (uint32_t)pr->weights[j];
+            q->tile_sums[(size_t)2 * (j / (8 * qieo::kThreads)) + 1] += (uint32_t)pr->values[j];
+        }
     }
     std::vector<uint64_t> T;
     build_thresholds(q->D, T);

@@ -152,8 +152,8 @@ struct GenParams {
                                   // block of a population sharded by rows; 0 otherwise)
     unsigned long long *gen_ns;   // resident form: device clock (ns) at the start of each
                                   // generation of the run and at its end, or NULL
-    uint16_t *fword;              // fixed-vector words F of the stored state (see f_index),
-                                  // or NULL when the instance keeps none
+    uint16_t *fword;              // [np][fstride] fixed-vector words F of the stored state
+                                  // (see allele_bytes), or NULL when the instance keeps none
     unsigned long long *fcnt;     // [7] vectors whose F is nonzero after generation t, in
                                   // slot t % 3 (an estimate while the words are not kept);
                                   // [3]: 1 once the words are kept; [4 + t % 3]: vectors
@@ -163,9 +163,10 @@ struct GenParams {
                                   // NULL
     unsigned long long *fprev;    // [np] packed row totals (SV << 26 | SW) of the last
                                   // generation, kept by the kernel that keeps F
-    unsigned long long *fdacc;    // [2 np] signed changes of a sparse generation's row
-                                  // totals (w, v), reset by the block that finishes the row
-    int32_t np8;                  // rows of a tile in F, in groups of 8: ceil(np / 8)
+    const uint32_t *ftile;        // [2 ntile] sums of the weights and of the values of each
+                                  // tile's genes (the bias of a sparse generation's changes)
+    int64_t fsum_w, fsum_v;       // sums of all weights and of all values
+    int32_t fstride;              // words of a row of F: ntile * 256
     unsigned long long sparse_min;   // a generation takes the sparse form when at least
                                      // this many vectors were fixed after the one before
     unsigned long long f_on_min;     // the words are kept from the first generation after
@@ -506,14 +507,7 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
 // gene i) when all eight qubits sit at theta = 0 or pi/2 (n = 0 or 2K: each allele is then
 // the side of its bound whatever the draw), and 0 otherwise; 0 is also always a safe value
 // ("not known to be fixed"), so F may be cleared at any time. Instances that keep F store
-// it per tile of 256 vectors in groups of 8 rows, the words of one vector's group adjacent:
-// (tile, row, v_in) at ((tile * np8 + row / 8) * 256 + v_in) * 8 + row % 8, so a thread
-// reads or writes the words of 8 rows of its vector as one 16-byte access.
-__device__ __forceinline__ size_t f_index(const GenParams &p, int tile, int row, int v_in)
-{
-    return (((size_t)tile * (size_t)p.np8 + (size_t)(row >> 3)) * kThreads + (size_t)v_in) * 8 +
-           (size_t)(row & 7);
-}
+// it row-major, fstride (= ntile * 256) words a row.
 
 // Alleles of four genes (bit i = gene i of the nibble) -> bytes (x0, x2, x1, x3), the order
 // narrow_sums takes: the multiplier's terms 1, 2^15, 2^6, 2^21 move bit 0 to bit 0, bit 1 to
@@ -545,7 +539,7 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
                                             const unsigned char *thr_bytes, bool &fixed,
                                             int &countdown, uint32_t &xbits, uint32_t &accn,
                                             int64_t &acw, int64_t &acv, uint32_t *zor = nullptr,
-                                            uint32_t *nsat = nullptr)
+                                            uint32_t *nsat = nullptr, uint32_t *nskip = nullptr)
 {
     const uint32_t off_top = (uint32_t)(8 * p.K);
     const uint32_t k8 = off_top * 0x00010001u;
@@ -566,11 +560,12 @@ __device__ __forceinline__ uint4 qubit_pass(const GenParams &p, const Keys &keys
         const uint32_t xa = b0 | (b1 << 8), xb = b2 | (b3 << 8);
         const uint32_t xs = (allele_nibble_hi(xa) >> 24) | ((allele_nibble_hi(xb) >> 20) & 0xf0u);
         const bool ok = sat && (!kCip || ((g.e8 ^ xs) & m8) == 0u);
-        if (nsat && sat && g.active) ++*nsat;
+        if (nsat && sat && g.active) *nsat += 16u;
         if (__all_sync(0xffffffffu, ok)) {
             fixed = true;
             xbits = xs;
             if (zor) *zor = 0u;
+            if (nskip && g.active) ++*nskip;
             if (kNarrow) {
                 accn = narrow_sums(xa, xb);
             } else {
@@ -647,8 +642,9 @@ __device__ __forceinline__ void add_row_sums(int lanes, bool leader, bool ok, in
 // The kernel that keeps F also keeps every row's totals (fprev): a dense generation adds
 // the tile-rows' sums as combine_row<true> does and the block that finishes a row stores
 // its totals; a sparse generation adds only the signed changes of the vectors it drew
-// again (fdacc, before the row's count with a fence in between), and the block that
-// finishes the row adds them to the totals of the generation before.
+// again, each tile-row's change biased by its tile's item sums so that the packed fields
+// stay non-negative, and the block that finishes the row removes the biases (their total is
+// the sum of all items) and adds the change to the totals of the generation before.
 __device__ __forceinline__ void combine_row_keep(const GenParams &p, int32_t c, uint64_t sw, uint64_t sv,
                                                  int32_t t)
 {
@@ -663,23 +659,19 @@ __device__ __forceinline__ void combine_row_keep(const GenParams &p, int32_t c, 
 }
 
 __device__ __forceinline__ void combine_row_delta(const GenParams &p, int32_t c, int32_t dw, int32_t dv,
-                                                  int32_t t)
+                                                  uint32_t bw, uint32_t bv, int32_t t)
 {
-    if ((dw | dv) != 0) {
-        atomicAdd(p.fdacc + 2 * (size_t)c, (unsigned long long)(long long)dw);
-        atomicAdd(p.fdacc + 2 * (size_t)c + 1, (unsigned long long)(long long)dv);
-        __threadfence();
-    }
-    const unsigned long long old = atomicAdd(p.acc + c, 1ull << 52);
+    // dw + bw >= 0 (a tile-row's sum cannot drop by more than its tile's weights), and the
+    // ntile biased changes add up to at most 2 fsum_w < 2^26, so the fields never carry
+    const unsigned long long add = (1ull << 52) | ((unsigned long long)(uint32_t)(dv + (int32_t)bv) << 26) |
+                                   (unsigned long long)(uint32_t)(dw + (int32_t)bw);
+    const unsigned long long old = atomicAdd(p.acc + c, add);
     if ((int32_t)(old >> 52) == p.ntile - 1) {
-        __threadfence();
-        const long long w = (long long)__ldcg(p.fdacc + 2 * (size_t)c);
-        const long long v = (long long)__ldcg(p.fdacc + 2 * (size_t)c + 1);
+        const unsigned long long full = old + add;
         p.acc[c] = 0ull;
-        p.fdacc[2 * (size_t)c] = 0ull;
-        p.fdacc[2 * (size_t)c + 1] = 0ull;
         const unsigned long long prev = p.fprev[c];
-        const int64_t SW = (int64_t)(prev & 0x3ffffffull) + w, SV = (int64_t)((prev >> 26) & 0x3ffffffull) + v;
+        const int64_t SW = (int64_t)(prev & 0x3ffffffull) + (int64_t)(full & 0x3ffffffull) - p.fsum_w;
+        const int64_t SV = (int64_t)((prev >> 26) & 0x3ffffffull) + (int64_t)((full >> 26) & 0x3ffffffull) - p.fsum_v;
         p.fprev[c] = ((unsigned long long)SV << 26) | (unsigned long long)SW;
         finish_row(p, c, SW, SV, t);
     }
@@ -691,12 +683,14 @@ __device__ __forceinline__ void combine_row_delta(const GenParams &p, int32_t c,
 // (combine_row_delta).
 template <bool kNarrow, int kMode = 0>
 __device__ __forceinline__ void flush_segment(const GenParams &p, int32_t t, int ra, int seg_rows,
-                                              uint32_t *s_acc32, unsigned long long *s_acc64)
+                                              uint32_t *s_acc32, unsigned long long *s_acc64, int tile = 0)
 {
     __syncthreads();
+    const uint32_t bw = kMode == 2 ? __ldg(p.ftile + 2 * tile) : 0u;
+    const uint32_t bv = kMode == 2 ? __ldg(p.ftile + 2 * tile + 1) : 0u;
     for (int i = threadIdx.x; i < seg_rows; i += kThreads) {
         if (kMode == 2) {
-            combine_row_delta(p, ra + i, (int32_t)s_acc32[2 * i], (int32_t)s_acc32[2 * i + 1], t);
+            combine_row_delta(p, ra + i, (int32_t)s_acc32[2 * i], (int32_t)s_acc32[2 * i + 1], bw, bv, t);
             s_acc32[2 * i] = 0u;
             s_acc32[2 * i + 1] = 0u;
         } else if (kMode == 1) {
@@ -857,16 +851,6 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-// Appends one 16-bit F word to the 8-word group q (a shift register: the first word of the
-// group ends in the low half of q.x after eight appends).
-__device__ __forceinline__ void f_push(uint4 &q, uint32_t w)
-{
-    q.x = __funnelshift_r(q.x, q.y, 16);
-    q.y = __funnelshift_r(q.y, q.z, 16);
-    q.z = __funnelshift_r(q.z, q.w, 16);
-    q.w = (q.w >> 16) | (w << 16);
-}
-
 // One tile segment (rows ra .. ra + seg_rows - 1 of tile `tile`) of one generation. kS8:
 // the state is stored as bytes (copied 8 bytes per pass, widened to 16-bit lanes).
 // kSegDelta: rule R1 deltas formed once per segment into s_delta. The host selects it with
@@ -876,9 +860,9 @@ __device__ __forceinline__ void f_push(uint4 &q, uint32_t w)
 // kUnroll2: the pass loop unrolled twice (the batched kernel: c4 4,692 vs 4,593 solves/s;
 // no gain for the single-instance kernels, c2 9.90 vs 9.70 us per generation).
 //
-// kF: the instance keeps fixed-vector words (tiles of 256 vectors, one row per pass, segments
-// starting at a multiple of 8 rows): the pass's F is formed from its threshold words and
-// alleles, the words of 8 rows are stored together, and nfix counts the nonzero ones.
+// kF: the instance keeps fixed-vector words (tiles of 256 vectors, one row per pass): every
+// pass stores its F, formed from its threshold words and alleles, and nfix counts the
+// nonzero ones.
 // Both count in nskip the vectors that did not draw (the fixed-allele passes).
 // kSample (an instance whose words are not kept yet): nfix counts 16 for every vector the
 // fixed-allele test finds at the bounds (the test runs on about one pass in 16 while the
@@ -915,11 +899,8 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     uint8_t *xst_ptr = xptr;
     const uint8_t *xo_ptr = xoptr;
     int rr = b.r_sub;
-    // kF: words of the current group of 8 rows (oldest in the low half of fq.x) and where
-    // the group goes
-    uint4 fq = make_uint4(0u, 0u, 0u, 0u);
-    uint4 *fptr = nullptr;
-    if constexpr (kF) fptr = reinterpret_cast<uint4 *>(p.fword + f_index(p, tile, ra, b.v_in));
+    uint16_t *fptr = nullptr;                   // kF: this thread's F word of row ra + rr
+    if constexpr (kF) fptr = p.fword + (size_t)ra * p.fstride + (size_t)g.vec;
     auto issue = [&](uint32_t stage, bool v) {
         if constexpr (kS8)
             cp_async8(slots + (size_t)stage * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
@@ -954,16 +935,13 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
         else sv = slots[(size_t)slot * kThreads];
 
         const bool ok = rr < seg_rows;
-        uint32_t xbits, accn, zor = 1u, nsat = 0u;
+        uint32_t xbits, accn, zor = 1u;
         int64_t acw, acv;
         bool fixed;
         sv = qubit_pass<kNarrow, kRule, kCip, Keys, kSegDelta>(p, keys, g, sv, xo, ra_key + rr, t, thr_bytes,
                                                                fixed, countdown, xbits, accn, acw, acv,
-                                                               kF ? &zor : nullptr, kSample ? &nsat : nullptr);
-        if constexpr (kSample) *nfix += 16u * nsat;
-        if constexpr (kF || kSample) {
-            if (fixed && g.active && ok) ++*nskip;
-        }
+                                                               kF ? &zor : nullptr, kSample ? nfix : nullptr,
+                                                               (kF || kSample) ? nskip : nullptr);
         if (g.active && ok) {
             if (!fixed) {               // a fixed pass leaves the state as it is
                 if constexpr (kS8) *st_ptr = pack8(sv);
@@ -972,24 +950,17 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
             *xst_ptr = (uint8_t)xbits;
         }
         if constexpr (kF) {
-            const uint32_t fw = (g.active && ok && zor == 0u) ? (0x100u | xbits) : 0u;
-            *nfix += fw != 0u ? 1u : 0u;
-            f_push(fq, fw);
-            if ((rr & 7) == 7) {
-                if (g.active) *fptr = fq;
-                fptr += kThreads;       // the next group: 256 vectors x 8 words on
+            const uint32_t fw = zor == 0u ? (0x100u | xbits) : 0u;
+            if (g.active && ok) {
+                *fptr = (uint16_t)fw;
+                *nfix += fw != 0u ? 1u : 0u;
             }
+            fptr += p.fstride;
         }
         add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
         st_ptr += sstep;
         xst_ptr += xstep;
         rr += rpp;
-    }
-    if constexpr (kF) {                 // the last group of a tile's rows: pad with zeros
-        if ((seg_rows & 7) != 0) {
-            for (int k = seg_rows & 7; k < 8; ++k) f_push(fq, 0u);
-            if (g.active) *fptr = fq;
-        }
     }
     cp_async_wait<0>();
     flush_segment<kNarrow, (kF || kSample) ? 1 : 0>(p, t, ra, seg_rows, s_acc32, s_acc64);
@@ -1002,27 +973,28 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 // the previous elite's allele, so CIP leaves it, the observation cannot differ from the
 // side, the state needs no read or write, and the vector's alleles, hence its share of the
 // row sums, are those of the generation before. Which vectors are unstable follows the
-// columns (a gene where the elite left the consensus is unstable in nearly every row), so a
-// warp whose lane kept its column would still run the full pass for almost every row.
-// Instead each warp:
-//   1. reads F of 8 rows of its 32 vectors at a time (one 16-byte load a lane) and writes a
-//      stable vector's alleles (its side bits); nothing else: the row totals of the
-//      generation before (fprev) already hold its share;
-//   2. lists the unstable (row, vector) pairs in its slice of a shared-memory ring;
-//   3. streams the listed vectors' state, and the word of the previous alleles, through
-//      per-thread cp.async rings, 32 per step, and runs the full pass on each (the vector's
-//      items and CIP steps are read from the slots of the lane that owns its column): CIP,
-//      QIP, the state, the alleles and, when it changed, F; its sums enter the row as the
-//      signed change against the previous alleles (two shared atomics), which
-//      combine_row_delta adds to the row's totals.
+// columns (a gene where the elite left the consensus is unstable in nearly every row), so
+// the warps split the segment by rows, not columns: warp w takes rows w, w + 8, ... and lane
+// l the 8 consecutive vectors 8 l .. 8 l + 7 of the tile, so every warp meets the same
+// columns and the same share of the work. Per row a warp:
+//   1. reads F of its 256 vectors (one 16-byte load a lane) and writes the stable vectors'
+//      alleles (their sides; 8 bytes a lane when all 8 are stable); nothing else: the row's
+//      totals of the generation before (fprev) already hold their share;
+//   2. lists the row's unstable vectors in its slice of a shared-memory ring.
+// It then streams the listed vectors' state through the per-thread cp.async ring, 32 per
+// step, and runs the full pass on each (the
+// vector's items and CIP steps are read from the slots of the thread that set up its
+// column): CIP, QIP, the state, the alleles and F; its sums enter the row as the signed
+// change against the previous alleles (shared atomics on the row's accumulators, which only
+// this warp touches), and combine_row_delta adds them to the row's totals.
 // Listing runs ahead of the copies, so the ring's 7 rows of look-ahead become 7 steps of
 // 32 listed vectors. All sums are exact integers, so the results equal the dense form's.
-// Segments start at a multiple of 8 rows and hold at most 256 (the row fits 8 bits of a
-// list entry: row << 6 | lane << 1 | F nonzero).
+// Segments hold at most 256 rows (a list entry holds the row, the vector, its previous
+// alleles, loaded with F, and whether its F was nonzero, so that F is written only when it
+// changes).
 // ---------------------------------------------------------------------------------------
 constexpr int kListCap = 512;               // entries of a warp's list (a power of two)
-__shared__ uint16_t s_list[kThreads / 32][kListCap];
-__shared__ uint32_t s_xo[kRingStages][kThreads];   // per-thread ring of previous-allele words
+__shared__ uint32_t s_list[kThreads / 32][kListCap];
 
 // Packed narrow sums (sum v << 16 | sum w) of 8 genes from their alleles (bit i = gene i)
 // and the vector's item byte vectors.
@@ -1034,137 +1006,149 @@ __device__ __forceinline__ uint32_t narrow_sums_bits(uint32_t x8, uint4 ib)
     return sw | (sv << 16);
 }
 
-// 4-byte global->shared copy; src_bytes = 0 writes zeros (nothing is read).
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
-}
-
 __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int ra, int seg_rows, int32_t t,
                                                const uint8_t *x_prev, uint8_t *x_cur, const uint8_t *elite_row,
                                                const unsigned char *thr_bytes, uint4 *slots,
-                                               uint32_t *s_acc32, uint16_t *list, uint32_t &nfix,
+                                               uint32_t *s_acc32, uint32_t *list, uint32_t &nfix,
                                                uint32_t &nskip)
 {
     constexpr uint32_t kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int wbase = threadIdx.x & ~31;        // slot (and tile vector) of the warp's lane 0
-    const uint32_t lt = (1u << lane) - 1u;
+    const int warp = threadIdx.x >> 5;
     const uint32_t off_top = (uint32_t)(8 * p.K);
     const uint32_t k8 = off_top * 0x00010001u;
     const uint32_t ra_key = (uint32_t)(ra + p.row0);
-    const size_t svec = (size_t)p.svec, xstride = (size_t)p.xstride;
+    const size_t svec = (size_t)p.svec, xstride = (size_t)p.xstride, fstride = (size_t)p.fstride;
+    const uint32_t vt = (uint32_t)tile * kThreads;              // the tile's first vector
+    const uint32_t vb = vt + 8u * (uint32_t)lane;               // this lane's first vector
+    const int nact = max(0, min(8, (int)((int64_t)svec - (int64_t)vb)));   // of its 8, active
+    const int nrows = seg_rows > warp ? (seg_rows - warp + 7) >> 3 : 0;     // this warp's rows
 
-    // F of the next groups of 8 rows in flight (one group's work is too short to cover a
-    // load's latency); the first loads go out before the segment's other loads
-    const bool active = (uint32_t)tile * kThreads + threadIdx.x < (uint32_t)p.svec;
-    const uint4 *fsrc = reinterpret_cast<const uint4 *>(p.fword + f_index(p, tile, ra, threadIdx.x));
-    const int nchunk = (seg_rows + 7) >> 3;
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    auto fload = [&](int k) -> uint4 {
-        return (active && k < nchunk) ? __ldcg(fsrc + (size_t)k * kThreads) : zero4;
+    // F and the previous alleles of this warp's next rows in flight (one row's work is too
+    // short to cover a load's latency); the first loads go out before the segment's others
+    const uint4 *fsrc = reinterpret_cast<const uint4 *>(p.fword + (size_t)(ra + warp) * fstride + vb);
+    const uint2 *xsrc = reinterpret_cast<const uint2 *>(x_prev + (size_t)(ra + warp) * xstride + vb);
+    const size_t fstep = fstride, xstep = xstride;              // 8 rows in uint4 / uint2 units
+    auto fload = [&](int m) -> uint4 {
+        return (nact > 0 && m < nrows) ? __ldcg(fsrc + (size_t)m * fstep) : make_uint4(0u, 0u, 0u, 0u);
     };
-    uint4 fb0 = fload(0), fb1 = fload(1), fb2 = fload(2), fb3 = fload(3), fb4 = fload(4), fb5 = fload(5);
+    auto xload = [&](int m) -> uint2 {
+        return (nact > 0 && m < nrows) ? __ldcg(xsrc + (size_t)m * xstep) : make_uint2(0u, 0u);
+    };
+    uint4 fb0 = fload(0), fb1 = fload(1), fb2 = fload(2);
+    uint2 xb0 = xload(0), xb1 = xload(1), xb2 = xload(2);
 
     SegCtx g;
     seg_setup<true, true, true>(p, g, tile, threadIdx.x, kThreads, elite_row);
-    __syncwarp();                               // lanes read the other lanes' slots
-    const uint32_t vec0 = (uint32_t)tile * kThreads + (uint32_t)wbase;
-    uint4 *const sbase = p.state + (size_t)ra * svec + vec0;       // row ra, the warp's vector 0
-    uint8_t *const xbase = x_cur + (size_t)ra * xstride + vec0;
-    const uint8_t *const xobase = x_prev + (size_t)ra * xstride + vec0;
-    // a pair word's halves are 0 exactly where the row is stable: F = 0x100 | the elite's
-    // alleles of this vector
-    const uint32_t tgt = (0x100u | g.e8) * 0x00010001u;
-    int chunk = 0;
+    // this lane's 8 elite alleles (the sides of its stable vectors), and the pair words a
+    // stable F equals: 0x100 | allele, per half
+    uint2 e8s = make_uint2(0u, 0u);
+    if (nact > 0) e8s = __ldcg(reinterpret_cast<const uint2 *>(elite_row + vb));
+    const uint32_t ew[2] = {e8s.x, e8s.y};
+    uint32_t tgt[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t b0 = (ew[k >> 1] >> (16 * (k & 1))) & 0xffu, b1 = (ew[k >> 1] >> (16 * (k & 1) + 8)) & 0xffu;
+        tgt[k] = (0x100u | b0) | ((0x100u | b1) << 16);
+    }
+    const uint32_t vmask = (1u << nact) - 1u;
+    __syncthreads();                            // every thread reads the slots of the block's columns
+    uint4 *const sbase = p.state + (size_t)ra * svec + vt;      // row ra, the tile's vector 0
+    uint8_t *const xbase = x_cur + (size_t)ra * xstride + vt;
+
+    int m = 0;                                  // this warp's rows listed so far
     uint32_t head = 0;                          // entries listed so far (warp-uniform)
 
-    // Step 1 and 2 for the next 8 rows (bit j of the masks = row r0 + j).
+    // Steps 1 and 2 for this warp's next row (row = warp + 8 m of the segment). A list entry
+    // is row << 17 | (F was nonzero) << 16 | previous alleles << 8 | vector of the tile.
     auto produce = [&]() {
         const uint4 f = fb0;
         fb0 = fb1;
         fb1 = fb2;
-        fb2 = fb3;
-        fb3 = fb4;
-        fb4 = fb5;
-        fb5 = fload(chunk + 6);
-        const int r0 = chunk << 3;
-        ++chunk;
-        const uint32_t d[4] = {f.x ^ tgt, f.y ^ tgt, f.z ^ tgt, f.w ^ tgt};
-        const int nvalid = g.active ? min(8, seg_rows - r0) : 0;
-        uint32_t sm = 0u;
+        fb2 = fload(m + 3);
+        const uint2 xo = xb0;
+        xb0 = xb1;
+        xb1 = xb2;
+        xb2 = xload(m + 3);
+        const int row = warp + 8 * m;
+        ++m;
+        const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
+        uint32_t sm = 0u, nz = 0u;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t h = (j & 1) ? (d[j >> 1] >> 16) : (d[j >> 1] & 0xffffu);
-            sm |= (h == 0u && j < nvalid ? 1u : 0u) << j;
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t w = (k & 1) ? (fw[k >> 1] >> 16) : (fw[k >> 1] & 0xffffu);
+            const uint32_t h = (k & 1) ? ((fw[k >> 1] ^ tgt[k >> 1]) >> 16) : ((fw[k >> 1] ^ tgt[k >> 1]) & 0xffffu);
+            sm |= (h == 0u ? 1u : 0u) << k;
+            nz |= (w != 0u ? 1u : 0u) << k;
         }
-        const uint32_t vm = nvalid >= 8 ? 0xffu : ((1u << nvalid) - 1u);
-        const uint32_t um = vm & ~sm;
-        nfix += (uint32_t)__popc(sm);
-        nskip += (uint32_t)__popc(sm);
-        uint8_t *xp = xbase + (size_t)r0 * xstride + lane;
-        const uint8_t side = (uint8_t)g.e8;     // a stable vector's alleles
+        sm &= vmask;
+        const uint32_t um = vmask & ~sm;
+        const uint32_t ns = (uint32_t)__popc(sm);
+        nfix += ns;
+        nskip += ns;
+        uint8_t *xp = xbase + (size_t)row * xstride + 8u * (uint32_t)lane;
+        if (sm == 0xffu) {
+            *reinterpret_cast<uint2 *>(xp) = e8s;
+        } else if (sm != 0u) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if ((sm >> j) & 1u) *xp = side;
-            xp += xstride;
+            for (int k = 0; k < 8; ++k)
+                if ((sm >> k) & 1u) xp[k] = (uint8_t)(ew[k >> 2] >> (8 * (k & 3)));
         }
-        if (__any_sync(kFull, um != 0u)) {
-            const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
+        // the row's unstable vectors, in lane order (an exclusive prefix sum of the counts)
+        const uint32_t cnt = (uint32_t)__popc(um);
+        if (__any_sync(kFull, cnt != 0u)) {
+            uint32_t pre = cnt;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t w = (j & 1) ? (fw[j >> 1] >> 16) : (fw[j >> 1] & 0xffffu);
-                const bool u = (um >> j) & 1u;
-                const uint32_t bal = __ballot_sync(kFull, u);
-                if (u)
-                    list[(head + (uint32_t)__popc(bal & lt)) & (kListCap - 1)] =
-                        (uint16_t)(((uint32_t)(r0 + j) << 6) | ((uint32_t)lane << 1) | (w != 0u ? 1u : 0u));
-                head += (uint32_t)__popc(bal);
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, pre, o);
+                if (lane >= o) pre += y;
             }
+            const uint32_t total = __shfl_sync(kFull, pre, 31);
+            uint32_t pos = head + pre - cnt;
+            uint32_t bits = um;
+            while (bits != 0u) {
+                const int k = __ffs((int)bits) - 1;
+                bits &= bits - 1u;
+                const uint32_t xk = ((k < 4 ? xo.x : xo.y) >> (8 * (k & 3))) & 0xffu;
+                list[pos & (kListCap - 1)] = ((uint32_t)row << 17) | (((nz >> k) & 1u) << 16) | (xk << 8) |
+                                             (8u * (uint32_t)lane + (uint32_t)k);
+                ++pos;
+            }
+            head += total;
         }
     };
 
-    // Copies of step j (entries 32 j .. 32 j + 31) into ring slot j % 8: the state and the
-    // aligned word holding the previous alleles; the step must be listed in full (or the
-    // listing finished).
+    // Copies of step j (entries 32 j .. 32 j + 31) into ring slot j % 8; the step must be
+    // listed in full (or the listing finished).
     auto issue = [&](uint32_t j) {
         const uint32_t i = j * 32u + (uint32_t)lane;
         const bool has = i < head;
         const void *src = p.state;
-        const void *xsrc = p.state;
         if (has) {
             const uint32_t e = list[i & (kListCap - 1)];
-            const size_t row = e >> 6, col = (e >> 1) & 31u;
-            src = sbase + row * svec + col;
-            xsrc = reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(xobase + row * xstride + col) &
-                                                  ~(uintptr_t)3);
+            src = sbase + (size_t)(e >> 17) * svec + (e & 255u);
         }
-        const uint32_t slot = j & (kRingStages - 1);
-        cp_async16(slots + (size_t)slot * kThreads, src, has ? 16u : 0u);
-        cp_async4(&s_xo[slot][threadIdx.x], xsrc, has ? 4u : 0u);
+        cp_async16(slots + (size_t)(j & (kRingStages - 1)) * kThreads, src, has ? 16u : 0u);
         cp_async_commit();
     };
 
-    // Step 3 for step j.
+    // Step 3 for step j; each vector's change goes to its row with two shared atomics.
     auto compute = [&](uint32_t j) {
         const uint32_t i = j * 32u + (uint32_t)lane;
         if (i >= head) return;
         const uint32_t e = list[i & (kListCap - 1)];
-        const uint32_t row = e >> 6;
-        const uint32_t col = (e >> 1) & 31u;
-        const int cv = wbase + (int)col;
-        const uint32_t ctr = 2u * (vec0 + col);
-        const uint32_t slot = j & (kRingStages - 1);
-        uint4 s = slots[(size_t)slot * kThreads];
-        const uint32_t xo = (s_xo[slot][threadIdx.x] >> (8u * ((vec0 + col) & 3u))) & 0xffu;
-        const uint4 d = s_delta[cv];
+        const uint32_t row = e >> 17;
+        const uint32_t col = e & 255u;
+        const uint32_t xo = (e >> 8) & 0xffu;
+        const uint32_t vec = vt + col;
+        uint4 s = slots[(size_t)(j & (kRingStages - 1)) * kThreads];
+        const uint4 d = s_delta[col];
         s.x = rotate_pair_signed(s.x, d.x, k8);
         s.y = rotate_pair_signed(s.y, d.y, k8);
         s.z = rotate_pair_signed(s.z, d.z, k8);
         s.w = rotate_pair_signed(s.w, d.w, k8);
-        const Draw4 r0 = philox4x32_10_rk(ctr, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
-        const Draw4 r1 = philox4x32_10_rk(ctr + 1u, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r0 = philox4x32_10_rk(2u * vec, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
+        const Draw4 r1 = philox4x32_10_rk(2u * vec + 1u, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
         const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
         const uint32_t sp[4] = {s.x, s.y, s.z, s.w};
         uint32_t xbits = 0u, z = 0u;
@@ -1176,7 +1160,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
             if ((u[k] < thr) || (off == off_top)) xbits |= 1u << k;
         }
         if (xbits != xo) {
-            const uint4 ib = s_item_bytes[cv];
+            const uint4 ib = s_item_bytes[col];
             const uint32_t a = narrow_sums_bits(xbits, ib), b = narrow_sums_bits(xo, ib);
             atomicAdd(s_acc32 + 2 * row, (a & 0xffffu) - (b & 0xffffu));
             atomicAdd(s_acc32 + 2 * row + 1, (a >> 16) - (b >> 16));
@@ -1184,7 +1168,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         sbase[(size_t)row * svec + col] = s;
         xbase[(size_t)row * xstride + col] = (uint8_t)xbits;
         const uint32_t fwn = z == 0u ? (0x100u | xbits) : 0u;
-        if (fwn != 0u || (e & 1u)) p.fword[f_index(p, tile, ra + (int)row, cv)] = (uint16_t)fwn;
+        if (fwn != 0u || ((e >> 16) & 1u)) p.fword[((size_t)ra + row) * fstride + vec] = (uint16_t)fwn;
         nfix += fwn != 0u ? 1u : 0u;
     };
 
@@ -1192,16 +1176,16 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     // the copies of jc + 7 are issued, and a burst stops once they are, so the live entries
     // (from step jc on) stay below 32 (jc + 8) + 256 <= 32 jc + 512, the list's size. The
     // loop between bursts issues and computes without listing.
-    while (chunk < nchunk && head < 8u * 32u) produce();
+    while (m < nrows && head < 8u * 32u) produce();
     __syncwarp();
 #pragma unroll 1
     for (uint32_t j = 0; j < kRingStages - 1; ++j) issue(j);
     uint32_t jc = 0;
 #pragma unroll 1
     for (;;) {
-        while (chunk < nchunk && head < (jc + 8u) * 32u) produce();
+        while (m < nrows && head < (jc + 8u) * 32u) produce();
         __syncwarp();
-        const bool done = chunk >= nchunk;
+        const bool done = m >= nrows;
         const uint32_t avail = done ? (head + 31u) / 32u : head / 32u;
         if (jc >= avail) break;
         const uint32_t jend = done ? avail : avail - (kRingStages - 1);
@@ -1213,7 +1197,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         }
     }
     cp_async_wait<0>();
-    flush_segment<true, 2>(p, t, ra, seg_rows, s_acc32, nullptr);
+    flush_segment<true, 2>(p, t, ra, seg_rows, s_acc32, nullptr, tile);
 }
 
 template <bool kNarrow>
@@ -2756,11 +2740,10 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
     }
     if (p.fword) {   // no qubit at a bound: every fixed-vector word 0
         uint4 *f = reinterpret_cast<uint4 *>(p.fword);
-        const size_t n = (size_t)p.ntile * (size_t)p.np8 * kThreads;
+        const size_t n = (size_t)p.np * (size_t)p.fstride / 8;
         for (size_t i = i0; i < n; i += stride) f[i] = make_uint4(0u, 0u, 0u, 0u);
         for (size_t i = i0; i < (size_t)p.np; i += stride) {
             p.fprev[i] = 0ull;
-            p.fdacc[2 * i] = p.fdacc[2 * i + 1] = 0ull;
         }
         if (i0 == 0)
             for (int i = 0; i < 7; ++i) p.fcnt[i] = 0ull;
