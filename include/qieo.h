@@ -242,9 +242,10 @@ typedef struct {
                                 that the previous elite turns away from their bound, run CIP,
                                 QIP and Evaluation in full; the rest contribute their sides.
                                 Kept by the one-launch-per-generation runs with the packed
-                                elite key, rule R1, items in [0, 255], 16-bit state and the
-                                default tile, unless QIEO_FLAG_NO_FIXED_WORDS,
-                                QIEO_FLAG_SIXTEEN or QIEO_FLAG_CONVERGE */
+                                elite key, items in [0, 255] whose weights and values each sum
+                                below 2^25, 16-bit state and the default tile, unless
+                                QIEO_FLAG_NO_FIXED_WORDS, QIEO_FLAG_SIXTEEN or
+                                QIEO_FLAG_CONVERGE */
 } qieo_launch_shape;
 
 qieo_status qieo_get_launch_shape(qieo_instance *inst, qieo_launch_shape *shape);

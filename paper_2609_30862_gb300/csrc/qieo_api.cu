@@ -230,8 +230,10 @@ struct PickRun {
 // per segment.
 PickGen<true, 0, true>::type gen_fn(const qieo_instance *q, bool ring, bool seg_delta)
 {
+    if (q->gp.fword && ring)   // fixed-vector words (R2 forms its rotation per vector)
+        return q->rule ? &qieo::generation_kernel<true, 1, true, false, false, true>
+                       : &qieo::generation_kernel<true, 0, true, false, true, true>;
     if (seg_delta && ring && q->rule == 0) {
-        if (q->gp.fword) return &qieo::generation_kernel<true, 0, true, false, true, true>;
         if (q->state8) return &qieo::generation_kernel<true, 0, true, true, true>;
         return q->narrow ? &qieo::generation_kernel<true, 0, true, false, true>
                          : &qieo::generation_kernel<false, 0, true, false, true>;
@@ -435,7 +437,7 @@ bool wants_fword(const qieo_instance *q, bool use_ring)
 {
     return !(q->flags & (QIEO_FLAG_NO_FIXED_WORDS | QIEO_FLAG_SIXTEEN | QIEO_FLAG_CONVERGE | QIEO_FLAG_UNFUSED |
                          QIEO_FLAG_COOPERATIVE)) &&
-           use_ring && q->narrow && !q->state8 && q->rule == 0 && q->key_ok && !q->host_de && q->lanes == 32 &&
+           use_ring && q->narrow && !q->state8 && q->key_ok && !q->host_de && q->lanes == 32 &&
            q->sum_w < ((int64_t)1 << 25) && q->sum_v < ((int64_t)1 << 25) && !q->tile_sums.empty() &&
            q->warps == 8 && q->owns_block && !q->row_block && !use_resident(q) && !use_cooperative(q);
 }
@@ -526,9 +528,10 @@ qieo_status configure(qieo_instance *q)
     qieo_status ost = resident_blocks(q->device, gen_kernel_of(q, use_ring, false), smem0, &bps_gen);
     if (ost == QIEO_OK) ost = resident_blocks(q->device, gen_kernel_of(q, use_ring, true), smem0, &bps_sd);
     if (ost == QIEO_OK) ost = resident_blocks(q->device, run_kernel_of(q, use_ring), smem0, &bps_run);
-    if (ost == QIEO_OK && use_ring && q->narrow && q->rule == 0 && !q->state8)
+    if (ost == QIEO_OK && use_ring && q->narrow && !q->state8)
         ost = resident_blocks(q->device,
-                              reinterpret_cast<const void *>(&qieo::generation_kernel<true, 0, true, false, true, true>),
+                              q->rule ? reinterpret_cast<const void *>(&qieo::generation_kernel<true, 1, true, false, false, true>)
+                                      : reinterpret_cast<const void *>(&qieo::generation_kernel<true, 0, true, false, true, true>),
                               ring + (size_t)kFwordMaxSegRows * row_bytes, &bps_f);
     if (ost != QIEO_OK) return ost;
     const int bps = std::min(std::min(kBlocksPerSm, bps_f), std::min(bps_gen, std::min(bps_sd, bps_run)));

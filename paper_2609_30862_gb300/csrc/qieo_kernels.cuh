@@ -967,8 +967,8 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 }
 
 // ---------------------------------------------------------------------------------------
-// Sparse form of a tile segment (instances that keep F: rule R1, packed sums, 16-bit state,
-// tiles of 256 vectors; generations that rotate, i.e. not a run's first). Once most of the
+// Sparse form of a tile segment (instances that keep F: packed sums, 16-bit state, tiles of
+// 256 vectors; generations that rotate, i.e. not a run's first). Once most of the
 // population has collapsed, most vectors are stable: every qubit at a bound on the side of
 // the previous elite's allele, so CIP leaves it, the observation cannot differ from the
 // side, the state needs no read or write, and the vector's alleles, hence its share of the
@@ -995,6 +995,7 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 // ---------------------------------------------------------------------------------------
 constexpr int kListCap = 512;               // entries of a warp's list (a power of two)
 __shared__ uint32_t s_list[kThreads / 32][kListCap];
+__shared__ uint8_t s_e8[kThreads];          // rule R2: the previous elite's alleles of the tile's vectors
 
 // Packed narrow sums (sum v << 16 | sum w) of 8 genes from their alleles (bit i = gene i)
 // and the vector's item byte vectors.
@@ -1006,6 +1007,7 @@ __device__ __forceinline__ uint32_t narrow_sums_bits(uint32_t x8, uint4 ib)
     return sw | (sv << 16);
 }
 
+template <int kRule>
 __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int ra, int seg_rows, int32_t t,
                                                const uint8_t *x_prev, uint8_t *x_cur, const uint8_t *elite_row,
                                                const unsigned char *thr_bytes, uint4 *slots,
@@ -1039,7 +1041,8 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     uint2 xb0 = xload(0), xb1 = xload(1), xb2 = xload(2);
 
     SegCtx g;
-    seg_setup<true, true, true>(p, g, tile, threadIdx.x, kThreads, elite_row);
+    seg_setup<true, true, kRule == 0>(p, g, tile, threadIdx.x, kThreads, elite_row);
+    if (kRule == 1) s_e8[threadIdx.x] = (uint8_t)g.e8;
     // this lane's 8 elite alleles (the sides of its stable vectors), and the pair words a
     // stable F equals: 0x100 | allele, per half
     uint2 e8s = make_uint2(0u, 0u);
@@ -1142,11 +1145,16 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         const uint32_t xo = (e >> 8) & 0xffu;
         const uint32_t vec = vt + col;
         uint4 s = slots[(size_t)(j & (kRingStages - 1)) * kThreads];
-        const uint4 d = s_delta[col];
-        s.x = rotate_pair_signed(s.x, d.x, k8);
-        s.y = rotate_pair_signed(s.y, d.y, k8);
-        s.z = rotate_pair_signed(s.z, d.z, k8);
-        s.w = rotate_pair_signed(s.w, d.w, k8);
+        if (kRule == 0) {                       // R1: every qubit toward the elite's allele
+            const uint4 d = s_delta[col];
+            s.x = rotate_pair_signed(s.x, d.x, k8);
+            s.y = rotate_pair_signed(s.y, d.y, k8);
+            s.z = rotate_pair_signed(s.z, d.z, k8);
+            s.w = rotate_pair_signed(s.w, d.w, k8);
+        } else {                                // R2: the qubits whose allele differed
+            const uint32_t e8c = s_e8[col];
+            s = rotate_vec(s, e8c, e8c ^ xo, k8);
+        }
         const Draw4 r0 = philox4x32_10_rk(2u * vec, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
         const Draw4 r1 = philox4x32_10_rk(2u * vec + 1u, ra_key + row, (uint32_t)t, 0u, p.rk0, p.rk1);
         const uint32_t u[8] = {r0.a, r0.b, r0.c, r0.d, r1.a, r1.b, r1.c, r1.d};
@@ -1289,8 +1297,8 @@ __device__ __forceinline__ void generation_body_queue(const GenParams &p, const 
         const int4 sg = __ldg(p.segq + qi);
         if constexpr (kF) {
             if (sparse)
-                sparse_segment(p, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots, s_acc32,
-                               s_list[threadIdx.x >> 5], nfix, nskip);
+                sparse_segment<kRule>(p, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots,
+                                      s_acc32, s_list[threadIdx.x >> 5], nfix, nskip);
             else if (keep)
                 ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta, false, true>(
                     p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots, s_acc32,
@@ -2006,8 +2014,9 @@ __global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) resident_run_kernel
 // 76 for the narrow ring form, which measured c3 348 vs 361 us per generation against the
 // 64 that four blocks would allow.
 //
-// kF: the variant for instances that keep F (rule R1, packed sums, 16-bit state, the ring,
-// per-segment deltas, deferred close with a segment queue); the host runs it only so.
+// kF: the variant for instances that keep F (packed sums, 16-bit state, the ring, deferred
+// close with a segment queue; rule R1 with per-segment deltas, or R2); the host runs it only
+// so.
 template <bool kNarrow, int kRule, bool kRing, bool kS8 = false, bool kSegDelta = false, bool kF = false>
 __global__ void __launch_bounds__(kThreads, kNarrow ? 3 : 2) generation_kernel(const GenParams p)
 {

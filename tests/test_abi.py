@@ -89,7 +89,8 @@ def test_defaults_and_errors_without_gpu(lib):
             Q.qieo_measure_integer_ceiling(reps)
         assert e.value.status == Q.QIEO_ERR_INVALID and "reps" in str(e.value)
     for call in (lambda: Q.qieo_get_generation_times(None, 4), lambda: Q.qieo_rows_observe(None, 0),
-                 lambda: Q.qieo_rows_rotate(None, [0, 1]), lambda: Q.qieo_get_allele_row(None, 0, 4)):
+                 lambda: Q.qieo_rows_rotate(None, [0, 1]), lambda: Q.qieo_get_allele_row(None, 0, 4),
+                 lambda: Q.qieo_get_drawn_vectors(None, 0, 4)):
         with pytest.raises(Q.QieoError) as e:
             call()
         assert e.value.status == Q.QIEO_ERR_INVALID

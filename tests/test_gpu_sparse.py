@@ -45,14 +45,14 @@ def check(I, st, gens):
     assert np.array_equal(bits, st.best_x)
 
 
-def run_both(prob, np_, chunks, seed, flags, shape=None, k0=None, fixed_words=1):
+def run_both(prob, np_, chunks, seed, flags, shape=None, k0=None, fixed_words=1, rule=0):
     from oracle import oracle as O
     gens = int(sum(chunks))
     st = O.State(np_, prob.ng)
     if k0 is not None:
         st.k[:] = k0
-    O.run(prob, np_, gens, seed=seed, state=st)
-    with Q.Instance(prob, np_, seed=seed, flags=flags) as I:
+    O.run(prob, np_, gens, seed=seed, state=st, rule=rule)
+    with Q.Instance(prob, np_, seed=seed, flags=flags, rule=rule) as I:
         if shape is not None:
             I.set_shape(*shape)
         assert I.shape().fixed_words == fixed_words
@@ -63,14 +63,16 @@ def run_both(prob, np_, chunks, seed, flags, shape=None, k0=None, fixed_words=1)
         check(I, st, gens)
 
 
+@pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("flags", [SPARSE, PG])
 @pytest.mark.parametrize("ng,np_,seed", [(4696, 70, 61), (2100, 19, 62), (1500, 8, 63)])
-def test_natural_collapse(flags, ng, np_, seed):
+def test_natural_collapse(flags, ng, np_, seed, rule):
     """Spread generations, the collapse, and the saturated tail, in runs of several lengths:
     three tiles with a ragged last one (4,696 genes), a ragged last group of 8 rows (70 and
     19 rows), one tile and one row group (1,500 x 8). SPARSE_ALWAYS takes the sparse form
-    from the first generation, the default once a quarter of the vectors is fixed."""
-    run_both(W.knapsack(ng, seed), np_, [1, 60, 139, 50], seed, flags)
+    from the first generation, the default once half of the vectors is fixed; rules R1 and
+    R2 (which rotates only the qubits whose allele differed from the elite's)."""
+    run_both(W.knapsack(ng, seed), np_, [1, 60, 139, 50], seed, flags, rule=rule)
 
 
 @pytest.mark.parametrize("flags", [SPARSE, PG])
@@ -81,13 +83,14 @@ def test_segment_lengths(flags, shape):
     run_both(W.knapsack(2100, 64), 600, [30, 90], 64, flags, shape=shape)
 
 
+@pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("flags", [SPARSE, PG])
-def test_from_saturated_states(flags):
+def test_from_saturated_states(flags, rule):
     """Every qubit at a bound from the start: rows share one pattern except 9 with 40 genes
     flipped, so the elite's column disagreements make whole columns unstable. The state is
     placed through a checkpoint, which clears the words."""
-    k0 = saturated_start(3001, 83, 71, n_odd=9, flips=40)
-    run_both(W.knapsack(3001, 71), 83, [1, 2, 37, 25], 71, flags, k0=k0)
+    k0 = saturated_start(3001, 83, 71 + rule, n_odd=9, flips=40)
+    run_both(W.knapsack(3001, 71), 83, [1, 2, 37, 25], 71, flags, k0=k0, rule=rule)
 
 
 def test_fixed_words_kept_where_the_form_allows():
@@ -95,7 +98,7 @@ def test_fixed_words_kept_where_the_form_allows():
     cases = [
         (PG, 0, 1),
         (PG | Q.QIEO_FLAG_NO_FIXED_WORDS, 0, 0),
-        (PG, 1, 0),                                   # rule R2
+        (PG, 1, 1),                                   # rule R2
         (PG | Q.QIEO_FLAG_STATE_I8, 0, 0),
         (PG | Q.QIEO_FLAG_FORCE_WIDE, 0, 0),
         (PG | Q.QIEO_FLAG_SIXTEEN, 0, 0),
@@ -193,3 +196,39 @@ def test_drawn_vectors_equal_the_oracle_count_of_unstable_vectors():
         I.run(2)
         with pytest.raises(Q.QieoError):
             I.drawn_vectors(0, 2)
+
+
+@pytest.mark.parametrize("D", [4, 12, 40, 1000])
+def test_other_rotation_steps(D):
+    """Other rotation steps π/D change K, the bound offsets 0 and 8K and the threshold table
+    whose zero low words mark a fixed vector; D = 4 (K = 1) saturates after one step."""
+    from oracle import oracle as O
+    prob, np_, seed = W.knapsack(2600, 100 + D), 40, 100 + D
+    gens = 140 if D < 1000 else 60
+    st = O.run(prob, np_, gens, seed=seed, D=D)
+    for flags in (SPARSE, PG):
+        with Q.Instance(prob, np_, seed=seed, D=D, flags=flags) as I:
+            assert I.shape().fixed_words == 1
+            I.run(gens // 3)
+            I.run(gens - gens // 3)
+            check(I, st, gens)
+
+
+def test_item_sums_at_the_form_limit():
+    """The form needs the sums of all weights and of all values below 2^25 (the biased row
+    changes of a sparse generation stay below 2^26): 131,584 weights of 255 (512 below 2^25)
+    keep the words and the run equals the oracle; 131,600 (at or above 2^25) do not."""
+    from oracle import oracle as O
+    limit = 1 << 25
+    ng = 131_584
+    below = W.custom_problem(np.full(ng, 255, dtype=np.int32), np.full(ng, 7, dtype=np.int32), 255 * ng // 2)
+    assert 255 * ng < limit
+    with Q.Instance(below, 24, seed=5, flags=SPARSE) as I:
+        assert I.shape().fixed_words == 1
+        I.run(80)
+        check(I, O.run(below, 24, 80, seed=5, kind="omp"), 80)
+    ng = 131_600
+    at = W.custom_problem(np.full(ng, 255, dtype=np.int32), np.full(ng, 7, dtype=np.int32), 255 * ng // 2)
+    assert 255 * ng >= limit
+    with Q.Instance(at, 4, seed=5, flags=PG) as I:
+        assert I.shape().fixed_words == 0
