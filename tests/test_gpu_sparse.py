@@ -109,6 +109,8 @@ def test_fixed_words_kept_where_the_form_allows():
     for flags, rule, want in cases:
         with Q.Instance(prob, 64, rule=rule, flags=flags) as I:
             assert I.shape().fixed_words == want, (flags, rule)
+    with Q.Instance(prob, 64, flags=PG, row0=0) as I:      # a row block of a sharded population
+        assert I.shape().fixed_words == 0
     with Q.Instance(prob, 64, flags=PG) as I:
         I.set_shape(32, 4, 0)                         # another tile: no words
         assert I.shape().fixed_words == 0
