@@ -190,6 +190,7 @@ struct qieo_instance {
     size_t fword_bytes = 0;
     size_t fword_state_bytes = 0;      // the counters, words and row totals (cleared together);
                                        // the tile sums after them stay
+    bool fword_dirty = false;          // a run since the last clear may have written words
     std::vector<uint32_t> tile_sums;   // per tile of 256 vectors: sum of weights, of values
 };
 
@@ -468,6 +469,7 @@ qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
             }
             q->fword_bytes = bytes;
             q->fword_state_bytes = 256 + words + prev;
+            q->fword_dirty = false;
             CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, bytes, q->stream));
             if ((int)q->tile_sums.size() != 2 * ntile) return fail(QIEO_ERR_INVALID, "internal: tile sums");
             CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(q->fword_mem) + 256 + words + prev, q->tile_sums.data(),
@@ -491,10 +493,13 @@ qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
 }
 
 // Every fixed-vector word to 0 (after the state changed outside the kernels that keep them),
-// with the counters and row totals; the tile sums stay.
+// with the counters and row totals; the tile sums stay. Nothing to do when no run of the
+// kernel that keeps them has happened since the words were last cleared (a batch member that
+// only runs in batches).
 qieo_status clear_fword(qieo_instance *q, cudaStream_t s)
 {
-    if (q->fword_state_bytes) CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, q->fword_state_bytes, s));
+    if (q->fword_state_bytes && q->fword_dirty) CUDA_TRY(cudaMemsetAsync(q->fword_mem, 0, q->fword_state_bytes, s));
+    q->fword_dirty = false;
     return QIEO_OK;
 }
 
@@ -934,6 +939,7 @@ qieo_status run_device(qieo_instance *q, int32_t G)
         if (st != QIEO_OK) return st;
     }
     if (use_resident(q) || use_cooperative(q)) return run_cooperative(q, G);
+    if (q->gp.fword) q->fword_dirty = true;
     const bool timing = (q->flags & QIEO_FLAG_TIME_KERNELS) != 0;
     const bool first_time = q->run_lengths_seen[G]++ == 0;
     if ((q->flags & (QIEO_FLAG_NO_GRAPH | QIEO_FLAG_TIME_GENERATIONS)) || (first_time && !q->graphs.count(G))) {
@@ -1431,6 +1437,7 @@ qieo_status qieo_reset(qieo_instance *q)
     CUDA_TRY(cudaGetLastError());
     if (q->hist_d)
         CUDA_TRY(cudaMemsetAsync(q->hist_d, 0, (size_t)q->hist_cap * sizeof(unsigned long long), q->stream));
+    q->fword_dirty = false;   // init_kernel clears the words with the state
     q->t = 0;
     q->rows_t = -1;
     if (q->flags & QIEO_FLAG_SYNC_RUN) return wait_stream(q->stream);
