@@ -76,3 +76,34 @@ def test_oracle_scan_on_host_cores():
     assert got[0] == ("serial", 1)
     assert got[1:] == [("omp", n) for n in sorted({1, 8, 16, cores}) if n <= cores]
     assert all(x["gene_updates_per_s"] > 0 and x["generations"] >= 1 for x in d["runs"])
+
+
+def test_work_adjusted_roofline_arithmetic():
+    """The work-adjusted bound of a generation is the slower of its draws at the integer
+    ceiling and its bytes at HBM: 32 B for each vector that drew, 3 B for each that did not."""
+    sys.path.insert(0, ROOT)
+    import bench
+    nvec, hbm, intc = 1000, 1.0, 8.0e6             # GB/s (1e9 B/s) and gene-updates/s
+    # all drew: draws 8000 / 8e6 = 1 ms; bytes 32e3 / 1e9 = 32 us -> 1 ms (integer-bound)
+    # none drew: bytes 3e3 / 1e9 = 3 us -> 3 us (HBM-bound)
+    w = bench.work_adjusted([2.0, 0.006], [1000, 0], nvec, hbm, intc)
+    assert abs(w["bound_us"] - (1000.0 + 3.0)) < 1e-6
+    assert abs(w["measured_us"] - 2006.0) < 1e-6
+    assert abs(w["frac"] - 1003.0 / 2006.0) < 1e-12
+    assert abs(w["drawn_fraction"] - 0.5) < 1e-12
+
+
+def test_profile_traffic_needs_the_current_kernel_source(tmp_path, monkeypatch):
+    """A committed ncu summary's traffic is used only when its source hash matches."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_c9.md").write_text("kernel_source_sha256: %s\ntraffic_bytes_per_generation: 123\n"
+                                  % bench.kernel_source_hash())
+    (prof / "old_c9.md").write_text("kernel_source_sha256: 0000000000000000\ntraffic_bytes_per_generation: 5\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: (prof / "k_c9.md").read_text().split()[1])
+    assert bench.profile_traffic("k", "c9") == 123.0
+    assert bench.profile_traffic("old", "c9") is None
+    assert bench.profile_traffic("missing", "c9") is None
