@@ -112,8 +112,9 @@ typedef struct {
                                           pass over all qubits (see qieo_launch_shape.
                                           fixed_words) */
 #define QIEO_FLAG_SPARSE_ALWAYS 0x4000 /* with fixed-vector words, take the sparse form in
-                                          every generation, however few vectors are fixed
-                                          (identical results; for tests and measurement) */
+                                          every generation that rotates (all but a run's
+                                          first), however few vectors are fixed (identical
+                                          results; for tests and measurement) */
 #define QIEO_FLAG_TIME_GENERATIONS 0x400 /* time every generation of a run for
                                             qieo_get_generation_times. In the resident form
                                             (qieo_launch_shape.resident) one thread reads the
@@ -202,7 +203,8 @@ qieo_status qieo_get_elite_history(qieo_instance *inst, int32_t first, int32_t n
 
 /* Work of generations first .. first+n-1 (all < t) of an instance that keeps fixed-vector
  * words (qieo_launch_shape.fixed_words): out[i] = the 8-gene vectors of generation first+i
- * that drew (ran QIP with a Philox draw per qubit, after their CIP); the rest were fixed, so
+ * that drew (ran QIP, Sec. III-B, with a Philox draw per qubit, after their CIP); the rest
+ * were fixed (every qubit at theta = 0 or pi/2, |alpha|^2 or |beta|^2 = 1, Sec. I), so
  * their alleles were known without a draw (the fixed-allele pass of the dense form, the
  * stable vectors of the sparse form). np * ceil(ng / 8) means every vector drew; generations
  * run in a batch, or restored by a checkpoint load, report that value (they are not counted).
