@@ -448,9 +448,9 @@ bool wants_fword(const qieo_instance *q, bool use_ring)
 qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
 {
     qieo::GenParams &g = q->gp;
-    // [counters: 256 B][the words: np x fstride][row totals: np x 8 B][tile item sums]
+    // [counters: 256 B][the words: np x fstride bits][row totals: np x 8 B][tile item sums]
     const int32_t fstride = ntile * qieo::kThreads;
-    const size_t words = align_up((size_t)q->np * (size_t)fstride * sizeof(uint16_t), 256);
+    const size_t words = align_up((size_t)q->np * (size_t)(fstride / 32) * sizeof(uint32_t), 256);
     const size_t prev = align_up((size_t)q->np * 8, 256);
     const size_t bytes = want ? 256 + words + prev + (size_t)ntile * 8 : 0;
     if (bytes != q->fword_bytes) {
@@ -478,7 +478,7 @@ qieo_status configure_fword(qieo_instance *q, bool want, int ntile)
     }
     char *base = static_cast<char *>(q->fword_mem);
     g.fcnt = bytes ? reinterpret_cast<unsigned long long *>(base) : nullptr;
-    g.fword = bytes ? reinterpret_cast<uint16_t *>(base + 256) : nullptr;
+    g.fword = bytes ? reinterpret_cast<uint32_t *>(base + 256) : nullptr;
     g.fprev = bytes ? reinterpret_cast<unsigned long long *>(base + 256 + words) : nullptr;
     g.ftile = bytes ? reinterpret_cast<const uint32_t *>(base + 256 + words + prev) : nullptr;
     g.fsum_w = q->sum_w;

@@ -152,8 +152,9 @@ struct GenParams {
                                   // block of a population sharded by rows; 0 otherwise)
     unsigned long long *gen_ns;   // resident form: device clock (ns) at the start of each
                                   // generation of the run and at its end, or NULL
-    uint16_t *fword;              // [np][fstride] fixed-vector words F of the stored state
-                                  // (see allele_bytes), or NULL when the instance keeps none
+    uint32_t *fword;              // [np][fstride / 32] fixed-vector words of the stored state
+                                  // (one bit per vector, see below), or NULL when the instance
+                                  // keeps none
     unsigned long long *fcnt;     // [7] vectors whose F is nonzero after generation t, in
                                   // slot t % 3 (an estimate while the words are not kept);
                                   // [3]: 1 once the words are kept; [4 + t % 3]: vectors
@@ -166,7 +167,7 @@ struct GenParams {
     const uint32_t *ftile;        // [2 ntile] sums of the weights and of the values of each
                                   // tile's genes (the bias of a sparse generation's changes)
     int64_t fsum_w, fsum_v;       // sums of all weights and of all values
-    int32_t fstride;              // words of a row of F: ntile * 256
+    int32_t fstride;              // vectors of a row of F: ntile * 256 (fstride / 32 words)
     unsigned long long sparse_min;   // a generation takes the sparse form when at least
                                      // this many vectors were fixed after the one before
     unsigned long long f_on_min;     // the words are kept from the first generation after
@@ -503,11 +504,13 @@ __device__ __forceinline__ uint32_t narrow_sums(uint32_t xa, uint32_t xb)
     return sw | (sv << 16);
 }
 
-// Fixed-vector words. F of a vector of the stored state is 0x100 | (its 8 alleles, bit i =
-// gene i) when all eight qubits sit at theta = 0 or pi/2 (n = 0 or 2K: each allele is then
-// the side of its bound whatever the draw), and 0 otherwise; 0 is also always a safe value
-// ("not known to be fixed"), so F may be cleared at any time. Instances that keep F store
-// it row-major, fstride (= ntile * 256) words a row.
+// Fixed-vector words. F of a vector of the stored state is 1 when all eight of its qubits
+// sit at theta = 0 or pi/2 (n = 0 or 2K: each allele is then the side of its bound whatever
+// the draw), else 0; 0 is also always a safe value ("not known to be fixed"), so F may be
+// cleared at any time. Instances that keep F store it row-major, one bit per vector, 32
+// vectors to a 32-bit word, fstride / 32 words a row. A fixed vector's sides are its alleles
+// of the generation that observed that state, so F and the previous allele plane together
+// say whether a vector is stable.
 
 // Alleles of four genes (bit i = gene i of the nibble) -> bytes (x0, x2, x1, x3), the order
 // narrow_sums takes: the multiplier's terms 1, 2^15, 2^6, 2^21 move bit 0 to bit 0, bit 1 to
@@ -861,8 +864,8 @@ __device__ __forceinline__ void cp_async_wait()
 // no gain for the single-instance kernels, c2 9.90 vs 9.70 us per generation).
 //
 // kF: the instance keeps fixed-vector words (tiles of 256 vectors, one row per pass): every
-// pass stores its F, formed from its threshold words and alleles, and nfix counts the
-// nonzero ones.
+// pass forms its F from its threshold words, each warp stores the 32 bits of its vectors as
+// one word, and nfix counts the set ones.
 // Both count in nskip the vectors that did not draw (the fixed-allele passes).
 // kSample (an instance whose words are not kept yet): nfix counts 16 for every vector the
 // fixed-allele test finds at the bounds (the test runs on about one pass in 16 while the
@@ -899,8 +902,8 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
     uint8_t *xst_ptr = xptr;
     const uint8_t *xo_ptr = xoptr;
     int rr = b.r_sub;
-    uint16_t *fptr = nullptr;                   // kF: this thread's F word of row ra + rr
-    if constexpr (kF) fptr = p.fword + (size_t)ra * p.fstride + (size_t)g.vec;
+    uint32_t *fptr = nullptr;                   // kF: this warp's F word of row ra + rr
+    if constexpr (kF) fptr = p.fword + (size_t)ra * (p.fstride >> 5) + (size_t)(g.vec >> 5);
     auto issue = [&](uint32_t stage, bool v) {
         if constexpr (kS8)
             cp_async8(slots + (size_t)stage * kThreads, v ? (const void *)ld_ptr : (const void *)p.state,
@@ -950,12 +953,11 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
             *xst_ptr = (uint8_t)xbits;
         }
         if constexpr (kF) {
-            const uint32_t fw = zor == 0u ? (0x100u | xbits) : 0u;
-            if (g.active && ok) {
-                *fptr = (uint16_t)fw;
-                *nfix += fw != 0u ? 1u : 0u;
-            }
-            fptr += p.fstride;
+            const bool fx = g.active && ok && zor == 0u;
+            const uint32_t fb = __ballot_sync(0xffffffffu, fx);
+            if ((threadIdx.x & 31) == 0 && ok) *fptr = fb;
+            *nfix += fx ? 1u : 0u;
+            fptr += p.fstride >> 5;
         }
         add_row_sums<kNarrow>(b.lanes, b.leader, ok, rr, accn, acw, acv, s_acc32, s_acc64);
         st_ptr += sstep;
@@ -1007,6 +1009,17 @@ __device__ __forceinline__ uint32_t narrow_sums_bits(uint32_t x8, uint4 ib)
     return sw | (sv << 16);
 }
 
+// Bit k = (byte k of a == byte k of b), for the 8 bytes of two uint2: the zero bytes of the
+// difference (0x80 in each, exactly: no borrow crosses a byte), gathered by a multiply whose
+// four terms move bit 7, 15, 23, 31 to bits 28-31 without carries.
+__device__ __forceinline__ uint32_t equal_bytes8(uint2 a, uint2 b)
+{
+    const uint32_t d0 = a.x ^ b.x, d1 = a.y ^ b.y;
+    const uint32_t z0 = ~(((d0 & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d0 | 0x7f7f7f7fu);
+    const uint32_t z1 = ~(((d1 & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d1 | 0x7f7f7f7fu);
+    return (((z0 >> 7) * 0x10204080u) >> 28) | ((((z1 >> 7) * 0x10204080u) >> 28) << 4);
+}
+
 template <int kRule>
 __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int ra, int seg_rows, int32_t t,
                                                const uint8_t *x_prev, uint8_t *x_cur, const uint8_t *elite_row,
@@ -1027,33 +1040,28 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     const int nrows = seg_rows > warp ? (seg_rows - warp + 7) >> 3 : 0;     // this warp's rows
 
     // F and the previous alleles of this warp's next rows in flight (one row's work is too
-    // short to cover a load's latency); the first loads go out before the segment's others
-    const uint4 *fsrc = reinterpret_cast<const uint4 *>(p.fword + (size_t)(ra + warp) * fstride + vb);
+    // short to cover a load's latency); the first loads go out before the segment's others.
+    // A lane's 8 vectors have 8 bits of F: byte l of the tile's 8 words of the row.
+    const uint8_t *fsrc = reinterpret_cast<const uint8_t *>(p.fword + (size_t)(ra + warp) * (fstride >> 5) +
+                                                            (vt >> 5)) + lane;
     const uint2 *xsrc = reinterpret_cast<const uint2 *>(x_prev + (size_t)(ra + warp) * xstride + vb);
-    const size_t fstep = fstride, xstep = xstride;              // 8 rows in uint4 / uint2 units
-    auto fload = [&](int m) -> uint4 {
-        return (nact > 0 && m < nrows) ? __ldcg(fsrc + (size_t)m * fstep) : make_uint4(0u, 0u, 0u, 0u);
+    const size_t fstep = 8 * (fstride >> 3), xstep = xstride;   // 8 rows in bytes / uint2 units
+    auto fload = [&](int m) -> uint32_t {
+        return (nact > 0 && m < nrows) ? (uint32_t)__ldcg(fsrc + (size_t)m * fstep) : 0u;
     };
     auto xload = [&](int m) -> uint2 {
         return (nact > 0 && m < nrows) ? __ldcg(xsrc + (size_t)m * xstep) : make_uint2(0u, 0u);
     };
-    uint4 fb0 = fload(0), fb1 = fload(1), fb2 = fload(2);
-    uint2 xb0 = xload(0), xb1 = xload(1), xb2 = xload(2);
+    uint32_t fb0 = fload(0), fb1 = fload(1), fb2 = fload(2), fb3 = fload(3), fb4 = fload(4), fb5 = fload(5);
+    uint2 xb0 = xload(0), xb1 = xload(1), xb2 = xload(2), xb3 = xload(3), xb4 = xload(4), xb5 = xload(5);
 
     SegCtx g;
     seg_setup<true, true, kRule == 0>(p, g, tile, threadIdx.x, kThreads, elite_row);
     if (kRule == 1) s_e8[threadIdx.x] = (uint8_t)g.e8;
-    // this lane's 8 elite alleles (the sides of its stable vectors), and the pair words a
-    // stable F equals: 0x100 | allele, per half
+    // this lane's 8 elite alleles: a vector is stable when it is fixed and its previous
+    // alleles (its sides) equal them
     uint2 e8s = make_uint2(0u, 0u);
     if (nact > 0) e8s = __ldcg(reinterpret_cast<const uint2 *>(elite_row + vb));
-    const uint32_t ew[2] = {e8s.x, e8s.y};
-    uint32_t tgt[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t b0 = (ew[k >> 1] >> (16 * (k & 1))) & 0xffu, b1 = (ew[k >> 1] >> (16 * (k & 1) + 8)) & 0xffu;
-        tgt[k] = (0x100u | b0) | ((0x100u | b1) << 16);
-    }
     const uint32_t vmask = (1u << nact) - 1u;
     __syncthreads();                            // every thread reads the slots of the block's columns
     uint4 *const sbase = p.state + (size_t)ra * svec + vt;      // row ra, the tile's vector 0
@@ -1063,28 +1071,25 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     uint32_t head = 0;                          // entries listed so far (warp-uniform)
 
     // Steps 1 and 2 for this warp's next row (row = warp + 8 m of the segment). A list entry
-    // is row << 17 | (F was nonzero) << 16 | previous alleles << 8 | vector of the tile.
+    // is row << 17 | (F was set) << 16 | previous alleles << 8 | vector of the tile.
     auto produce = [&]() {
-        const uint4 f = fb0;
+        const uint32_t fbits = fb0;
         fb0 = fb1;
         fb1 = fb2;
-        fb2 = fload(m + 3);
+        fb2 = fb3;
+        fb3 = fb4;
+        fb4 = fb5;
+        fb5 = fload(m + 6);
         const uint2 xo = xb0;
         xb0 = xb1;
         xb1 = xb2;
-        xb2 = xload(m + 3);
+        xb2 = xb3;
+        xb3 = xb4;
+        xb4 = xb5;
+        xb5 = xload(m + 6);
         const int row = warp + 8 * m;
         ++m;
-        const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
-        uint32_t sm = 0u, nz = 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t w = (k & 1) ? (fw[k >> 1] >> 16) : (fw[k >> 1] & 0xffffu);
-            const uint32_t h = (k & 1) ? ((fw[k >> 1] ^ tgt[k >> 1]) >> 16) : ((fw[k >> 1] ^ tgt[k >> 1]) & 0xffffu);
-            sm |= (h == 0u ? 1u : 0u) << k;
-            nz |= (w != 0u ? 1u : 0u) << k;
-        }
-        sm &= vmask;
+        const uint32_t sm = fbits & equal_bytes8(xo, e8s) & vmask;
         const uint32_t um = vmask & ~sm;
         const uint32_t ns = (uint32_t)__popc(sm);
         nfix += ns;
@@ -1095,7 +1100,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         } else if (sm != 0u) {
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                if ((sm >> k) & 1u) xp[k] = (uint8_t)(ew[k >> 2] >> (8 * (k & 3)));
+                if ((sm >> k) & 1u) xp[k] = (uint8_t)((k < 4 ? e8s.x : e8s.y) >> (8 * (k & 3)));
         }
         // the row's unstable vectors, in lane order (an exclusive prefix sum of the counts)
         const uint32_t cnt = (uint32_t)__popc(um);
@@ -1113,7 +1118,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
                 const int k = __ffs((int)bits) - 1;
                 bits &= bits - 1u;
                 const uint32_t xk = ((k < 4 ? xo.x : xo.y) >> (8 * (k & 3))) & 0xffu;
-                list[pos & (kListCap - 1)] = ((uint32_t)row << 17) | (((nz >> k) & 1u) << 16) | (xk << 8) |
+                list[pos & (kListCap - 1)] = ((uint32_t)row << 17) | (((fbits >> k) & 1u) << 16) | (xk << 8) |
                                              (8u * (uint32_t)lane + (uint32_t)k);
                 ++pos;
             }
@@ -1175,9 +1180,13 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         }
         sbase[(size_t)row * svec + col] = s;
         xbase[(size_t)row * xstride + col] = (uint8_t)xbits;
-        const uint32_t fwn = z == 0u ? (0x100u | xbits) : 0u;
-        if (fwn != 0u || ((e >> 16) & 1u)) p.fword[((size_t)ra + row) * fstride + vec] = (uint16_t)fwn;
-        nfix += fwn != 0u ? 1u : 0u;
+        const uint32_t fx = z == 0u ? 1u : 0u;
+        if (fx != ((e >> 16) & 1u)) {            // F changed: set or clear this vector's bit
+            uint32_t *w = p.fword + ((size_t)ra + row) * (fstride >> 5) + (vec >> 5);
+            if (fx) atomicOr(w, 1u << (vec & 31u));
+            else atomicAnd(w, ~(1u << (vec & 31u)));
+        }
+        nfix += fx;
     };
 
     // Listing runs ahead of the copies in bursts: the steps up to jc + 7 are listed before
@@ -2749,7 +2758,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(GenParams p, size_t stat
     }
     if (p.fword) {   // no qubit at a bound: every fixed-vector word 0
         uint4 *f = reinterpret_cast<uint4 *>(p.fword);
-        const size_t n = (size_t)p.np * (size_t)p.fstride / 8;
+        const size_t n = (size_t)p.np * (size_t)(p.fstride >> 5) / 4;
         for (size_t i = i0; i < n; i += stride) f[i] = make_uint4(0u, 0u, 0u, 0u);
         for (size_t i = i0; i < (size_t)p.np; i += stride) {
             p.fprev[i] = 0ull;
