@@ -1045,12 +1045,15 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     const uint8_t *fsrc = reinterpret_cast<const uint8_t *>(p.fword + (size_t)(ra + warp) * (fstride >> 5) +
                                                             (vt >> 5)) + lane;
     const uint2 *xsrc = reinterpret_cast<const uint2 *>(x_prev + (size_t)(ra + warp) * xstride + vb);
-    const size_t fstep = 8 * (fstride >> 3), xstep = xstride;   // 8 rows in bytes / uint2 units
+    // 8 rows in bytes / uint2 units; both below 2^32, so each address is one 32 x 32 -> 64
+    // multiply-add
+    const uint32_t fstep = (uint32_t)fstride, xstep = (uint32_t)xstride;
+    const int mlim = nact > 0 ? nrows : 0;      // rows this lane loads
     auto fload = [&](int m) -> uint32_t {
-        return (nact > 0 && m < nrows) ? (uint32_t)__ldcg(fsrc + (size_t)m * fstep) : 0u;
+        return m < mlim ? (uint32_t)__ldcg(fsrc + (size_t)(uint32_t)m * (size_t)fstep) : 0u;
     };
     auto xload = [&](int m) -> uint2 {
-        return (nact > 0 && m < nrows) ? __ldcg(xsrc + (size_t)m * xstep) : make_uint2(0u, 0u);
+        return m < mlim ? __ldcg(xsrc + (size_t)(uint32_t)m * (size_t)xstep) : make_uint2(0u, 0u);
     };
     uint32_t fb0 = fload(0), fb1 = fload(1), fb2 = fload(2), fb3 = fload(3), fb4 = fload(4), fb5 = fload(5);
     uint2 xb0 = xload(0), xb1 = xload(1), xb2 = xload(2), xb3 = xload(3), xb4 = xload(4), xb5 = xload(5);
@@ -1066,6 +1069,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     __syncthreads();                            // every thread reads the slots of the block's columns
     uint4 *const sbase = p.state + (size_t)ra * svec + vt;      // row ra, the tile's vector 0
     uint8_t *const xbase = x_cur + (size_t)ra * xstride + vt;
+    uint8_t *const xlane = xbase + 8u * (uint32_t)lane;         // this lane's alleles, row 0
 
     int m = 0;                                  // this warp's rows listed so far
     uint32_t head = 0;                          // entries listed so far (warp-uniform)
@@ -1094,8 +1098,10 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         const uint32_t ns = (uint32_t)__popc(sm);
         nfix += ns;
         nskip += ns;
-        uint8_t *xp = xbase + (size_t)row * xstride + 8u * (uint32_t)lane;
-        if (sm == 0xffu) {
+        // The stable vectors' alleles; with all 8 vectors active, the unstable ones' bytes go
+        // too and are overwritten by their own pass after the __syncwarp that ends the listing
+        uint8_t *xp = xlane + (size_t)(uint32_t)row * (size_t)xstep;
+        if (nact == 8 && sm != 0u) {
             *reinterpret_cast<uint2 *>(xp) = e8s;
         } else if (sm != 0u) {
 #pragma unroll
@@ -1195,11 +1201,12 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     // loop between bursts issues and computes without listing.
     while (m < nrows && head < 8u * 32u) produce();
     __syncwarp();
+    const bool any = m < nrows || head != 0u;   // else every row was stable: no copies
 #pragma unroll 1
-    for (uint32_t j = 0; j < kRingStages - 1; ++j) issue(j);
+    for (uint32_t j = 0; any && j < kRingStages - 1; ++j) issue(j);
     uint32_t jc = 0;
 #pragma unroll 1
-    for (;;) {
+    while (any) {
         while (m < nrows && head < (jc + 8u) * 32u) produce();
         __syncwarp();
         const bool done = m >= nrows;
