@@ -1020,6 +1020,9 @@ __device__ __forceinline__ uint32_t equal_bytes8(uint2 a, uint2 b)
     return (((z0 >> 7) * 0x10204080u) >> 28) | ((((z1 >> 7) * 0x10204080u) >> 28) << 4);
 }
 
+// Rows of F and previous alleles a warp of the sparse form has in flight.
+constexpr int kSparseAhead = 4;
+
 template <int kRule>
 __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int ra, int seg_rows, int32_t t,
                                                const uint8_t *x_prev, uint8_t *x_cur, const uint8_t *elite_row,
@@ -1055,8 +1058,13 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     auto xload = [&](int m) -> uint2 {
         return m < mlim ? __ldcg(xsrc + (size_t)(uint32_t)m * (size_t)xstep) : make_uint2(0u, 0u);
     };
-    uint32_t fb0 = fload(0), fb1 = fload(1), fb2 = fload(2), fb3 = fload(3), fb4 = fload(4), fb5 = fload(5);
-    uint2 xb0 = xload(0), xb1 = xload(1), xb2 = xload(2), xb3 = xload(3), xb4 = xload(4), xb5 = xload(5);
+    uint32_t fb[kSparseAhead];                  // slot i: row m + ((i - m) mod kSparseAhead)
+    uint2 xb[kSparseAhead];
+#pragma unroll
+    for (int i = 0; i < kSparseAhead; ++i) {
+        fb[i] = fload(i);
+        xb[i] = xload(i);
+    }
 
     SegCtx g;
     seg_setup<true, true, kRule == 0>(p, g, tile, threadIdx.x, kThreads, elite_row);
@@ -1076,21 +1084,11 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
 
     // Steps 1 and 2 for this warp's next row (row = warp + 8 m of the segment). A list entry
     // is row << 17 | (F was set) << 16 | previous alleles << 8 | vector of the tile.
-    auto produce = [&]() {
-        const uint32_t fbits = fb0;
-        fb0 = fb1;
-        fb1 = fb2;
-        fb2 = fb3;
-        fb3 = fb4;
-        fb4 = fb5;
-        fb5 = fload(m + 6);
-        const uint2 xo = xb0;
-        xb0 = xb1;
-        xb1 = xb2;
-        xb2 = xb3;
-        xb3 = xb4;
-        xb4 = xb5;
-        xb5 = xload(m + 6);
+    auto produce = [&](uint32_t &fslot, uint2 &xslot) {
+        const uint32_t fbits = fslot;
+        const uint2 xo = xslot;
+        fslot = fload(m + kSparseAhead);        // the slot's next row
+        xslot = xload(m + kSparseAhead);
         const int row = warp + 8 * m;
         ++m;
         const uint32_t sm = fbits & equal_bytes8(xo, e8s) & vmask;
@@ -1129,6 +1127,23 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
                 ++pos;
             }
             head += total;
+        }
+    };
+
+    // Lists rows while m < nrows and head < lim. Row m sits in slot m % 4: a slot is read
+    // once, when its row is listed, and refilled at once, so each load stays in flight for
+    // four rows (moving the window through the registers would wait for every load at the
+    // next row).
+    static_assert(kSparseAhead == 4, "slots are selected by m % 4");
+    auto list_rows = [&](uint32_t lim) {
+#pragma unroll 1
+        for (;;) {
+            switch (m & 3) {
+            case 0: if (!(m < nrows && head < lim)) return; produce(fb[0], xb[0]); [[fallthrough]];
+            case 1: if (!(m < nrows && head < lim)) return; produce(fb[1], xb[1]); [[fallthrough]];
+            case 2: if (!(m < nrows && head < lim)) return; produce(fb[2], xb[2]); [[fallthrough]];
+            default: if (!(m < nrows && head < lim)) return; produce(fb[3], xb[3]);
+            }
         }
     };
 
@@ -1199,7 +1214,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     // the copies of jc + 7 are issued, and a burst stops once they are, so the live entries
     // (from step jc on) stay below 32 (jc + 8) + 256 <= 32 jc + 512, the list's size. The
     // loop between bursts issues and computes without listing.
-    while (m < nrows && head < 8u * 32u) produce();
+    list_rows(8u * 32u);
     __syncwarp();
     const bool any = m < nrows || head != 0u;   // else every row was stable: no copies
 #pragma unroll 1
@@ -1207,7 +1222,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     uint32_t jc = 0;
 #pragma unroll 1
     while (any) {
-        while (m < nrows && head < (jc + 8u) * 32u) produce();
+        list_rows((jc + 8u) * 32u);
         __syncwarp();
         const bool done = m >= nrows;
         const uint32_t avail = done ? (head + 31u) / 32u : head / 32u;
