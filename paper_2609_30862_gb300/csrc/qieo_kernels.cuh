@@ -997,6 +997,10 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 // ---------------------------------------------------------------------------------------
 constexpr int kListCap = 512;               // entries of a warp's list (a power of two)
 __shared__ uint32_t s_list[kThreads / 32][kListCap];
+// The queue index and descriptor of a block's next segment in sparse generations (written by
+// thread 0 during the current segment, read after its last barrier)
+__shared__ int32_t s_next_qi;
+__shared__ int4 s_next_sg;
 __shared__ uint8_t s_e8[kThreads];          // rule R2: the previous elite's alleles of the tile's vectors
 
 // Packed narrow sums (sum v << 16 | sum w) of 8 genes from their alleles (bit i = gene i)
@@ -1028,7 +1032,7 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
                                                const uint8_t *x_prev, uint8_t *x_cur, const uint8_t *elite_row,
                                                const unsigned char *thr_bytes, uint4 *slots,
                                                uint32_t *s_acc32, uint32_t *list, uint32_t &nfix,
-                                               uint32_t &nskip)
+                                               uint32_t &nskip, int32_t next)
 {
     constexpr uint32_t kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1216,6 +1220,10 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
     // loop between bursts issues and computes without listing.
     list_rows(8u * 32u);
     __syncwarp();
+    // thread 0: the next segment's descriptor (its index, taken at the segment's start, has
+    // arrived by now), published before the flush's last barrier
+    int4 sg_next = make_int4(0, 0, 0, 0);
+    if (threadIdx.x == 0 && next < p.nsegs) sg_next = __ldg(p.segq + next);
     const bool any = m < nrows || head != 0u;   // else every row was stable: no copies
 #pragma unroll 1
     for (uint32_t j = 0; any && j < kRingStages - 1; ++j) issue(j);
@@ -1236,6 +1244,10 @@ __device__ __forceinline__ void sparse_segment(const GenParams &p, int tile, int
         }
     }
     cp_async_wait<0>();
+    if (threadIdx.x == 0) {      // every thread read the current ones before the setup barrier
+        s_next_qi = next;
+        s_next_sg = sg_next;
+    }
     flush_segment<true, 2>(p, t, ra, seg_rows, s_acc32, nullptr, tile);
 }
 
@@ -1315,21 +1327,25 @@ __device__ __forceinline__ void generation_body_queue(const GenParams &p, const 
     clear_row_sums<kNarrow>(p.seg_rows_max, s_acc32, s_acc64);
     // Sparse generations: thread 0 takes the next segment's index while the block works on
     // the current one (the atomic's round trip is off the block's path; a sparse
-    // segment's work is short) and publishes it after the segment's last barrier, with one
-    // more barrier before every thread reads it. Dense ones take it when they need it
-    // (holding a second segment would coarsen the end of the guided schedule).
-    if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
+    // segment's work is short), loads its descriptor once the index has arrived, and
+    // publishes both before the segment's last barrier (the flush's), which every thread
+    // passes before reading them. Dense ones take the index when they need it (holding a
+    // second segment would coarsen the end of the guided schedule).
+    if (threadIdx.x == 0) {
+        s_qi = (int32_t)atomicAdd(ctr, 1u);
+        if (kF && sparse && s_qi < p.nsegs) s_next_sg = __ldg(p.segq + s_qi);
+    }
     __syncthreads();
     int32_t qi = s_qi;
     for (;;) {
         if (qi >= p.nsegs) break;
         int32_t next = 0;
         if (sparse && threadIdx.x == 0) next = (int32_t)atomicAdd(ctr, 1u);
-        const int4 sg = __ldg(p.segq + qi);
+        const int4 sg = (kF && sparse) ? s_next_sg : __ldg(p.segq + qi);
         if constexpr (kF) {
             if (sparse)
                 sparse_segment<kRule>(p, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots,
-                                      s_acc32, s_list[threadIdx.x >> 5], nfix, nskip);
+                                      s_acc32, s_list[threadIdx.x >> 5], nfix, nskip, next);
             else if (keep)
                 ring_segment<kNarrow, kRule, kCip, ParamKeys, kS8, kSegDelta, false, true>(
                     p, ParamKeys{p}, b, sg.x, sg.y, sg.z, t, x_prev, x_cur, elite_row, thr_bytes, slots, s_acc32,
@@ -1343,15 +1359,14 @@ __device__ __forceinline__ void generation_body_queue(const GenParams &p, const 
                                                                           x_prev, x_cur, elite_row, thr_bytes,
                                                                           slots, s_acc32, s_acc64, countdown);
         }
-        if (sparse) {
-            if (threadIdx.x == 0) s_qi = next;
-            __syncthreads();
+        if (kF && sparse) {
+            qi = s_next_qi;             // published before the flush's last barrier
         } else {
             // every thread has read the index before the segment's first barrier
             if (threadIdx.x == 0) s_qi = (int32_t)atomicAdd(ctr, 1u);
             __syncthreads();
+            qi = s_qi;
         }
-        qi = s_qi;
     }
     if constexpr (kF) {
         // one atomic per block for each count
