@@ -237,9 +237,10 @@ typedef struct {
                                 a GB300, unless QIEO_FLAG_STREAMED, QIEO_FLAG_COOPERATIVE,
                                 QIEO_FLAG_PER_GENERATION, QIEO_FLAG_TIME_GENERATIONS,
                                 QIEO_FLAG_CONVERGE, elite_on_host or byte state) */
-    int32_t fixed_words;     /* out: 1 when the instance keeps a fixed-vector word per 8 genes
-                                (16 bits: all eight qubits at theta = 0 or pi/2, and their
-                                sides), so that a generation in which most vectors are fixed
+    int32_t fixed_words;     /* out: 1 when the instance keeps a fixed-vector bit per 8 genes
+                                (set when all eight qubits sit at theta = 0 or pi/2; their
+                                sides are the vector's previous alleles), so that a
+                                generation in which most vectors are fixed
                                 takes the sparse form: only the vectors that are not fixed, or
                                 that the previous elite turns away from their bound, run CIP,
                                 QIP and Evaluation in full; the rest contribute their sides.
