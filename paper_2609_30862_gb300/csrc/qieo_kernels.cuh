@@ -979,9 +979,10 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 // the warps split the segment by rows, not columns: warp w takes rows w, w + 8, ... and lane
 // l the 8 consecutive vectors 8 l .. 8 l + 7 of the tile, so every warp meets the same
 // columns and the same share of the work. Per row a warp:
-//   1. reads F of its 256 vectors (one 16-byte load a lane) and writes the stable vectors'
-//      alleles (their sides; 8 bytes a lane when all 8 are stable); nothing else: the row's
-//      totals of the generation before (fprev) already hold their share;
+//   1. reads F of its 256 vectors and their previous alleles (one byte and 8 bytes a lane,
+//      loaded four rows ahead) and writes the stable vectors' alleles (their sides; one
+//      8-byte store a lane); nothing else: the row's totals of the generation before
+//      (fprev) already hold their share;
 //   2. lists the row's unstable vectors in its slice of a shared-memory ring.
 // It then streams the listed vectors' state through the per-thread cp.async ring, 32 per
 // step, and runs the full pass on each (the
@@ -992,8 +993,7 @@ __device__ __forceinline__ void ring_segment(const GenParams &p, const Keys &key
 // Listing runs ahead of the copies, so the ring's 7 rows of look-ahead become 7 steps of
 // 32 listed vectors. All sums are exact integers, so the results equal the dense form's.
 // Segments hold at most 256 rows (a list entry holds the row, the vector, its previous
-// alleles, loaded with F, and whether its F was nonzero, so that F is written only when it
-// changes).
+// alleles and its F bit, so that F is written only when it changes).
 // ---------------------------------------------------------------------------------------
 constexpr int kListCap = 512;               // entries of a warp's list (a power of two)
 __shared__ uint32_t s_list[kThreads / 32][kListCap];
@@ -1014,7 +1014,7 @@ __device__ __forceinline__ uint32_t narrow_sums_bits(uint32_t x8, uint4 ib)
 }
 
 // Bit k = (byte k of a == byte k of b), for the 8 bytes of two uint2: the zero bytes of the
-// difference (0x80 in each, exactly: no borrow crosses a byte), gathered by a multiply whose
+// difference (0x80 in each, exactly: no carry crosses a byte), gathered by a multiply whose
 // four terms move bit 7, 15, 23, 31 to bits 28-31 without carries.
 __device__ __forceinline__ uint32_t equal_bytes8(uint2 a, uint2 b)
 {
