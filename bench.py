@@ -570,16 +570,22 @@ def generation_phases(Q, prob, c, np_, G, rank, flags, stream, torch, hbm_peak, 
     return out
 
 
+# Bytes a vector that did not draw needs in a sparse generation: its fixed-vector bit and its
+# previous alleles read, its alleles written.
+STABLE_BYTES = 1.0 / 8.0 + 1.0 + 1.0
+
+
 def work_adjusted(ms, drawn, nvec, hbm_peak, int_peak):
     """The roofline of the work each generation actually needed. A vector that drew (the
     qieo_get_drawn_vectors count) needs its 8 draws at the measured integer ceiling and its
-    32 B of state (read and written); one that did not needs its fixed-vector word read and
-    its alleles written (3 B). Per generation the bound is the slower of the two; the
-    fraction is the sum of the bounds over the sum of the measured times."""
+    32 B of state (read and written); one that did not needs its fixed-vector bit and its
+    previous alleles read and its alleles written (STABLE_BYTES = 1/8 + 1 + 1 B). Per
+    generation the bound is the slower of the two; the fraction is the sum of the bounds
+    over the sum of the measured times."""
     import numpy as np
     d = np.asarray(drawn, dtype=np.float64)
     t_int = 8.0 * d / int_peak
-    t_hbm = (32.0 * d + 3.0 * (nvec - d)) / (hbm_peak * 1e9)
+    t_hbm = (32.0 * d + STABLE_BYTES * (nvec - d)) / (hbm_peak * 1e9)
     bound = np.maximum(t_int, t_hbm)
     meas = np.asarray(ms, dtype=np.float64) * 1e-3
     return {"frac": float(bound.sum() / meas.sum()),
@@ -589,7 +595,7 @@ def work_adjusted(ms, drawn, nvec, hbm_peak, int_peak):
             "frac_per_25": [round(float(bound[i:i + 25].sum() / meas[i:i + 25].sum()), 3)
                             for i in range(0, len(d), 25)],
             "what": "per generation: max(8 draws per vector that drew at the measured integer "
-                    "ceiling, (32 B per vector that drew + 3 B per one that did not) at the "
+                    "ceiling, (32 B per vector that drew + 2.125 B per one that did not) at the "
                     "measured HBM bandwidth), summed, over the measured generation times"}
 
 

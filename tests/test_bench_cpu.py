@@ -80,16 +80,18 @@ def test_oracle_scan_on_host_cores():
 
 def test_work_adjusted_roofline_arithmetic():
     """The work-adjusted bound of a generation is the slower of its draws at the integer
-    ceiling and its bytes at HBM: 32 B for each vector that drew, 3 B for each that did not."""
+    ceiling and its bytes at HBM: 32 B for each vector that drew, 2.125 B (a fixed-vector
+    bit and the previous alleles read, the alleles written) for each that did not."""
     sys.path.insert(0, ROOT)
     import bench
+    assert bench.STABLE_BYTES == 2.125
     nvec, hbm, intc = 1000, 1.0, 8.0e6             # GB/s (1e9 B/s) and gene-updates/s
     # all drew: draws 8000 / 8e6 = 1 ms; bytes 32e3 / 1e9 = 32 us -> 1 ms (integer-bound)
-    # none drew: bytes 3e3 / 1e9 = 3 us -> 3 us (HBM-bound)
+    # none drew: bytes 2.125e3 / 1e9 = 2.125 us (HBM-bound)
     w = bench.work_adjusted([2.0, 0.006], [1000, 0], nvec, hbm, intc)
-    assert abs(w["bound_us"] - (1000.0 + 3.0)) < 1e-6
+    assert abs(w["bound_us"] - (1000.0 + 2.125)) < 1e-6
     assert abs(w["measured_us"] - 2006.0) < 1e-6
-    assert abs(w["frac"] - 1003.0 / 2006.0) < 1e-12
+    assert abs(w["frac"] - 1002.125 / 2006.0) < 1e-12
     assert abs(w["drawn_fraction"] - 0.5) < 1e-12
 
 
