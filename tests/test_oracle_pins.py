@@ -3,8 +3,9 @@
 Each test ties one part of the oracle to the paper or to mathematics that the oracle's
 code does not share: an independent Philox implementation, a 60-digit evaluation of the
 threshold table, a dynamic-programming knapsack optimum and the closed-form cases of
-eq. (1), binomial frequencies of the observation, and the amplitude (rotation-matrix)
-form of the loop against the angle-index form.
+eq. (1), binomial frequencies of the observation, the amplitude (rotation-matrix) form of
+the loop against the angle-index form, and the loop's fixed points at the bounds (qubits at
+theta = 0 or pi/2 on the elite's side).
 """
 import math
 import os
@@ -347,3 +348,43 @@ def test_convergence_window_one_and_cap(oracle_mod):
     assert _first_converged(full.hist_f, 20) is None
     r2 = O.run(prob, 17, 150, seed=8, rule=1, window=20)
     assert int(r2.t[0]) == 150 and not r2.stopped and np.array_equal(r2.k, full.k)
+
+
+@pytest.mark.parametrize("rule,D,start", [(0, 100, "fresh"), (0, 12, "fresh"), (1, 100, "saturated"),
+                                          (0, 100, "saturated")])
+def test_qubits_at_a_bound_on_the_elite_side_stay_put(oracle_mod, rule, D, start):
+    """What lets a generation skip most of its work once the population has collapsed: a
+    qubit at theta = 0 or pi/2 (angle index -K or K) observes its side whatever the draw
+    (T[0] = 0, T[2K] = 2^32), and CIP leaves it when that side is the elite's allele (R1
+    rotates toward the elite's allele and it already sits at that bound; R2 rotates only the
+    qubits whose allele differs from the elite's). So an 8-gene vector whose qubits all sit at
+    the bound on the side of generation t's elite keeps its angle indices through CIP(t), and
+    generation t + 1 observes exactly the elite's alleles there. Checked vector by vector on
+    every generation of runs from the initial state (R1 collapses them) and from saturated
+    states (rows sharing one pattern but for a few; R2 keeps a fresh population spread), with
+    the checked vectors a majority by the end."""
+    from saturated import saturated_start
+    O = oracle_mod
+    ng, np_, seed, G = 2400, 48, 40 + rule + D, (150 if start == "fresh" else 40)
+    K, nv = D // 4, ng // 8
+    prob = W.knapsack(ng, seed)
+    st = O.State(np_, ng)
+    if start == "saturated":
+        st.k[:] = saturated_start(ng, np_, seed, n_odd=6, flips=30, D=D)
+    checked, last_frac = 0, 0.0
+    for t in range(G - 1):
+        k_obs = st.k.copy()                              # observed by generation t
+        O.run(prob, np_, 1, seed=seed, rule=rule, D=D, state=st)   # generation t and CIP(t)
+        xe = st.x[int(st.hist_e[-1])].astype(np.int16).reshape(nv, 8)
+        at = (np.abs(k_obs.astype(np.int32)) == K).reshape(np_, nv, 8)
+        side = (k_obs > 0).astype(np.int16).reshape(np_, nv, 8)
+        stable = (at & (side == xe[None])).all(axis=2)    # [np_, nv]
+        k_next = st.k.reshape(np_, nv, 8)
+        assert np.array_equal(k_next[stable], k_obs.reshape(np_, nv, 8)[stable]), t
+        nxt = O.run(prob, np_, 1, seed=seed, rule=rule, D=D, state=st.copy())   # generation t + 1
+        x_next = nxt.x.reshape(np_, nv, 8)
+        want = np.broadcast_to(xe[None], (np_, nv, 8)).astype(np.uint8)
+        assert np.array_equal(x_next[stable], want[stable]), t
+        checked += int(stable.sum())
+        last_frac = float(stable.mean())
+    assert last_frac > 0.5 and checked > 0
