@@ -35,7 +35,9 @@
  * Pins (tests): Philox against PyTorch's independent header implementation; the
  * threshold table against a 60-digit evaluation; eq. (1) against a dynamic-programming
  * knapsack optimum and closed-form special cases; observation frequencies against
- * sin^2; the angle-index form (qo_run) against the amplitude form (qo_run_fp64).
+ * sin^2; the angle-index form (qo_run) against the amplitude form (qo_run_fp64); the
+ * loop's fixed points at the bounds (qubits at theta = 0 or pi/2 on the elite's side keep
+ * their angle and observe the elite's allele).
  * The exact trajectory of the heuristic has no printed values in the paper: beyond the
  * agreement of the two forms it is parity unpinned.
  *
