@@ -612,6 +612,9 @@ class Instance:
         return qieo_get_generation_times(self.h, n)
 
     def drawn_vectors(self, first: int, n: int) -> np.ndarray:
+        """Per generation first .. first + n - 1, the 8-gene vectors that drew (observed by
+        Philox draws) in an instance that keeps fixed-vector bits: every vector in a dense
+        generation, only the unstable ones in a sparse generation."""
         return qieo_get_drawn_vectors(self.h, first, n)
 
     def phase_times(self):
